@@ -1,0 +1,414 @@
+/*
+ * FP64 CPU oracle for the two-dimensional 16-velocity (D2V16) thermal
+ * multiple-relaxation-time finite-difference lattice Boltzmann step of
+ * Chen, Xu, Zhang, Li and Succi, "Multiple-Relaxation-Time Lattice Boltzmann
+ * Approach to Compressible Flows with Flexible Specific-Heat Ratio and Prandtl
+ * Number" (arXiv:1004.5442).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the plain, slow, obviously-correct
+ * statement of what the GPU library computes.  Only the tests, the smoke check
+ * and the benchmark's CPU-baseline leg may load it.  It shares no code, header
+ * or table with the CUDA library: the model (velocities, eta, M) is built here
+ * from the paper's definitions and inverted here by Gauss-Jordan elimination.
+ *
+ * Everything is FP64, dense 16x16 loops, no blocking, fusion or reordering
+ * beyond what the method states:
+ *   Eq. 3        d_t f_i + v_ia d_a f_i = -Minv_il S_lk (fhat_k - fhat_k^eq)
+ *   Sect. "Construction of energy-conserving MRT LB model": velocity set,
+ *                eta_i, gamma = (b+2)/b, forward-Euler time stepping and
+ *                Lax-Wendroff space discretisation
+ *   Appendix     rows m_1..m_16 of M and the equilibria fhat^eq_1..16
+ *   Eq. 12 text  P = rho R T, e = b rho R T + j^2/rho (R = 1 throughout,
+ *                Sect. "Numerical Simulation and Analysis")
+ *   Sect. (b)    boundary nodes held at f^eq = Minv fhat^eq; y periodic
+ *
+ * Readings where the paper is silent (each listed in the design doc):
+ *   - order inside the "cyc" groups: (1,0),(0,1),(-1,0),(0,-1) and
+ *     (1,1),(-1,1),(-1,-1),(1,-1) times the group speed factor;
+ *   - "first-order upwind" in time is forward Euler; the Lax-Wendroff space
+ *     operator is applied axis by axis with the dt-dependent second
+ *     difference, without a mixed x-y term; the collision is explicit at t_n;
+ *   - eta enters M only as eta_i^2 = 25/4 for i = 1..4, 0 otherwise;
+ *   - a fixed-equilibrium boundary is one ghost cell beyond the domain that
+ *     holds, for ever, the initial f (= f^eq of the initial state) of the
+ *     adjacent domain cell.
+ *
+ * Storage: f[i][y][x], i = 0..15 (paper's i = 1..16), x fastest, no padding.
+ */
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define NV 16
+
+enum { ORC_BC_PERIODIC = 0, ORC_BC_FIXED_EQ = 1 };
+
+typedef struct {
+    int nx, ny;
+    double dx, dt;     /* dy == dx */
+    double b;          /* total number of degrees of freedom; gamma = (b+2)/b */
+    double s[NV];      /* relaxation rates s_1..s_16 in 1/time */
+    int bc_x, bc_y;    /* ORC_BC_PERIODIC or ORC_BC_FIXED_EQ */
+} orc_cfg;
+
+/* ------------------------------------------------------------------------ */
+/* Model: velocity set, eta_i, M and its inverse.                            */
+/* ------------------------------------------------------------------------ */
+
+/* D2V16 velocity set (Sect. "Construction of energy-conserving MRT LB model",
+ * velocity table): cyc(+-1,0) for i=1..4, cyc(+-6,0) for i=5..8,
+ * sqrt(2)(+-1,+-1) for i=9..12, (3/sqrt(2))(+-1,+-1) for i=13..16. */
+void orc_velocities(double vx[NV], double vy[NV], double eta2[NV])
+{
+    static const double axis[4][2] = {{1, 0}, {0, 1}, {-1, 0}, {0, -1}};
+    static const double diag[4][2] = {{1, 1}, {-1, 1}, {-1, -1}, {1, -1}};
+    const double c_diag2 = sqrt(2.0);
+    const double c_diag3 = 3.0 / sqrt(2.0);
+    for (int k = 0; k < 4; ++k) {
+        vx[k] = axis[k][0];            vy[k] = axis[k][1];
+        vx[4 + k] = 6.0 * axis[k][0];  vy[4 + k] = 6.0 * axis[k][1];
+        vx[8 + k] = c_diag2 * diag[k][0];  vy[8 + k] = c_diag2 * diag[k][1];
+        vx[12 + k] = c_diag3 * diag[k][0]; vy[12 + k] = c_diag3 * diag[k][1];
+    }
+    /* eta_i = 5/2 for i = 1..4 and 0 otherwise; it enters only squared. */
+    for (int i = 0; i < NV; ++i) eta2[i] = (i < 4) ? 6.25 : 0.0;
+}
+
+/* Transformation matrix, Appendix: M = (m_1, ..., m_16)^T with
+ *   m_1 = 1, m_2 = vx, m_3 = vy, m_4 = v^2 + eta^2, m_5 = v^2,
+ *   m_6 = vx^2 - vy^2, m_7 = vx vy, m_8 = vx (v^2+eta^2), m_9 = vy (v^2+eta^2),
+ *   m_10 = vx v^2, m_11 = vy v^2, m_12 = vx (vx^2-vy^2), m_13 = vy (vx^2-vy^2),
+ *   m_14 = v^2 (v^2+eta^2), m_15 = vx vy (v^2+eta^2),
+ *   m_16 = (vx^2-vy^2)(v^2+eta^2).
+ * M[k*16 + i] = m_{k+1, i+1}. */
+void orc_build_M(const double vx[NV], const double vy[NV], const double eta2[NV],
+                 double *M)
+{
+    for (int i = 0; i < NV; ++i) {
+        const double x = vx[i], y = vy[i];
+        const double v2 = x * x + y * y;
+        const double w = v2 + eta2[i];
+        const double d = x * x - y * y;
+        M[0 * NV + i] = 1.0;
+        M[1 * NV + i] = x;
+        M[2 * NV + i] = y;
+        M[3 * NV + i] = w;
+        M[4 * NV + i] = v2;
+        M[5 * NV + i] = d;
+        M[6 * NV + i] = x * y;
+        M[7 * NV + i] = x * w;
+        M[8 * NV + i] = y * w;
+        M[9 * NV + i] = x * v2;
+        M[10 * NV + i] = y * v2;
+        M[11 * NV + i] = x * d;
+        M[12 * NV + i] = y * d;
+        M[13 * NV + i] = v2 * w;
+        M[14 * NV + i] = x * y * w;
+        M[15 * NV + i] = d * w;
+    }
+}
+
+/* Gauss-Jordan elimination with partial pivoting on an n x n row-major
+ * matrix.  Returns 0 on success, -1 if a pivot is exactly zero. */
+int orc_invert(const double *A, double *Ainv, int n)
+{
+    double *a = (double *)malloc(sizeof(double) * (size_t)n * (size_t)(2 * n));
+    if (!a) return -1;
+    for (int r = 0; r < n; ++r)
+        for (int c = 0; c < 2 * n; ++c)
+            a[r * 2 * n + c] = (c < n) ? A[r * n + c] : (c - n == r ? 1.0 : 0.0);
+    for (int col = 0; col < n; ++col) {
+        int piv = col;
+        for (int r = col + 1; r < n; ++r)
+            if (fabs(a[r * 2 * n + col]) > fabs(a[piv * 2 * n + col])) piv = r;
+        if (a[piv * 2 * n + col] == 0.0) { free(a); return -1; }
+        if (piv != col)
+            for (int c = 0; c < 2 * n; ++c) {
+                double t = a[col * 2 * n + c];
+                a[col * 2 * n + c] = a[piv * 2 * n + c];
+                a[piv * 2 * n + c] = t;
+            }
+        const double p = a[col * 2 * n + col];
+        for (int c = 0; c < 2 * n; ++c) a[col * 2 * n + c] /= p;
+        for (int r = 0; r < n; ++r) {
+            if (r == col) continue;
+            const double m = a[r * 2 * n + col];
+            if (m == 0.0) continue;
+            for (int c = 0; c < 2 * n; ++c) a[r * 2 * n + c] -= m * a[col * 2 * n + c];
+        }
+    }
+    for (int r = 0; r < n; ++r)
+        for (int c = 0; c < n; ++c) Ainv[r * n + c] = a[r * 2 * n + n + c];
+    free(a);
+    return 0;
+}
+
+/* The oracle's model, built once per process. */
+static double g_vx[NV], g_vy[NV], g_eta2[NV], g_M[NV * NV], g_Minv[NV * NV];
+static int g_model_ready = 0;
+
+static void ensure_model(void)
+{
+    if (g_model_ready) return;
+    orc_velocities(g_vx, g_vy, g_eta2);
+    orc_build_M(g_vx, g_vy, g_eta2, g_M);
+    orc_invert(g_M, g_Minv, NV);
+    g_model_ready = 1;
+}
+
+/* Copy out the oracle's model: velocities, eta^2, M and M^-1 (row-major). */
+void orc_model(double vx[NV], double vy[NV], double eta2[NV], double *M, double *Minv)
+{
+    ensure_model();
+    memcpy(vx, g_vx, sizeof g_vx);
+    memcpy(vy, g_vy, sizeof g_vy);
+    memcpy(eta2, g_eta2, sizeof g_eta2);
+    memcpy(M, g_M, sizeof g_M);
+    memcpy(Minv, g_Minv, sizeof g_Minv);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Equilibrium moments (Appendix) and the macroscopic closure (Eq. 12 text). */
+/* ------------------------------------------------------------------------ */
+
+/* fhat^eq_1..16 from the conserved moments rho, jx, jy, e (R = 1):
+ * P = rho R T with e = b rho R T + j^2/rho, so P = (e - j^2/rho)/b. */
+void orc_feq_moments(double rho, double jx, double jy, double e, double b,
+                     double out[NV])
+{
+    const double R = 1.0;
+    const double j2 = jx * jx + jy * jy;
+    const double P = (e - j2 / rho) / b;
+    const double T = P / (rho * R);
+    const double dj = jx * jx - jy * jy;
+    out[0] = rho;
+    out[1] = jx;
+    out[2] = jy;
+    out[3] = e;
+    out[4] = 2.0 * P + j2 / rho;
+    out[5] = dj / rho;
+    out[6] = jx * jy / rho;
+    out[7] = (e + 2.0 * P) * jx / rho;
+    out[8] = (e + 2.0 * P) * jy / rho;
+    out[9] = (4.0 * P + jx * jx / rho + jy * jy / rho) * jx / rho;
+    out[10] = (4.0 * P + jx * jx / rho + jy * jy / rho) * jy / rho;
+    out[11] = (2.0 * P + jx * jx / rho - jy * jy / rho) * jx / rho;
+    out[12] = (-2.0 * P + jx * jx / rho - jy * jy / rho) * jy / rho;
+    out[13] = 2.0 * (b + 2.0) * rho * R * R * T * T
+            + (6.0 + b) * R * T * j2 / rho
+            + j2 * j2 / (rho * rho * rho);
+    out[14] = ((b + 4.0) * P + j2 / rho) * jx * jy / (rho * rho);
+    out[15] = ((b + 4.0) * P + j2 / rho) * dj / (rho * rho);
+}
+
+/* Velocity-space equilibrium f^eq = M^-1 fhat^eq (Sect. (b), boundary nodes;
+ * also the initial state). */
+void orc_feq(double rho, double ux, double uy, double T, double b, double feq[NV])
+{
+    ensure_model();
+    const double jx = rho * ux, jy = rho * uy;
+    const double e = b * rho * T + (jx * jx + jy * jy) / rho;
+    double m[NV];
+    orc_feq_moments(rho, jx, jy, e, b, m);
+    for (int i = 0; i < NV; ++i) {
+        double acc = 0.0;
+        for (int k = 0; k < NV; ++k) acc += g_Minv[i * NV + k] * m[k];
+        feq[i] = acc;
+    }
+}
+
+/* Initial state: f_i(x, y) = f^eq_i(rho, u, T) for every cell. */
+void orc_init(int nx, int ny, double b, const double *rho, const double *ux,
+              const double *uy, const double *T, double *f)
+{
+    const size_t n = (size_t)nx * (size_t)ny;
+    for (size_t c = 0; c < n; ++c) {
+        double feq[NV];
+        orc_feq(rho[c], ux[c], uy[c], T[c], b, feq);
+        for (int i = 0; i < NV; ++i) f[(size_t)i * n + c] = feq[i];
+    }
+}
+
+/* Fixed-equilibrium ghost cells, taken from the initial f: gx[i][side][y]
+ * (side 0 = x = -1, side 1 = x = nx) and gy[i][side][x] (side 0 = y = -1,
+ * side 1 = y = ny).  Each ghost copies the adjacent domain cell. */
+void orc_ghosts_from_initial(int nx, int ny, const double *f0, double *gx, double *gy)
+{
+    const size_t n = (size_t)nx * (size_t)ny;
+    for (int i = 0; i < NV; ++i) {
+        for (int y = 0; y < ny; ++y) {
+            gx[((size_t)i * 2 + 0) * ny + y] = f0[(size_t)i * n + (size_t)y * nx + 0];
+            gx[((size_t)i * 2 + 1) * ny + y] = f0[(size_t)i * n + (size_t)y * nx + (nx - 1)];
+        }
+        for (int x = 0; x < nx; ++x) {
+            gy[((size_t)i * 2 + 0) * nx + x] = f0[(size_t)i * n + 0 * (size_t)nx + x];
+            gy[((size_t)i * 2 + 1) * nx + x] = f0[(size_t)i * n + (size_t)(ny - 1) * nx + x];
+        }
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* One time step.                                                           */
+/* ------------------------------------------------------------------------ */
+
+/* f_i at (x, y) where x may be -1..nx and y may be -1..ny (one at a time). */
+static double fat(const orc_cfg *c, const double *f, const double *gx,
+                  const double *gy, int i, int x, int y)
+{
+    const int nx = c->nx, ny = c->ny;
+    const size_t n = (size_t)nx * (size_t)ny;
+    if (x < 0 || x >= nx) {
+        if (c->bc_x == ORC_BC_PERIODIC) {
+            x = (x + nx) % nx;
+        } else {
+            const int side = (x < 0) ? 0 : 1;
+            return gx[((size_t)i * 2 + side) * ny + y];
+        }
+    }
+    if (y < 0 || y >= ny) {
+        if (c->bc_y == ORC_BC_PERIODIC) {
+            y = (y + ny) % ny;
+        } else {
+            const int side = (y < 0) ? 0 : 1;
+            return gy[((size_t)i * 2 + side) * nx + x];
+        }
+    }
+    return f[(size_t)i * n + (size_t)y * nx + x];
+}
+
+/* f^{n+1} from f^n.  For every cell and every velocity i (Eq. 3 with
+ * forward Euler in time and Lax-Wendroff in space):
+ *   fhat = M f                          (moments, Appendix rows)
+ *   fhat^eq from rho, jx, jy, e          (Appendix equilibria)
+ *   Omega_i = -sum_k Minv_ik s_k (fhat_k - fhat^eq_k)
+ *   Adv_i = sum_{a in x,y} [ -(c/2)(f_+ - f_-) + (c^2/2)(f_+ - 2 f + f_-) ],
+ *           c = v_ia dt/dx, f_+- the neighbours at +-1 along a
+ *   f_i^{n+1} = f_i + Adv_i + dt Omega_i
+ * gx/gy are the fixed-equilibrium ghosts (ignored on periodic axes). */
+void orc_step(const orc_cfg *c, const double *f, const double *gx, const double *gy,
+              double *fnew)
+{
+    ensure_model();
+    const int nx = c->nx, ny = c->ny;
+    const size_t n = (size_t)nx * (size_t)ny;
+    const double lam = c->dt / c->dx;
+#pragma omp parallel for schedule(static)
+    for (int y = 0; y < ny; ++y) {
+        for (int x = 0; x < nx; ++x) {
+            double fl[NV], fh[NV], fe[NV], om[NV];
+            for (int i = 0; i < NV; ++i) fl[i] = f[(size_t)i * n + (size_t)y * nx + x];
+            for (int k = 0; k < NV; ++k) {
+                double acc = 0.0;
+                for (int i = 0; i < NV; ++i) acc += g_M[k * NV + i] * fl[i];
+                fh[k] = acc;
+            }
+            orc_feq_moments(fh[0], fh[1], fh[2], fh[3], c->b, fe);
+            double delta[NV];
+            for (int k = 0; k < NV; ++k) delta[k] = c->s[k] * (fh[k] - fe[k]);
+            for (int i = 0; i < NV; ++i) {
+                double acc = 0.0;
+                for (int k = 0; k < NV; ++k) acc += g_Minv[i * NV + k] * delta[k];
+                om[i] = -acc;
+            }
+            for (int i = 0; i < NV; ++i) {
+                const double f0 = fl[i];
+                const double cx = g_vx[i] * lam, cy = g_vy[i] * lam;
+                const double fxp = fat(c, f, gx, gy, i, x + 1, y);
+                const double fxm = fat(c, f, gx, gy, i, x - 1, y);
+                const double fyp = fat(c, f, gx, gy, i, x, y + 1);
+                const double fym = fat(c, f, gx, gy, i, x, y - 1);
+                const double adv_x = -0.5 * cx * (fxp - fxm) + 0.5 * cx * cx * (fxp - 2.0 * f0 + fxm);
+                const double adv_y = -0.5 * cy * (fyp - fym) + 0.5 * cy * cy * (fyp - 2.0 * f0 + fym);
+                fnew[(size_t)i * n + (size_t)y * nx + x] = f0 + adv_x + adv_y + c->dt * om[i];
+            }
+        }
+    }
+}
+
+/* nsteps steps from f in place; work holds one more f (16*nx*ny doubles). */
+void orc_run(const orc_cfg *c, double *f, const double *gx, const double *gy,
+             long nsteps, double *work)
+{
+    const size_t bytes = sizeof(double) * NV * (size_t)c->nx * (size_t)c->ny;
+    double *a = f, *bb = work;
+    for (long s = 0; s < nsteps; ++s) {
+        orc_step(c, a, gx, gy, bb);
+        double *t = a; a = bb; bb = t;
+    }
+    if (a != f) memcpy(f, a, bytes);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Macroscopic fields and conserved totals.                                 */
+/* ------------------------------------------------------------------------ */
+
+/* rho = fhat_1, u = j/rho, T = (e - j^2/rho)/(b rho R) (Eq. 12 text). */
+void orc_macro(int nx, int ny, double b, const double *f, double *rho, double *ux,
+               double *uy, double *T)
+{
+    ensure_model();
+    const size_t n = (size_t)nx * (size_t)ny;
+    for (size_t c = 0; c < n; ++c) {
+        double m[4] = {0, 0, 0, 0};
+        for (int k = 0; k < 4; ++k)
+            for (int i = 0; i < NV; ++i) m[k] += g_M[k * NV + i] * f[(size_t)i * n + c];
+        rho[c] = m[0];
+        ux[c] = m[1] / m[0];
+        uy[c] = m[2] / m[0];
+        T[c] = (m[3] - (m[1] * m[1] + m[2] * m[2]) / m[0]) / (b * m[0]);
+    }
+}
+
+/* Pairwise (recursive halving) summation of v[0..n-1]. */
+static double pairwise_sum(const double *v, size_t n)
+{
+    if (n <= 8) {
+        double s = 0.0;
+        for (size_t i = 0; i < n; ++i) s += v[i];
+        return s;
+    }
+    const size_t h = n / 2;
+    return pairwise_sum(v, h) + pairwise_sum(v + h, n - h);
+}
+
+/* Conserved totals sum over cells of (rho, jx, jy, e) times dx*dy: the four
+ * collision invariants fhat_1..fhat_4 (Sect. "Construction ...": density,
+ * momentum and energy are conserved by the collision). */
+void orc_totals(int nx, int ny, double dx, const double *f, double out[4])
+{
+    ensure_model();
+    const size_t n = (size_t)nx * (size_t)ny;
+    double *q = (double *)malloc(sizeof(double) * n);
+    if (!q) { out[0] = out[1] = out[2] = out[3] = NAN; return; }
+    for (int k = 0; k < 4; ++k) {
+        for (size_t c = 0; c < n; ++c) {
+            double acc = 0.0;
+            for (int i = 0; i < NV; ++i) acc += g_M[k * NV + i] * f[(size_t)i * n + c];
+            q[c] = acc;
+        }
+        out[k] = pairwise_sum(q, n) * dx * dx;
+    }
+    free(q);
+}
+
+/* Thread control for the OpenMP loops (1 = serial). */
+void orc_set_threads(int nthreads)
+{
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#else
+    (void)nthreads;
+#endif
+}
+
+int orc_get_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
