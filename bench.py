@@ -1,0 +1,346 @@
+#!/usr/bin/env python3
+"""Throughput benchmark of the fused MRT-FDLB step (cell-updates/s).
+
+Workload: the 4096 x 4096 periodic Kelvin-Helmholtz double shear layer
+(gamma 5/3, Pr 0.5, CFL 0.1), FP32 state and arithmetic, TMA strip kernel.
+A benchmark step is one time step of the whole grid (moments, relaxation,
+inverse transform, Lax-Wendroff advection and Euler update of all 16.8 M
+cells).  The state (2 x 1.07 GB) is larger than L2, so no flush is needed.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Reported on one JSON line (rank 0): device-timed throughput, the end-to-end
+rate through the C ABI with host buffers (initial fields uploaded, totals read
+back every step, final fields downloaded), the roofline of the step kernel
+against the measured HBM copy bandwidth, the SM clocks seen during the timed
+region, and the FP64 CPU oracle timed on a bounded sample of the same
+workload.  With --gpus N > 1 (torchrun) every rank advances its own replica:
+the step has no exchange between GPUs (weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+BYTES_PER_CELL_F32 = 128      # 16 f_i read + 16 written, 4 bytes each
+BYTES_PER_CELL_F64 = 256
+FALLBACK_HBM_GBS = 6800.0
+KERNEL_SOURCES = ["paper_1004_5442_gb300/csrc/step_kernels.cu", "paper_1004_5442_gb300/csrc/model.cuh",
+                  "paper_1004_5442_gb300/csrc/internal.h"]
+PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "step_tma_f32_kh4096.md")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--n", type=int, default=4096, help="grid edge (default 4096)")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------
+def dist_init(n_gpus):
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    return rank, world, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def allmax(x, world):
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits", "-lms", "200",
+                 "-i", str(self.index)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.lines = []
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in getattr(self, "lines", []):
+            parts = [p.strip() for p in l.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx = float(parts[1])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": mx, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def measured_peak_hbm():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic():
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current kernel source."""
+    try:
+        text = open(PROFILE_SUMMARY).read()
+    except OSError:
+        return None
+    m = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", text)
+    hsh = re.search(r"kernel_source_hash:\s*([0-9a-f]+)", text)
+    if not m or not hsh or hsh.group(1) != kernel_source_hash():
+        return None
+    return float(m.group(1))
+
+
+# ---------------------------------------------------------------------------
+def cpu_oracle_rate(w, budget_s=12.0, max_steps=None, rows=512):
+    """The FP64 oracle on a band of the workload (all nx columns, `rows`
+    rows, periodic), stepped until budget_s of wall time has passed."""
+    import oracle
+    oracle.build()
+    threads = oracle.get_threads()
+    band = slice(0, rows)
+    g = oracle.create(w.nx, rows, w.dx, w.dt, w.b, w.s, w.rho[band], w.ux[band], w.uy[band], w.T[band],
+                      oracle.BC_PERIODIC, oracle.BC_PERIODIC)
+    work = np.zeros_like(g.f)
+    cfg = g.cfg()
+    import ctypes
+    lib = oracle.lib()
+    p = lambda a: a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    steps = 0
+    t0 = time.perf_counter()
+    while True:
+        lib.orc_run(ctypes.byref(cfg), p(g.f), p(g.gx), p(g.gy), 1, p(work))
+        steps += 1
+        el = time.perf_counter() - t0
+        if (max_steps is not None and steps >= max_steps) or (max_steps is None and el >= budget_s and steps >= 2):
+            break
+    rate = w.nx * rows * steps / el
+    return rate, threads, f"{w.nx}x{rows} band of the workload's initial state, periodic, {steps} oracle steps, {el:.1f} s"
+
+
+# ---------------------------------------------------------------------------
+def run_reference(args):
+    rank, world, local = int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), 0
+    if rank != 0:
+        return
+    from paper_1004_5442_gb300 import workloads as W
+    w = W.kelvin_helmholtz(n=args.n, nsteps=0)
+    import oracle
+    oracle.build()
+    rows = 128
+    band = slice(0, rows)
+    g = oracle.create(w.nx, rows, w.dx, w.dt, w.b, w.s, w.rho[band], w.ux[band], w.uy[band], w.T[band],
+                      oracle.BC_PERIODIC, oracle.BC_PERIODIC)
+    oracle.run(g, max(args.warmup, 0))
+    t0 = time.perf_counter()
+    oracle.run(g, args.steps)
+    el = time.perf_counter() - t0
+    rate = w.nx * rows * args.steps / el
+    sample = f"{w.nx}x{rows} band of the {args.n}^2 workload, periodic, FP64 oracle, {args.steps} steps"
+    line = {"impl": "reference", "metric": "cell_updates_per_s", "value": rate, "unit": "cell-updates/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"kelvin_helmholtz_{args.n}x{args.n}", "sample_rows": rows},
+            "cpu_baseline": {"value": rate, "unit": "cell-updates/s", "cores": oracle.get_threads(),
+                             "kind": "oracle", "sample": sample},
+            "e2e": {"value": rate, "unit": "cell-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+def run_ours(args):
+    import torch
+    rank, world, local = dist_init(args.gpus)
+    torch.cuda.set_device(local)
+    from paper_1004_5442_gb300 import build as B
+    B.build()
+    from paper_1004_5442_gb300 import binding as Bd
+    from paper_1004_5442_gb300 import workloads as W
+
+    w = W.kelvin_helmholtz(n=args.n, nsteps=0, seed=rank)
+    cells = w.nx * w.ny
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        grid = Bd.Grid.from_workload(w, precision=Bd.FP32, kernel=Bd.KERNEL_TMA, stream=stream.cuda_stream)
+    assert grid.info()["kernel"] == Bd.KERNEL_TMA
+    # warm-up
+    grid.step(max(args.warmup, 3))
+    torch.cuda.synchronize()
+    assert grid.health() == Bd.MRT_OK
+
+    # timed region: K steps, CUDA events on the grid's stream
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier(world)
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        ev0.record(stream)
+        grid.step(args.steps)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    barrier(world)
+    ms = ev0.elapsed_time(ev1)
+    ms = allmax(ms, world)
+    tot = grid.totals()
+    assert grid.health() == Bd.MRT_OK and np.all(np.isfinite(tot))
+    value = world * cells * args.steps / (ms * 1e-3)
+    per_launch_s = ms * 1e-3 / args.steps
+    peak, peak_kind = measured_peak_hbm()
+    achieved = BYTES_PER_CELL_F32 * cells / per_launch_s / 1e9
+    traffic = profiled_traffic()
+    grid.close()
+
+    line = {"metric": "cell_updates_per_s", "value": value, "unit": "cell-updates/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": f"kelvin_helmholtz_{w.nx}x{w.ny}_fp32", "nx": w.nx, "ny": w.ny,
+                       "gamma": w.gamma, "Pr": w.Pr, "cfl": 0.1, "precision": "fp32", "kernel": "tma",
+                       "l2": "state 2 x %.2f GB > 129 MB L2, no flush" % (16 * cells * 4 / 1e9),
+                       "parallelism": f"replicas{world}"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic,
+                         "peak_source": f"{peak_kind} hbm_gbs",
+                         "algorithmic_bytes_per_launch": BYTES_PER_CELL_F32 * cells,
+                         "timing": "CUDA events on the launching stream over K launches (last one also reduces totals)"},
+            "gpu_launches": args.steps + 1,
+            "clocks": clk.summary()}
+
+    # FP64 state and arithmetic (FP64 ALU bound on this part), same workload
+    if not args.no_fp64:
+        with torch.cuda.stream(stream):
+            g64 = Bd.Grid.from_workload(w, precision=Bd.FP64, kernel=Bd.KERNEL_TMA, stream=stream.cuda_stream)
+        g64.step(3)
+        k64 = max(5, args.steps // 10)
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        g64.step(k64)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        ms64 = ev0.elapsed_time(ev1)
+        assert g64.health() == Bd.MRT_OK
+        g64.close()
+        per64 = ms64 * 1e-3 / k64
+        line["fp64"] = {"value": cells / per64, "unit": "cell-updates/s", "steps": k64,
+                        "hbm_achieved_gbs": BYTES_PER_CELL_F64 * cells / per64 / 1e9,
+                        "hbm_frac": BYTES_PER_CELL_F64 * cells / per64 / 1e9 / peak, "bound": "alu (FP64)"}
+
+    # end to end through the C ABI with pinned host buffers
+    if not args.no_e2e:
+        host = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in (w.rho, w.ux, w.uy, w.T)]
+        outs = [torch.empty((w.ny, w.nx), dtype=torch.float64).pin_memory() for _ in range(4)]
+        p = Bd.make_params(w.nx, w.ny, w.dx, w.dt, w.gamma, w.s, w.bc_x, w.bc_y, Bd.FP32, 0.0, Bd.KERNEL_TMA)
+        torch.cuda.synchronize()
+        barrier(world)
+        t0 = time.perf_counter()
+        g2 = Bd.Grid(p, *(h.numpy() for h in host), stream=stream.cuda_stream)
+        for _ in range(args.steps):
+            g2.step(1)
+            g2.totals()
+        g2.macro([o.numpy() for o in outs])
+        el = time.perf_counter() - t0
+        barrier(world)
+        el = allmax(el, world)
+        g2.close()
+        h2d = 4 * 8 * cells
+        d2h = 4 * 8 * cells + 32 * args.steps
+        line["e2e"] = {"value": world * cells * args.steps / el, "unit": "cell-updates/s",
+                       "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
+                       "what": "mrt_create from pinned host rho,u,v,T; per step mrt_step(1) + "
+                               "mrt_conserved_totals (D2H); final mrt_get_macro to pinned host"}
+
+    if rank == 0 and world == 1 and not args.no_cpu:
+        rate, cores, sample = cpu_oracle_rate(w)
+        line["cpu_baseline"] = {"value": rate, "unit": "cell-updates/s", "cores": cores, "kind": "oracle",
+                                "sample": sample}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,135 @@
+/*
+ * mrtfdlb.h - C ABI of the GB300 (sm_103a) library for the two-dimensional
+ * 16-velocity (D2V16) thermal multiple-relaxation-time finite-difference
+ * lattice Boltzmann method of Chen, Xu, Zhang, Li and Succi (arXiv:1004.5442).
+ *
+ * Method, per time step dt and for every cell (Eq. 3 of the paper):
+ *   fhat   = M f                     moments; rows m_1..m_16 (Appendix)
+ *   Delta_k = s_k (fhat_k - fhat^eq_k) relaxation with a diagonal S;
+ *                                    fhat^eq from rho, j, e (Appendix), with
+ *                                    P = rho T, e = b rho T + j^2/rho, R = 1
+ *   Omega   = -M^-1 Delta            back to velocity space
+ *   f^{n+1} = f + Adv(f) + dt Omega  forward Euler in time; Adv is the
+ *                                    Lax-Wendroff operator applied along x and
+ *                                    along y (Sect. "Construction of
+ *                                    energy-conserving MRT LB model")
+ * gamma = (b+2)/b; the velocity set is the D2V16 table of the same section
+ * with eta_i = 5/2 on the four unit-speed velocities.
+ *
+ * Conventions shared by every entry point:
+ *   - Fields are row-major [ny][nx], x fastest, cell centres at
+ *     ((i+1/2)dx, (j+1/2)dx); dy = dx.
+ *   - Distribution arrays exchanged with the caller are [16][ny][nx] in the
+ *     grid's precision (float for MRT_FP32, double for MRT_FP64); the
+ *     velocity index order is (1,0),(0,1),(-1,0),(0,-1) times 1 and 6, then
+ *     (1,1),(-1,1),(-1,-1),(1,-1) times sqrt(2) and 3/sqrt(2).
+ *   - The library owns all device state of a grid; the caller owns every
+ *     array passed in or out.  Pointers flagged "on device" are CUDA device
+ *     pointers of the current device; otherwise host pointers.
+ *   - Every call returns an mrt_status; nothing aborts or throws across the
+ *     ABI.  mrt_last_error() gives a one-line reason for the last failure of
+ *     the calling thread.
+ *   - A grid is bound to the device that was current at mrt_create and to the
+ *     stream given there; calls that launch work are asynchronous on that
+ *     stream, calls that return data to the host synchronise it.  A grid
+ *     handle is not thread-safe.
+ */
+#ifndef MRTFDLB_H
+#define MRTFDLB_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum mrt_status {
+    MRT_OK = 0,
+    MRT_EINVAL = 1,     /* invalid argument (sizes, rates, states, null) */
+    MRT_ENOMEM = 2,     /* device or host allocation failed */
+    MRT_ECUDA = 3,      /* a CUDA runtime or driver call failed */
+    MRT_EUNSTABLE = 4,  /* the health flag tripped: rho or P non-positive or not finite */
+    MRT_ETIMEOUT = 5    /* a bounded device-side wait ran out */
+} mrt_status;
+
+typedef enum mrt_precision { MRT_FP32 = 0, MRT_FP64 = 1 } mrt_precision;
+
+/* Boundary treatment of one axis.  MRT_BC_FIXED_EQ: one ghost cell beyond
+ * each end holds, for the whole run, the initial f of the adjacent domain
+ * cell, i.e. f^eq = M^-1 fhat^eq of its initial state (Sect. (b): boundary
+ * nodes set to f^eq). */
+typedef enum mrt_bc { MRT_BC_PERIODIC = 0, MRT_BC_FIXED_EQ = 1 } mrt_bc;
+
+/* Step kernel selection: MRT_KERNEL_AUTO picks the TMA-staged strip kernel
+ * where it applies, MRT_KERNEL_DIRECT the one-thread-per-cell kernel that
+ * reads its stencil straight from global memory. */
+typedef enum mrt_kernel { MRT_KERNEL_AUTO = 0, MRT_KERNEL_TMA = 1, MRT_KERNEL_DIRECT = 2 } mrt_kernel;
+
+typedef struct mrt_params {
+    int nx, ny;         /* cells; each >= 3 */
+    double dx;          /* cell size (dy = dx), > 0 */
+    double dt;          /* time step, > 0 */
+    double gamma;       /* specific-heat ratio, > 1; b = 2/(gamma-1) */
+    double Pr;          /* > 0: s_8 = s_9 = Pr * s_6 (Pr = s_8/s_6 from Eqs. 12b,d);
+                           <= 0: s_8, s_9 taken from s[] as given */
+    double s[16];       /* relaxation rates s_1..s_16 in 1/time, finite, >= 0;
+                           s_1..s_4 act on conserved moments and have no effect */
+    int bc_x, bc_y;     /* mrt_bc per axis */
+    int precision;      /* mrt_precision of the stored f and of the arithmetic */
+    int kernel;         /* mrt_kernel */
+} mrt_params;
+
+typedef struct mrt_grid mrt_grid;
+
+/* Create a grid and set f = f^eq(rho, u, T) in every cell (Sect. (b):
+ * f^eq = M^-1 fhat^eq).  rho, ux, uy, T are [ny][nx] doubles, on the device
+ * if fields_on_device, else on the host.  stream is a cudaStream_t (NULL =
+ * legacy default stream).  Errors: MRT_EINVAL for nx or ny < 3, dx, dt <= 0,
+ * gamma <= 1, a negative or non-finite rate, a null pointer, and for an
+ * initial state with rho <= 0, T <= 0 or a non-finite value (checked on the
+ * device); MRT_ENOMEM; MRT_ECUDA.  Synchronises the stream once. */
+mrt_status mrt_create(const mrt_params *params, const double *rho, const double *ux,
+                      const double *uy, const double *T, int fields_on_device,
+                      void *stream, mrt_grid **out);
+
+/* Advance nsteps >= 0 time steps (Eq. 3, forward Euler + Lax-Wendroff).
+ * Asynchronous.  The conserved totals of the final state are reduced in the
+ * same pass (FP64 block partials) and kept for mrt_conserved_totals. */
+mrt_status mrt_step(mrt_grid *g, long nsteps);
+
+/* Macroscopic fields of the current state: rho = fhat_1, u = j/rho,
+ * T = (e - j^2/rho)/(b rho) (R = 1).  Outputs are [ny][nx] doubles, on the
+ * device if dst_on_device (asynchronous on the grid's stream), else on the
+ * host (synchronises).  Any output pointer may be NULL to skip it. */
+mrt_status mrt_get_macro(mrt_grid *g, double *rho, double *ux, double *uy, double *T,
+                         int dst_on_device);
+
+/* Conserved totals sum_cells (rho, j_x, j_y, e) * dx * dy of the current
+ * state, accumulated in FP64 with a fixed summation order (deterministic).
+ * out[4] is host memory; synchronises the grid's stream.  Returns
+ * MRT_EUNSTABLE if the health flag has tripped (out is still written). */
+mrt_status mrt_conserved_totals(mrt_grid *g, double out[4]);
+
+/* Copy the raw state f [16][ny][nx] (grid precision) out of / into the grid;
+ * for checkpoint/resume and tests.  Host copies synchronise. */
+mrt_status mrt_get_f(mrt_grid *g, void *f, int on_device);
+mrt_status mrt_set_f(mrt_grid *g, const void *f, int on_device);
+
+/* Synchronise the grid's stream and report the health flag: MRT_OK,
+ * MRT_EUNSTABLE (non-positive or non-finite rho or pressure met by a step),
+ * MRT_ETIMEOUT (a device-side wait ran out) or MRT_ECUDA. */
+mrt_status mrt_health(mrt_grid *g);
+
+/* Information about a grid: steps taken so far, and the element pitch and
+ * plane stride of its padded device layout (for diagnostics). */
+mrt_status mrt_info(const mrt_grid *g, long *steps, long *pitch, long *plane_stride,
+                    int *kernel_in_use);
+
+/* Release every device resource of the grid (synchronises its stream). */
+void mrt_destroy(mrt_grid *g);
+
+const char *mrt_status_str(mrt_status s);
+const char *mrt_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MRTFDLB_H */

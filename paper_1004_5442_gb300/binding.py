@@ -1,0 +1,199 @@
+"""ctypes binding of the C ABI in include/mrtfdlb.h (argument marshalling only).
+
+Every step of the method runs in the CUDA library; this module converts
+numpy arrays / torch tensors to pointers, passes torch's current CUDA stream,
+and turns error codes into exceptions.  If the compiled library is missing
+the import fails loudly: there is no CPU path.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libmrtfdlb.so")
+
+MRT_OK, MRT_EINVAL, MRT_ENOMEM, MRT_ECUDA, MRT_EUNSTABLE, MRT_ETIMEOUT = range(6)
+FP32, FP64 = 0, 1
+BC_PERIODIC, BC_FIXED_EQ = 0, 1
+KERNEL_AUTO, KERNEL_TMA, KERNEL_DIRECT = 0, 1, 2
+
+# every symbol include/mrtfdlb.h declares
+EXPORTED = ["mrt_create", "mrt_step", "mrt_get_macro", "mrt_conserved_totals", "mrt_get_f",
+            "mrt_set_f", "mrt_health", "mrt_info", "mrt_destroy", "mrt_status_str",
+            "mrt_last_error"]
+
+
+class MrtError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{_STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+_STATUS = {MRT_OK: "MRT_OK", MRT_EINVAL: "MRT_EINVAL", MRT_ENOMEM: "MRT_ENOMEM",
+           MRT_ECUDA: "MRT_ECUDA", MRT_EUNSTABLE: "MRT_EUNSTABLE", MRT_ETIMEOUT: "MRT_ETIMEOUT"}
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("dx", ctypes.c_double),
+                ("dt", ctypes.c_double), ("gamma", ctypes.c_double), ("Pr", ctypes.c_double),
+                ("s", ctypes.c_double * 16), ("bc_x", ctypes.c_int), ("bc_y", ctypes.c_int),
+                ("precision", ctypes.c_int), ("kernel", ctypes.c_int)]
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libmrtfdlb.so (built by paper_1004_5442_gb300.build)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"CUDA library not built: {path} (run paper_1004_5442_gb300.build.build())")
+    L = ctypes.CDLL(path)
+    vp, dp, ip = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.c_int
+    L.mrt_create.argtypes = [ctypes.POINTER(Params), vp, vp, vp, vp, ip, vp, ctypes.POINTER(vp)]
+    L.mrt_step.argtypes = [vp, ctypes.c_long]
+    L.mrt_get_macro.argtypes = [vp, vp, vp, vp, vp, ip]
+    L.mrt_conserved_totals.argtypes = [vp, dp]
+    L.mrt_get_f.argtypes = [vp, vp, ip]
+    L.mrt_set_f.argtypes = [vp, vp, ip]
+    L.mrt_health.argtypes = [vp]
+    L.mrt_info.argtypes = [vp, ctypes.POINTER(ctypes.c_long), ctypes.POINTER(ctypes.c_long),
+                           ctypes.POINTER(ctypes.c_long), ctypes.POINTER(ctypes.c_int)]
+    L.mrt_destroy.argtypes = [vp]
+    L.mrt_destroy.restype = None
+    L.mrt_status_str.restype = ctypes.c_char_p
+    L.mrt_status_str.argtypes = [ip]
+    L.mrt_last_error.restype = ctypes.c_char_p
+    for name in ("mrt_create", "mrt_step", "mrt_get_macro", "mrt_conserved_totals", "mrt_get_f",
+                 "mrt_set_f", "mrt_health", "mrt_info"):
+        getattr(L, name).restype = ctypes.c_int
+    _lib = L
+    return L
+
+
+def check(code: int) -> None:
+    if code != MRT_OK:
+        raise MrtError(code, load().mrt_last_error().decode())
+
+
+def _ptr(a) -> int:
+    """Address of a C-contiguous numpy array or torch tensor."""
+    if isinstance(a, np.ndarray):
+        assert a.flags["C_CONTIGUOUS"], "array must be C-contiguous"
+        return a.ctypes.data
+    assert a.is_contiguous(), "tensor must be contiguous"
+    return a.data_ptr()
+
+
+def _on_device(a) -> int:
+    return int(not isinstance(a, np.ndarray) and a.is_cuda)
+
+
+def _torch_stream():
+    import torch
+    return torch.cuda.current_stream().cuda_stream
+
+
+def make_params(nx, ny, dx, dt, gamma, s, bc_x=BC_PERIODIC, bc_y=BC_PERIODIC, precision=FP32,
+                Pr=0.0, kernel=KERNEL_AUTO) -> Params:
+    p = Params()
+    p.nx, p.ny, p.dx, p.dt, p.gamma, p.Pr = int(nx), int(ny), float(dx), float(dt), float(gamma), float(Pr)
+    for k in range(16):
+        p.s[k] = float(s[k])
+    p.bc_x, p.bc_y, p.precision, p.kernel = int(bc_x), int(bc_y), int(precision), int(kernel)
+    return p
+
+
+class Grid:
+    """A grid owned by the CUDA library (handle wrapper)."""
+
+    def __init__(self, params: Params, rho, ux, uy, T, stream=None):
+        L = load()
+        self.params = params
+        self.nx, self.ny = params.nx, params.ny
+        self.fp64 = params.precision == FP64
+        arrs = [rho, ux, uy, T]
+        dev = {_on_device(a) for a in arrs}
+        if len(dev) != 1:
+            raise ValueError("fields must all be on the host or all on the device")
+        on_dev = dev.pop()
+        if not on_dev:
+            arrs = [np.ascontiguousarray(np.broadcast_to(np.asarray(a, dtype=np.float64),
+                                                         (self.ny, self.nx))) for a in arrs]
+        if stream is None:
+            stream = _torch_stream() if on_dev else 0
+        self.stream = stream
+        h = ctypes.c_void_p()
+        check(L.mrt_create(ctypes.byref(params), *(ctypes.c_void_p(_ptr(a)) for a in arrs),
+                           on_dev, ctypes.c_void_p(stream), ctypes.byref(h)))
+        self._h = h
+
+    @classmethod
+    def from_workload(cls, w, precision=FP32, kernel=KERNEL_AUTO, stream=None):
+        p = make_params(w.nx, w.ny, w.dx, w.dt, w.gamma, w.s, w.bc_x, w.bc_y, precision, 0.0, kernel)
+        return cls(p, w.rho, w.ux, w.uy, w.T, stream=stream)
+
+    @property
+    def handle(self):
+        return self._h
+
+    def step(self, n: int = 1) -> None:
+        check(load().mrt_step(self._h, int(n)))
+
+    def macro(self, out=None):
+        """(rho, ux, uy, T) as float64 numpy arrays (or into given device tensors)."""
+        if out is None:
+            out = [np.empty((self.ny, self.nx)) for _ in range(4)]
+        check(load().mrt_get_macro(self._h, *(ctypes.c_void_p(_ptr(o)) for o in out),
+                                   _on_device(out[0])))
+        return tuple(out)
+
+    def totals(self) -> np.ndarray:
+        out = np.zeros(4)
+        check(load().mrt_conserved_totals(self._h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+        return out
+
+    def get_f(self, out=None) -> np.ndarray:
+        if out is None:
+            out = np.empty((16, self.ny, self.nx), dtype=np.float64 if self.fp64 else np.float32)
+        check(load().mrt_get_f(self._h, ctypes.c_void_p(_ptr(out)), _on_device(out)))
+        return out
+
+    def set_f(self, f) -> None:
+        if isinstance(f, np.ndarray):
+            f = np.ascontiguousarray(f, dtype=np.float64 if self.fp64 else np.float32)
+        check(load().mrt_set_f(self._h, ctypes.c_void_p(_ptr(f)), _on_device(f)))
+
+    def health(self) -> int:
+        return int(load().mrt_health(self._h))
+
+    def info(self) -> dict:
+        steps, pitch, plane = ctypes.c_long(), ctypes.c_long(), ctypes.c_long()
+        kern = ctypes.c_int()
+        check(load().mrt_info(self._h, ctypes.byref(steps), ctypes.byref(pitch), ctypes.byref(plane),
+                              ctypes.byref(kern)))
+        return {"steps": steps.value, "pitch": pitch.value, "plane": plane.value,
+                "kernel": kern.value}
+
+    def close(self) -> None:
+        if getattr(self, "_h", None) is not None and self._h.value:
+            load().mrt_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

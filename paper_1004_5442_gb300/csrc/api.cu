@@ -1,0 +1,731 @@
+// api.cu - the C ABI declared in include/mrtfdlb.h: grid creation from
+// macroscopic fields (f = M^-1 fhat^eq, Sect. (b)), the time-step driver,
+// macroscopic readout, conserved totals and raw state access.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "../../include/mrtfdlb.h"
+#include "internal.h"
+
+using namespace mrt;
+
+// ---------------------------------------------------------------------------
+// Errors
+// ---------------------------------------------------------------------------
+static thread_local char g_err[512] = "";
+
+static mrt_status fail(mrt_status s, const char* fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof g_err, fmt, ap);
+    va_end(ap);
+    return s;
+}
+
+#define CUDA_TRY(call)                                                                      \
+    do {                                                                                    \
+        cudaError_t e_ = (call);                                                            \
+        if (e_ != cudaSuccess)                                                              \
+            return fail(e_ == cudaErrorMemoryAllocation ? MRT_ENOMEM : MRT_ECUDA, "%s: %s", \
+                        #call, cudaGetErrorString(e_));                                     \
+    } while (0)
+
+// ---------------------------------------------------------------------------
+// Model blocks (host, FP64)
+// ---------------------------------------------------------------------------
+namespace {
+
+// Gauss-Jordan with partial pivoting on an n x n matrix (n <= 4).
+bool invert_small(int n, const double* A, double* Ainv) {
+    double a[4][8];
+    for (int r = 0; r < n; ++r)
+        for (int c = 0; c < 2 * n; ++c) a[r][c] = c < n ? A[r * n + c] : (c - n == r ? 1.0 : 0.0);
+    for (int c = 0; c < n; ++c) {
+        int p = c;
+        for (int r = c + 1; r < n; ++r)
+            if (std::fabs(a[r][c]) > std::fabs(a[p][c])) p = r;
+        if (a[p][c] == 0.0) return false;
+        if (p != c)
+            for (int k = 0; k < 2 * n; ++k) std::swap(a[p][k], a[c][k]);
+        const double d = a[c][c];
+        for (int k = 0; k < 2 * n; ++k) a[c][k] /= d;
+        for (int r = 0; r < n; ++r) {
+            if (r == c) continue;
+            const double m = a[r][c];
+            for (int k = 0; k < 2 * n; ++k) a[r][k] -= m * a[c][k];
+        }
+    }
+    for (int r = 0; r < n; ++r)
+        for (int c = 0; c < n; ++c) Ainv[r * n + c] = a[r][n + c];
+    return true;
+}
+
+// The five blocks of M in the group-combination basis (see model.cuh).
+bool build_blocks(double A[16], double B[16], double C1[4], double C2[4]) {
+    for (int g = 0; g < 4; ++g) {
+        A[0 * 4 + g] = 1.0;
+        A[1 * 4 + g] = kW(g);
+        A[2 * 4 + g] = kV(g);
+        A[3 * 4 + g] = kV(g) * kW(g);
+        B[0 * 4 + g] = kU(g);
+        B[1 * 4 + g] = kU(g) * kW(g);
+        B[2 * 4 + g] = kU(g) * kV(g);
+        B[3 * 4 + g] = g < 2 ? kU(g) * kV(g) : 0.0;
+    }
+    for (int g = 0; g < 2; ++g) {
+        C1[0 * 2 + g] = kV(g);
+        C1[1 * 2 + g] = kV(g) * kW(g);
+        C2[0 * 2 + g] = 0.5 * kV(2 + g);
+        C2[1 * 2 + g] = 0.5 * kV(2 + g) * kW(2 + g);
+    }
+    return true;
+}
+
+}  // namespace
+
+namespace mrt {
+
+int mrt_init_coef_build(double b, InitCoef* o) {
+    double A[16], B[16], C1[4], C2[4];
+    build_blocks(A, B, C1, C2);
+    if (!invert_small(4, A, &o->Ainv[0][0]) || !invert_small(4, B, &o->Binv[0][0]) ||
+        !invert_small(2, C1, &o->C1inv[0][0]) || !invert_small(2, C2, &o->C2inv[0][0]))
+        return -1;
+    o->b = b;
+    return 0;
+}
+
+int mrt_model_build(double dx, double dt, double b, const double s[16], Coef<double>* k) {
+    InitCoef ic;
+    if (mrt_init_coef_build(b, &ic) != 0) return -1;
+    for (int g = 0; g < 4; ++g) {
+        const double scS = -0.25;
+        const double scD = g < 2 ? -0.5 : -0.25;
+        k->kS[g][0] = scS * ic.Ainv[g][2];  // m5
+        k->kS[g][1] = scS * ic.Ainv[g][3];  // m14
+        k->kD[g][0] = scD * ic.Binv[g][1];  // m8 / m9
+        k->kD[g][1] = scD * ic.Binv[g][2];  // m10 / m11
+        k->kD[g][2] = scD * ic.Binv[g][3];  // m12 / -m13
+        const double c = kU(g) * dt / dx;
+        k->lwp[g] = 0.5 * (c * c + c);
+        k->lwq[g] = 0.5 * (c * c - c);
+    }
+    for (int g = 0; g < 2; ++g)
+        for (int j = 0; j < 2; ++j) {
+            k->kQ[g][j] = -0.25 * ic.C1inv[g][j];
+            k->kX[g][j] = -0.25 * ic.C2inv[g][j];
+        }
+    for (int kk = 0; kk < 12; ++kk) k->sig[kk] = s[4 + kk] * dt;
+    k->inv_b = 1.0 / b;
+    k->c14a = 2.0 * (b + 2.0);
+    k->c14b = 6.0 + b;
+    k->c15 = b + 4.0;
+    return 0;
+}
+
+}  // namespace mrt
+
+// ---------------------------------------------------------------------------
+// Small kernels: initialisation, ghosts, macroscopic fields, reductions
+// ---------------------------------------------------------------------------
+namespace {
+
+// f = M^-1 fhat^eq(rho, u, T) per cell, in FP64, stored as T.
+template <class T>
+__global__ void init_kernel(Layout L, InitCoef ic, const double* __restrict__ rho,
+                            const double* __restrict__ ux, const double* __restrict__ uy,
+                            const double* __restrict__ Tf, T* __restrict__ f, unsigned* flag) {
+    const long n = (long)L.nx * L.ny;
+    for (long c = blockIdx.x * (long)blockDim.x + threadIdx.x; c < n; c += (long)gridDim.x * blockDim.x) {
+        const int x = (int)(c % L.nx), y = (int)(c / L.nx);
+        const double r = rho[c], u = ux[c], v = uy[c], t = Tf[c];
+        if (!(r > 0.0) || !(t > 0.0) || !isfinite(r) || !isfinite(t) || !isfinite(u) || !isfinite(v))
+            atomicOr(flag, FLAG_UNSTABLE);
+        const double b = ic.b;
+        const double jx = r * u, jy = r * v;
+        const double P = r * t;
+        const double j2r = jx * u + jy * v;
+        const double e = b * P + j2r;
+        // Appendix equilibria (R = 1)
+        double m[16];
+        m[0] = r; m[1] = jx; m[2] = jy; m[3] = e;
+        m[4] = 2 * P + j2r;
+        m[5] = jx * u - jy * v;
+        m[6] = jx * v;
+        m[7] = (e + 2 * P) * u;
+        m[8] = (e + 2 * P) * v;
+        m[9] = (4 * P + j2r) * u;
+        m[10] = (4 * P + j2r) * v;
+        m[11] = (2 * P + m[5]) * u;
+        m[12] = (m[5] - 2 * P) * v;
+        const double u2 = u * u + v * v;
+        m[13] = 2 * (b + 2) * P * t + (6 + b) * t * j2r + j2r * u2;
+        m[14] = ((b + 4) * P + j2r) * u * v;
+        m[15] = ((b + 4) * P + j2r) * (u * u - v * v);
+        // block inverses
+        const double a1[4] = {m[0], m[3], m[4], m[13]};
+        const double ex[4] = {m[1], m[7], m[9], m[11]};
+        const double ey[4] = {m[2], m[8], m[10], -m[12]};
+        const double b1[2] = {m[5], m[15]};
+        const double b2[2] = {m[6], m[14]};
+        double out[16];
+        for (int g = 0; g < 4; ++g) {
+            double S = 0, Dx = 0, Dy = 0;
+            for (int k = 0; k < 4; ++k) {
+                S += ic.Ainv[g][k] * a1[k];
+                Dx += ic.Binv[g][k] * ex[k];
+                Dy += ic.Binv[g][k] * ey[k];
+            }
+            if (g < 2) {
+                const double Q = ic.C1inv[g][0] * b1[0] + ic.C1inv[g][1] * b1[1];
+                out[4 * g + 0] = 0.25 * S + 0.5 * Dx + 0.25 * Q;
+                out[4 * g + 2] = 0.25 * S - 0.5 * Dx + 0.25 * Q;
+                out[4 * g + 1] = 0.25 * S + 0.5 * Dy - 0.25 * Q;
+                out[4 * g + 3] = 0.25 * S - 0.5 * Dy - 0.25 * Q;
+            } else {
+                const double X = ic.C2inv[g - 2][0] * b2[0] + ic.C2inv[g - 2][1] * b2[1];
+                out[4 * g + 0] = 0.25 * (S + Dx + Dy + X);
+                out[4 * g + 1] = 0.25 * (S - Dx + Dy - X);
+                out[4 * g + 2] = 0.25 * (S - Dx - Dy + X);
+                out[4 * g + 3] = 0.25 * (S + Dx - Dy - X);
+            }
+        }
+        const long o = (long)(y + 1) * L.pitch + L.G + x;
+        for (int i = 0; i < 16; ++i) f[i * L.plane + o] = (T)out[i];
+    }
+}
+
+// Ghost columns, then ghost rows, of every plane: periodic axes copy the
+// opposite edge, fixed-equilibrium axes copy the adjacent edge.
+template <class T>
+__global__ void ghost_cols_kernel(Layout L, int per_x, T* f) {
+    const long n = 16L * L.ny;
+    for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < n; t += (long)gridDim.x * blockDim.x) {
+        const int i = (int)(t / L.ny), y = (int)(t % L.ny);
+        T* row = f + i * L.plane + (long)(y + 1) * L.pitch;
+        row[L.G - 1] = per_x ? row[L.G + L.nx - 1] : row[L.G];
+        row[L.G + L.nx] = per_x ? row[L.G] : row[L.G + L.nx - 1];
+    }
+}
+
+template <class T>
+__global__ void ghost_rows_kernel(Layout L, int per_y, T* f) {
+    const long n = 16L * L.nx;
+    for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < n; t += (long)gridDim.x * blockDim.x) {
+        const int i = (int)(t / L.nx), x = (int)(t % L.nx);
+        T* p = f + i * L.plane + L.G + x;
+        p[0] = per_y ? p[(long)L.ny * L.pitch] : p[L.pitch];
+        p[(long)(L.ny + 1) * L.pitch] = per_y ? p[L.pitch] : p[(long)L.ny * L.pitch];
+    }
+}
+
+template <class T>
+__device__ __forceinline__ void cons_moments(const T* f, const Layout& L, long o, double q[4]) {
+    double v[16];
+    for (int i = 0; i < 16; ++i) v[i] = (double)f[i * L.plane + o];
+    double S[4], Dx[4], Dy[4];
+    for (int g = 0; g < 4; ++g) {
+        const double* a = v + 4 * g;
+        S[g] = (a[0] + a[2]) + (a[1] + a[3]);
+        const double d02 = a[0] - a[2], d13 = a[1] - a[3];
+        Dx[g] = g < 2 ? d02 : d02 - d13;
+        Dy[g] = g < 2 ? d13 : d02 + d13;
+    }
+    q[0] = (S[0] + S[1]) + (S[2] + S[3]);
+    q[1] = kU(0) * Dx[0] + kU(1) * Dx[1] + kU(2) * Dx[2] + kU(3) * Dx[3];
+    q[2] = kU(0) * Dy[0] + kU(1) * Dy[1] + kU(2) * Dy[2] + kU(3) * Dy[3];
+    q[3] = kW(0) * S[0] + kW(1) * S[1] + kW(2) * S[2] + kW(3) * S[3];
+}
+
+// rho, u, T per cell (FP64); T = (e - j^2/rho)/(b rho).
+template <class T>
+__global__ void macro_kernel(Layout L, double b, const T* __restrict__ f, double* rho, double* ux,
+                             double* uy, double* Tf) {
+    const long n = (long)L.nx * L.ny;
+    for (long c = blockIdx.x * (long)blockDim.x + threadIdx.x; c < n; c += (long)gridDim.x * blockDim.x) {
+        const int x = (int)(c % L.nx), y = (int)(c / L.nx);
+        double q[4];
+        cons_moments<T>(f, L, (long)(y + 1) * L.pitch + L.G + x, q);
+        if (rho) rho[c] = q[0];
+        if (ux) ux[c] = q[1] / q[0];
+        if (uy) uy[c] = q[2] / q[0];
+        if (Tf) Tf[c] = (q[3] - (q[1] * q[1] + q[2] * q[2]) / q[0]) / (b * q[0]);
+    }
+}
+
+constexpr int RED_THREADS = 256;
+
+// FP64 block partials of (rho, jx, jy, e) over the whole state.
+template <class T>
+__global__ void __launch_bounds__(RED_THREADS) totals_partial_kernel(Layout L, const T* __restrict__ f,
+                                                                     double* partials) {
+    __shared__ double red[RED_THREADS / 32][4];
+    const long n = (long)L.nx * L.ny;
+    double acc[4] = {0, 0, 0, 0};
+    for (long c = blockIdx.x * (long)blockDim.x + threadIdx.x; c < n; c += (long)gridDim.x * blockDim.x) {
+        const int x = (int)(c % L.nx), y = (int)(c / L.nx);
+        double q[4];
+        cons_moments<T>(f, L, (long)(y + 1) * L.pitch + L.G + x, q);
+        for (int k = 0; k < 4; ++k) acc[k] += q[k];
+    }
+    for (int k = 0; k < 4; ++k)
+        for (int o = 16; o > 0; o >>= 1) acc[k] += __shfl_xor_sync(0xffffffffu, acc[k], o);
+    if ((threadIdx.x & 31) == 0)
+        for (int k = 0; k < 4; ++k) red[threadIdx.x >> 5][k] = acc[k];
+    __syncthreads();
+    if (threadIdx.x == 0)
+        for (int k = 0; k < 4; ++k) {
+            double s = 0;
+            for (int w = 0; w < RED_THREADS / 32; ++w) s += red[w][k];
+            partials[4 * blockIdx.x + k] = s;
+        }
+}
+
+// Fixed-order sum of nparts block partials, times dx*dy, into out[4].
+__global__ void __launch_bounds__(RED_THREADS) totals_final_kernel(const double* partials, int nparts,
+                                                                   double scale, double* out) {
+    __shared__ double red[RED_THREADS][4];
+    double acc[4] = {0, 0, 0, 0};
+    for (int p = threadIdx.x; p < nparts; p += RED_THREADS)
+        for (int k = 0; k < 4; ++k) acc[k] += partials[4 * p + k];
+    for (int k = 0; k < 4; ++k) red[threadIdx.x][k] = acc[k];
+    __syncthreads();
+    for (int s = RED_THREADS / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s)
+            for (int k = 0; k < 4; ++k) red[threadIdx.x][k] += red[threadIdx.x + s][k];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0)
+        for (int k = 0; k < 4; ++k) out[k] = red[0][k] * scale;
+}
+
+int grid_for(long n, int threads, int cap = 4096) {
+    long b = (n + threads - 1) / threads;
+    if (b < 1) b = 1;
+    return (int)(b > cap ? cap : b);
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Grid object
+// ---------------------------------------------------------------------------
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                  const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                  const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+struct mrt_grid {
+    mrt_params p;
+    int fp64;
+    size_t elem;
+    Layout L;
+    void* f[2] = {nullptr, nullptr};
+    int cur = 0;
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    unsigned* flag = nullptr;        // device flag word
+    double* partials = nullptr;      // 4 doubles per CTA
+    int max_parts = 0;
+    double* totals_dev = nullptr;    // 4 doubles
+    bool totals_fresh = false;
+    double* macro_tmp = nullptr;     // 4 fields, for host readout
+    long steps = 0;
+    int kernel = MRT_KERNEL_DIRECT;  // in use
+    CUtensorMap maps[2];
+    int tma_grid_x = 0, tma_grid_y = 0, rows_per_cta = 0;
+    Coef<double> kd;
+    Coef<float> kf;
+    double b;
+};
+
+static EncodeTiledFn get_encode() {
+    static EncodeTiledFn fn = nullptr;
+    if (!fn) {
+        void* ptr = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault,
+                                             &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(ptr);
+    }
+    return fn;
+}
+
+static mrt_status make_maps(mrt_grid* g) {
+    EncodeTiledFn enc = get_encode();
+    if (!enc) return fail(MRT_ECUDA, "cuTensorMapEncodeTiled entry point unavailable");
+    const int boxw = g->fp64 ? tma_boxw<double>() : tma_boxw<float>();
+    for (int b = 0; b < 2; ++b) {
+        cuuint64_t dims[3] = {(cuuint64_t)g->L.pitch, (cuuint64_t)(g->L.ny + 2), 16};
+        cuuint64_t strides[2] = {(cuuint64_t)(g->L.pitch * g->elem),
+                                 (cuuint64_t)(g->L.plane * g->elem)};
+        cuuint32_t box[3] = {(cuuint32_t)boxw, 1, 16};
+        cuuint32_t estr[3] = {1, 1, 1};
+        CUresult r = enc(&g->maps[b], g->fp64 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
+                         3, g->f[b], dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                         CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) return fail(MRT_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+    }
+    return MRT_OK;
+}
+
+static mrt_status validate(const mrt_params* p) {
+    if (!p) return fail(MRT_EINVAL, "params is NULL");
+    if (p->nx < 3 || p->ny < 3) return fail(MRT_EINVAL, "nx and ny must be >= 3 (got %d x %d)", p->nx, p->ny);
+    if ((long)p->nx * p->ny > (1L << 31)) return fail(MRT_EINVAL, "grid too large");
+    if (!(p->dx > 0) || !std::isfinite(p->dx)) return fail(MRT_EINVAL, "dx must be finite and > 0");
+    if (!(p->dt > 0) || !std::isfinite(p->dt)) return fail(MRT_EINVAL, "dt must be finite and > 0");
+    if (!(p->gamma > 1) || !std::isfinite(p->gamma)) return fail(MRT_EINVAL, "gamma must be > 1");
+    for (int k = 0; k < 16; ++k)
+        if (!(p->s[k] >= 0) || !std::isfinite(p->s[k]))
+            return fail(MRT_EINVAL, "rate s_%d must be finite and >= 0", k + 1);
+    if (!std::isfinite(p->Pr)) return fail(MRT_EINVAL, "Pr must be finite");
+    if (p->bc_x != MRT_BC_PERIODIC && p->bc_x != MRT_BC_FIXED_EQ) return fail(MRT_EINVAL, "bad bc_x");
+    if (p->bc_y != MRT_BC_PERIODIC && p->bc_y != MRT_BC_FIXED_EQ) return fail(MRT_EINVAL, "bad bc_y");
+    if (p->precision != MRT_FP32 && p->precision != MRT_FP64) return fail(MRT_EINVAL, "bad precision");
+    if (p->kernel < MRT_KERNEL_AUTO || p->kernel > MRT_KERNEL_DIRECT) return fail(MRT_EINVAL, "bad kernel");
+    return MRT_OK;
+}
+
+static void release(mrt_grid* g) {
+    if (!g) return;
+    int prev = -1;
+    cudaGetDevice(&prev);
+    cudaSetDevice(g->device);
+    if (g->stream) cudaStreamSynchronize(g->stream);
+    cudaFree(g->f[0]);
+    cudaFree(g->f[1]);
+    cudaFree(g->flag);
+    cudaFree(g->partials);
+    cudaFree(g->totals_dev);
+    cudaFree(g->macro_tmp);
+    if (prev >= 0) cudaSetDevice(prev);
+    delete g;
+}
+
+template <class T>
+static void launch_ghosts(mrt_grid* g, int buf) {
+    T* f = static_cast<T*>(g->f[buf]);
+    ghost_cols_kernel<T><<<grid_for(16L * g->L.ny, 256), 256, 0, g->stream>>>(g->L, g->p.bc_x == MRT_BC_PERIODIC, f);
+    ghost_rows_kernel<T><<<grid_for(16L * g->L.nx, 256), 256, 0, g->stream>>>(g->L, g->p.bc_y == MRT_BC_PERIODIC, f);
+}
+
+template <class T>
+static mrt_status do_init(mrt_grid* g, const double* rho, const double* ux, const double* uy,
+                          const double* T_) {
+    InitCoef ic;
+    if (mrt_init_coef_build(g->b, &ic) != 0) return fail(MRT_ECUDA, "model blocks singular");
+    const long n = (long)g->L.nx * g->L.ny;
+    init_kernel<T><<<grid_for(n, 256), 256, 0, g->stream>>>(g->L, ic, rho, ux, uy, T_,
+                                                            static_cast<T*>(g->f[0]), g->flag);
+    CUDA_TRY(cudaGetLastError());
+    launch_ghosts<T>(g, 0);
+    CUDA_TRY(cudaGetLastError());
+    // both buffers carry the same ghosts (fixed ones are never rewritten)
+    CUDA_TRY(cudaMemcpyAsync(g->f[1], g->f[0], 16 * g->L.plane * g->elem, cudaMemcpyDeviceToDevice, g->stream));
+    return MRT_OK;
+}
+
+extern "C" mrt_status mrt_create(const mrt_params* params, const double* rho, const double* ux,
+                                 const double* uy, const double* T, int fields_on_device,
+                                 void* stream, mrt_grid** out) {
+    mrt_status st = validate(params);
+    if (st != MRT_OK) return st;
+    if (!out || !rho || !ux || !uy || !T) return fail(MRT_EINVAL, "null pointer argument");
+    *out = nullptr;
+    const long n = (long)params->nx * params->ny;
+    mrt_grid* g = new (std::nothrow) mrt_grid();
+    if (!g) return fail(MRT_ENOMEM, "host allocation failed");
+    g->p = *params;
+    if (g->p.Pr > 0) g->p.s[7] = g->p.s[8] = g->p.Pr * g->p.s[5];
+    g->fp64 = params->precision == MRT_FP64;
+    g->elem = g->fp64 ? 8 : 4;
+    g->b = 2.0 / (params->gamma - 1.0);
+    g->stream = static_cast<cudaStream_t>(stream);
+    cudaGetDevice(&g->device);
+    const int G = (int)(128 / g->elem);
+    const long per128 = 128 / (long)g->elem;
+    g->L.nx = params->nx;
+    g->L.ny = params->ny;
+    g->L.G = G;
+    // room for the right ghost column, and for a whole TMA box even when the
+    // grid is narrower than one strip
+    const long need = std::max<long>(G + params->nx + 1, G + TMA_W + 16 / (long)g->elem);
+    g->L.pitch = (need + per128 - 1) / per128 * per128;
+    g->L.plane = g->L.pitch * (params->ny + 2);
+    if (mrt_model_build(params->dx, params->dt, g->b, g->p.s, &g->kd) != 0) {
+        delete g;
+        return fail(MRT_ECUDA, "model blocks singular");
+    }
+    coef_cast<float, double>(g->kd, &g->kf);
+
+    auto bail = [&](mrt_status s) { release(g); return s; };
+    const size_t bytes = 16 * (size_t)g->L.plane * g->elem;
+    cudaError_t e;
+    if ((e = cudaMalloc(&g->f[0], bytes)) != cudaSuccess || (e = cudaMalloc(&g->f[1], bytes)) != cudaSuccess)
+        return bail(fail(e == cudaErrorMemoryAllocation ? MRT_ENOMEM : MRT_ECUDA,
+                         "cudaMalloc of 2 x %zu bytes failed: %s", bytes, cudaGetErrorString(e)));
+    if ((e = cudaMemsetAsync(g->f[0], 0, bytes, g->stream)) != cudaSuccess ||
+        (e = cudaMemsetAsync(g->f[1], 0, bytes, g->stream)) != cudaSuccess)
+        return bail(fail(MRT_ECUDA, "memset: %s", cudaGetErrorString(e)));
+    if ((e = cudaMalloc(&g->flag, sizeof(unsigned))) != cudaSuccess ||
+        (e = cudaMemsetAsync(g->flag, 0, sizeof(unsigned), g->stream)) != cudaSuccess ||
+        (e = cudaMalloc(&g->totals_dev, 4 * sizeof(double))) != cudaSuccess)
+        return bail(fail(MRT_ENOMEM, "cudaMalloc: %s", cudaGetErrorString(e)));
+
+    // kernel choice and launch geometry
+    int kernel = params->kernel == MRT_KERNEL_AUTO ? MRT_KERNEL_TMA : params->kernel;
+    int parts = 0;
+    if (kernel == MRT_KERNEL_TMA) {
+        int occ = 0, sms = 0;
+        e = g->fp64 ? tma_occupancy<double>(&occ) : tma_occupancy<float>(&occ);
+        if (e != cudaSuccess) return bail(fail(MRT_ECUDA, "occupancy query: %s", cudaGetErrorString(e)));
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, g->device);
+        if (occ < 1) occ = 1;
+        const int strips = (params->nx + TMA_W - 1) / TMA_W;
+        const long resident = (long)sms * occ;
+        long chunks = (resident + strips - 1) / strips;
+        if (chunks < 1) chunks = 1;
+        int rows = (int)((params->ny + chunks - 1) / chunks);
+        if (rows < 1) rows = 1;
+        g->rows_per_cta = rows;
+        g->tma_grid_x = strips;
+        g->tma_grid_y = (params->ny + rows - 1) / rows;
+        parts = g->tma_grid_x * g->tma_grid_y;
+    } else {
+        dim3 gr, bl;
+        if (g->fp64) direct_grid<double>(g->L, &gr, &bl); else direct_grid<float>(g->L, &gr, &bl);
+        parts = (int)(gr.x * gr.y);
+    }
+    g->kernel = kernel;
+    const int red_parts = grid_for((long)params->nx * params->ny, RED_THREADS, 1024);
+    g->max_parts = parts > red_parts ? parts : red_parts;
+    if ((e = cudaMalloc(&g->partials, 4 * sizeof(double) * (size_t)g->max_parts)) != cudaSuccess)
+        return bail(fail(MRT_ENOMEM, "cudaMalloc partials: %s", cudaGetErrorString(e)));
+
+    // initial fields on the device
+    const double* d_in[4] = {rho, ux, uy, T};
+    double* staged = nullptr;
+    if (!fields_on_device) {
+        if ((e = cudaMalloc(&staged, 4 * sizeof(double) * (size_t)n)) != cudaSuccess)
+            return bail(fail(MRT_ENOMEM, "cudaMalloc staging: %s", cudaGetErrorString(e)));
+        for (int q = 0; q < 4; ++q) {
+            const double* src = q == 0 ? rho : q == 1 ? ux : q == 2 ? uy : T;
+            if ((e = cudaMemcpyAsync(staged + q * n, src, n * sizeof(double), cudaMemcpyHostToDevice,
+                                     g->stream)) != cudaSuccess) {
+                cudaFree(staged);
+                return bail(fail(MRT_ECUDA, "upload: %s", cudaGetErrorString(e)));
+            }
+            d_in[q] = staged + q * n;
+        }
+    }
+    st = g->fp64 ? do_init<double>(g, d_in[0], d_in[1], d_in[2], d_in[3])
+                 : do_init<float>(g, d_in[0], d_in[1], d_in[2], d_in[3]);
+    if (staged) {
+        cudaStreamSynchronize(g->stream);
+        cudaFree(staged);
+    }
+    if (st != MRT_OK) return bail(st);
+    if (kernel == MRT_KERNEL_TMA) {
+        st = make_maps(g);
+        if (st != MRT_OK) return bail(st);
+    }
+    {
+        // the initial state is validated by the init kernel through the flag
+        unsigned h = 0;
+        if ((e = cudaMemcpyAsync(&h, g->flag, sizeof h, cudaMemcpyDeviceToHost, g->stream)) != cudaSuccess ||
+            (e = cudaStreamSynchronize(g->stream)) != cudaSuccess)
+            return bail(fail(MRT_ECUDA, "init: %s", cudaGetErrorString(e)));
+        if (h & FLAG_UNSTABLE) return bail(fail(MRT_EINVAL, "initial state: rho and T must be finite and > 0"));
+    }
+    *out = g;
+    return MRT_OK;
+}
+
+template <class T>
+static mrt_status step_impl(mrt_grid* g, long nsteps) {
+    StepArgs<T> a;
+    a.L = g->L;
+    a.per_x = g->p.bc_x == MRT_BC_PERIODIC;
+    a.per_y = g->p.bc_y == MRT_BC_PERIODIC;
+    a.rows_per_cta = g->rows_per_cta;
+    a.partials = g->partials;
+    a.flag = g->flag;
+    if constexpr (sizeof(T) == 8) a.k = g->kd; else a.k = g->kf;
+    for (long s = 0; s < nsteps; ++s) {
+        const bool totals = s == nsteps - 1;
+        a.in = static_cast<const T*>(g->f[g->cur]);
+        a.out = static_cast<T*>(g->f[g->cur ^ 1]);
+        cudaError_t e;
+        int parts;
+        if (g->kernel == MRT_KERNEL_TMA) {
+            e = launch_step_tma<T>(&g->maps[g->cur], a, g->tma_grid_x, g->tma_grid_y, totals, g->stream);
+            parts = g->tma_grid_x * g->tma_grid_y;
+        } else {
+            e = launch_step_direct<T>(a, totals, g->stream);
+            dim3 gr, bl;
+            direct_grid<T>(g->L, &gr, &bl);
+            parts = (int)(gr.x * gr.y);
+        }
+        if (e != cudaSuccess) return fail(MRT_ECUDA, "step launch: %s", cudaGetErrorString(e));
+        if (totals) {
+            totals_final_kernel<<<1, RED_THREADS, 0, g->stream>>>(g->partials, parts, g->p.dx * g->p.dx,
+                                                                 g->totals_dev);
+            CUDA_TRY(cudaGetLastError());
+        }
+        g->cur ^= 1;
+        g->steps++;
+    }
+    if (nsteps > 0) g->totals_fresh = true;
+    return MRT_OK;
+}
+
+extern "C" mrt_status mrt_step(mrt_grid* g, long nsteps) {
+    if (!g) return fail(MRT_EINVAL, "grid is NULL");
+    if (nsteps < 0) return fail(MRT_EINVAL, "nsteps must be >= 0");
+    if (nsteps == 0) return MRT_OK;
+    return g->fp64 ? step_impl<double>(g, nsteps) : step_impl<float>(g, nsteps);
+}
+
+template <class T>
+static mrt_status macro_impl(mrt_grid* g, double* rho, double* ux, double* uy, double* Tf) {
+    const long n = (long)g->L.nx * g->L.ny;
+    macro_kernel<T><<<grid_for(n, 256), 256, 0, g->stream>>>(g->L, g->b, static_cast<const T*>(g->f[g->cur]),
+                                                             rho, ux, uy, Tf);
+    CUDA_TRY(cudaGetLastError());
+    return MRT_OK;
+}
+
+extern "C" mrt_status mrt_get_macro(mrt_grid* g, double* rho, double* ux, double* uy, double* T,
+                                    int dst_on_device) {
+    if (!g) return fail(MRT_EINVAL, "grid is NULL");
+    const long n = (long)g->L.nx * g->L.ny;
+    if (dst_on_device) return g->fp64 ? macro_impl<double>(g, rho, ux, uy, T) : macro_impl<float>(g, rho, ux, uy, T);
+    if (!g->macro_tmp) CUDA_TRY(cudaMalloc(&g->macro_tmp, 4 * sizeof(double) * (size_t)n));
+    double* d[4];
+    double* h[4] = {rho, ux, uy, T};
+    for (int q = 0; q < 4; ++q) d[q] = h[q] ? g->macro_tmp + q * n : nullptr;
+    mrt_status st = g->fp64 ? macro_impl<double>(g, d[0], d[1], d[2], d[3]) : macro_impl<float>(g, d[0], d[1], d[2], d[3]);
+    if (st != MRT_OK) return st;
+    for (int q = 0; q < 4; ++q)
+        if (h[q]) CUDA_TRY(cudaMemcpyAsync(h[q], d[q], n * sizeof(double), cudaMemcpyDeviceToHost, g->stream));
+    CUDA_TRY(cudaStreamSynchronize(g->stream));
+    return MRT_OK;
+}
+
+template <class T>
+static mrt_status totals_impl(mrt_grid* g) {
+    const long n = (long)g->L.nx * g->L.ny;
+    const int blocks = grid_for(n, RED_THREADS, 1024);
+    totals_partial_kernel<T><<<blocks, RED_THREADS, 0, g->stream>>>(g->L, static_cast<const T*>(g->f[g->cur]),
+                                                                     g->partials);
+    CUDA_TRY(cudaGetLastError());
+    totals_final_kernel<<<1, RED_THREADS, 0, g->stream>>>(g->partials, blocks, g->p.dx * g->p.dx, g->totals_dev);
+    CUDA_TRY(cudaGetLastError());
+    g->totals_fresh = true;
+    return MRT_OK;
+}
+
+extern "C" mrt_status mrt_conserved_totals(mrt_grid* g, double out[4]) {
+    if (!g || !out) return fail(MRT_EINVAL, "null argument");
+    if (!g->totals_fresh) {
+        mrt_status st = g->fp64 ? totals_impl<double>(g) : totals_impl<float>(g);
+        if (st != MRT_OK) return st;
+    }
+    unsigned flag = 0;
+    CUDA_TRY(cudaMemcpyAsync(out, g->totals_dev, 4 * sizeof(double), cudaMemcpyDeviceToHost, g->stream));
+    CUDA_TRY(cudaMemcpyAsync(&flag, g->flag, sizeof flag, cudaMemcpyDeviceToHost, g->stream));
+    CUDA_TRY(cudaStreamSynchronize(g->stream));
+    if (flag & FLAG_TIMEOUT) return fail(MRT_ETIMEOUT, "a device-side wait ran out");
+    if (flag & FLAG_UNSTABLE) return fail(MRT_EUNSTABLE, "non-positive or non-finite rho or pressure");
+    return MRT_OK;
+}
+
+static mrt_status copy_f(mrt_grid* g, void* f, int on_device, bool to_grid) {
+    const size_t rowb = (size_t)g->L.nx * g->elem;
+    const size_t dpitch = (size_t)g->L.pitch * g->elem;
+    const cudaMemcpyKind kind = to_grid ? (on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice)
+                                        : (on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost);
+    char* dev = static_cast<char*>(g->f[g->cur]);
+    char* usr = static_cast<char*>(f);
+    for (int i = 0; i < 16; ++i) {
+        char* dplane = dev + ((size_t)i * g->L.plane + g->L.pitch + g->L.G) * g->elem;
+        char* uplane = usr + (size_t)i * g->L.nx * g->L.ny * g->elem;
+        cudaError_t e = to_grid
+            ? cudaMemcpy2DAsync(dplane, dpitch, uplane, rowb, rowb, g->L.ny, kind, g->stream)
+            : cudaMemcpy2DAsync(uplane, rowb, dplane, dpitch, rowb, g->L.ny, kind, g->stream);
+        if (e != cudaSuccess) return fail(MRT_ECUDA, "state copy: %s", cudaGetErrorString(e));
+    }
+    if (!on_device) CUDA_TRY(cudaStreamSynchronize(g->stream));
+    return MRT_OK;
+}
+
+extern "C" mrt_status mrt_get_f(mrt_grid* g, void* f, int on_device) {
+    if (!g || !f) return fail(MRT_EINVAL, "null argument");
+    return copy_f(g, f, on_device, false);
+}
+
+extern "C" mrt_status mrt_set_f(mrt_grid* g, const void* f, int on_device) {
+    if (!g || !f) return fail(MRT_EINVAL, "null argument");
+    mrt_status st = copy_f(g, const_cast<void*>(f), on_device, true);
+    if (st != MRT_OK) return st;
+    // periodic ghosts follow the new state; fixed-equilibrium ghosts keep the
+    // boundary values set at creation
+    const int per_x = g->p.bc_x == MRT_BC_PERIODIC, per_y = g->p.bc_y == MRT_BC_PERIODIC;
+    if (per_x || per_y) {
+        if (g->fp64) {
+            double* fd = static_cast<double*>(g->f[g->cur]);
+            if (per_x) ghost_cols_kernel<double><<<grid_for(16L * g->L.ny, 256), 256, 0, g->stream>>>(g->L, 1, fd);
+            if (per_y) ghost_rows_kernel<double><<<grid_for(16L * g->L.nx, 256), 256, 0, g->stream>>>(g->L, 1, fd);
+        } else {
+            float* ff = static_cast<float*>(g->f[g->cur]);
+            if (per_x) ghost_cols_kernel<float><<<grid_for(16L * g->L.ny, 256), 256, 0, g->stream>>>(g->L, 1, ff);
+            if (per_y) ghost_rows_kernel<float><<<grid_for(16L * g->L.nx, 256), 256, 0, g->stream>>>(g->L, 1, ff);
+        }
+        CUDA_TRY(cudaGetLastError());
+    }
+    g->totals_fresh = false;
+    return MRT_OK;
+}
+
+extern "C" mrt_status mrt_health(mrt_grid* g) {
+    if (!g) return fail(MRT_EINVAL, "grid is NULL");
+    unsigned flag = 0;
+    CUDA_TRY(cudaMemcpyAsync(&flag, g->flag, sizeof flag, cudaMemcpyDeviceToHost, g->stream));
+    CUDA_TRY(cudaStreamSynchronize(g->stream));
+    if (flag & FLAG_TIMEOUT) return fail(MRT_ETIMEOUT, "a device-side wait ran out");
+    if (flag & FLAG_UNSTABLE) return fail(MRT_EUNSTABLE, "non-positive or non-finite rho or pressure");
+    return MRT_OK;
+}
+
+extern "C" mrt_status mrt_info(const mrt_grid* g, long* steps, long* pitch, long* plane_stride,
+                               int* kernel_in_use) {
+    if (!g) return fail(MRT_EINVAL, "grid is NULL");
+    if (steps) *steps = g->steps;
+    if (pitch) *pitch = g->L.pitch;
+    if (plane_stride) *plane_stride = g->L.plane;
+    if (kernel_in_use) *kernel_in_use = g->kernel;
+    return MRT_OK;
+}
+
+extern "C" void mrt_destroy(mrt_grid* g) { release(g); }
+
+extern "C" const char* mrt_status_str(mrt_status s) {
+    switch (s) {
+        case MRT_OK: return "MRT_OK";
+        case MRT_EINVAL: return "MRT_EINVAL";
+        case MRT_ENOMEM: return "MRT_ENOMEM";
+        case MRT_ECUDA: return "MRT_ECUDA";
+        case MRT_EUNSTABLE: return "MRT_EUNSTABLE";
+        case MRT_ETIMEOUT: return "MRT_ETIMEOUT";
+    }
+    return "MRT_UNKNOWN";
+}
+
+extern "C" const char* mrt_last_error(void) { return g_err; }

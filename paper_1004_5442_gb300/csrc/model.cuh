@@ -1,0 +1,244 @@
+// model.cuh - the D2V16 MRT-FDLB model as the GPU kernels apply it.
+//
+// The 16 velocities form four groups of four (Sect. "Construction of
+// energy-conserving MRT LB model", velocity table):
+//   g = 0: speed 1 on the axes, eta^2 = 25/4;  g = 1: speed 6 on the axes;
+//   g = 2: sqrt(2)(+-1,+-1);                    g = 3: (3/sqrt(2))(+-1,+-1).
+// Members of an axis group: +x, +y, -x, -y; of a diagonal group:
+// (+,+), (-,+), (-,-), (+,-).  Per group the four values are combined into
+//   S = f0+f1+f2+f3, Dx, Dy, and Q (axis: (f0+f2)-(f1+f3)) or
+//   X (diagonal: (f0+f2)-(f1+f3)),
+// and every Appendix moment row m_k is a combination of one kind of these
+// over the groups (the rows split by their symmetry under the square's
+// rotations and reflections):
+//   (m1, m4, m5, m14)  from S_0..S_3      4x4 block A
+//   (m2, m8, m10, m12) from Dx_0..Dx_3    4x4 block B
+//   (m3, m9, m11, m13) from Dy_0..Dy_3    B with the m13 row negated
+//   (m6, m16)          from Q_0, Q_1      2x2 block C1
+//   (m7, m15)          from X_2, X_3      2x2 block C2
+// so M f costs 32 adds plus 56 multiply-adds instead of 256, and M^-1 is
+// the inverse of these blocks followed by the inverse butterflies.  The
+// blocks are built and inverted on the host in FP64 (mrt_model_build) and
+// passed to the kernels as FP32 or FP64 constants.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace mrt {
+
+constexpr int NV = 16;
+
+// Per-group constants: component magnitude u (speed on an axis, or the
+// common |v_x| = |v_y| of a diagonal), V = |v|^2 and W = |v|^2 + eta^2.
+__host__ __device__ constexpr double kU(int g) {
+    return g == 0 ? 1.0 : g == 1 ? 6.0 : g == 2 ? 1.4142135623730951 : 2.1213203435596424;
+}
+__host__ __device__ constexpr double kV(int g) { return g == 0 ? 1.0 : g == 1 ? 36.0 : g == 2 ? 4.0 : 9.0; }
+__host__ __device__ constexpr double kW(int g) { return g == 0 ? 7.25 : g == 1 ? 36.0 : g == 2 ? 4.0 : 9.0; }
+
+// Everything a step kernel needs besides the state.
+template <class T>
+struct Coef {
+    // Collision increment dt*Omega in the combined basis, already scaled by
+    // the inverse butterflies' 1/4 or 1/2 and by -1:
+    T kS[4][2];   // S_g    <- (Delta_5, Delta_14)
+    T kD[4][3];   // Dx_g   <- (Delta_8, Delta_10, Delta_12); Dy_g <- (Delta_9, Delta_11, -Delta_13)
+    T kQ[2][2];   // Q_g    <- (Delta_6, Delta_16), g = 0, 1
+    T kX[2][2];   // X_g    <- (Delta_7, Delta_15), g = 2, 3
+    T sig[12];    // sigma_k = s_k dt for k = 5..16
+    // Lax-Wendroff weights per group with c = u_g dt/dx:
+    // p = (c^2 + c)/2 on the upwind neighbour, q = (c^2 - c)/2 on the other.
+    T lwp[4], lwq[4];
+    T inv_b;      // 1/b
+    T c14a;       // 2 (b + 2)
+    T c14b;       // 6 + b
+    T c15;        // b + 4
+};
+
+// Host-side, FP64: builds the blocks from (u, V, W), inverts them and fills
+// the FP64 constants; returns 0 on success.  dx, dt, b and s[16] as given.
+int mrt_model_build(double dx, double dt, double b, const double s[16], Coef<double>* out);
+
+// Full (unscaled) block inverses, used by the initialisation kernel to map
+// equilibrium moments to f.  Ainv[g][k]: k over (m1, m4, m5, m14);
+// Binv[g][k]: k over (m2, m8, m10, m12); C1inv / C2inv over (m6, m16) / (m7, m15).
+struct InitCoef {
+    double Ainv[4][4];
+    double Binv[4][4];
+    double C1inv[2][2];
+    double C2inv[2][2];
+    double b;
+};
+int mrt_init_coef_build(double b, InitCoef* out);
+
+template <class Dst, class Src>
+inline void coef_cast(const Coef<Src>& a, Coef<Dst>* o) {
+    for (int g = 0; g < 4; ++g) {
+        for (int j = 0; j < 2; ++j) o->kS[g][j] = (Dst)a.kS[g][j];
+        for (int j = 0; j < 3; ++j) o->kD[g][j] = (Dst)a.kD[g][j];
+        o->lwp[g] = (Dst)a.lwp[g];
+        o->lwq[g] = (Dst)a.lwq[g];
+    }
+    for (int g = 0; g < 2; ++g)
+        for (int j = 0; j < 2; ++j) {
+            o->kQ[g][j] = (Dst)a.kQ[g][j];
+            o->kX[g][j] = (Dst)a.kX[g][j];
+        }
+    for (int k = 0; k < 12; ++k) o->sig[k] = (Dst)a.sig[k];
+    o->inv_b = (Dst)a.inv_b;
+    o->c14a = (Dst)a.c14a;
+    o->c14b = (Dst)a.c14b;
+    o->c15 = (Dst)a.c15;
+}
+
+#ifdef __CUDACC__
+
+// Stencil positions handed to a fetch functor.
+enum Pos { C = 0, XM = 1, XP = 2, YM = 3, YP = 4 };
+
+// Conserved moments (rho, jx, jy, e) of a 16-vector, from the group sums.
+template <class T>
+__device__ __forceinline__ void conserved_moments(const T f[NV], T& rho, T& jx, T& jy, T& e) {
+    T S[4], Dx[4], Dy[4];
+#pragma unroll
+    for (int g = 0; g < 4; ++g) {
+        const T* q = f + 4 * g;
+        const T d02 = q[0] - q[2], d13 = q[1] - q[3];
+        S[g] = (q[0] + q[2]) + (q[1] + q[3]);
+        if (g < 2) { Dx[g] = d02; Dy[g] = d13; }
+        else { Dx[g] = d02 - d13; Dy[g] = d02 + d13; }
+    }
+    rho = (S[0] + S[1]) + (S[2] + S[3]);
+    jx = (T)kU(0) * Dx[0] + (T)kU(1) * Dx[1] + (T)kU(2) * Dx[2] + (T)kU(3) * Dx[3];
+    jy = (T)kU(0) * Dy[0] + (T)kU(1) * Dy[1] + (T)kU(2) * Dy[2] + (T)kU(3) * Dy[3];
+    e = (T)kW(0) * S[0] + (T)kW(1) * S[1] + (T)kW(2) * S[2] + (T)kW(3) * S[3];
+}
+
+// One cell of one time step (Eq. 3, forward Euler + Lax-Wendroff):
+// reads the stencil through F(i, pos), writes f^{n+1} to out and returns
+// the cell's input rho and P for the health check.
+template <class T, class Fetch>
+__device__ __forceinline__ void cell_update(const Fetch& F, const Coef<T>& k, T out[NV],
+                                            T& rho_in, T& P_in) {
+    T f[NV];
+#pragma unroll
+    for (int i = 0; i < NV; ++i) f[i] = F(i, C);
+
+    // ---- forward transform: butterflies, then the five blocks ----------
+    T S[4], Dx[4], Dy[4], QX[4];
+#pragma unroll
+    for (int g = 0; g < 4; ++g) {
+        const T* q = f + 4 * g;
+        const T s02 = q[0] + q[2], s13 = q[1] + q[3];
+        const T d02 = q[0] - q[2], d13 = q[1] - q[3];
+        S[g] = s02 + s13;
+        QX[g] = s02 - s13;
+        if (g < 2) { Dx[g] = d02; Dy[g] = d13; }
+        else { Dx[g] = d02 - d13; Dy[g] = d02 + d13; }
+    }
+    const T U0 = (T)kU(0), U1 = (T)kU(1), U2 = (T)kU(2), U3 = (T)kU(3);
+    const T m1 = (S[0] + S[1]) + (S[2] + S[3]);
+    const T m4 = (T)kW(0) * S[0] + (T)kW(1) * S[1] + (T)kW(2) * S[2] + (T)kW(3) * S[3];
+    const T m5 = (T)kV(0) * S[0] + (T)kV(1) * S[1] + (T)kV(2) * S[2] + (T)kV(3) * S[3];
+    const T m14 = (T)(kV(0) * kW(0)) * S[0] + (T)(kV(1) * kW(1)) * S[1]
+                + (T)(kV(2) * kW(2)) * S[2] + (T)(kV(3) * kW(3)) * S[3];
+    const T m2 = U0 * Dx[0] + U1 * Dx[1] + U2 * Dx[2] + U3 * Dx[3];
+    const T m8 = (T)(kU(0) * kW(0)) * Dx[0] + (T)(kU(1) * kW(1)) * Dx[1]
+               + (T)(kU(2) * kW(2)) * Dx[2] + (T)(kU(3) * kW(3)) * Dx[3];
+    const T m10 = (T)(kU(0) * kV(0)) * Dx[0] + (T)(kU(1) * kV(1)) * Dx[1]
+                + (T)(kU(2) * kV(2)) * Dx[2] + (T)(kU(3) * kV(3)) * Dx[3];
+    const T m12 = (T)(kU(0) * kV(0)) * Dx[0] + (T)(kU(1) * kV(1)) * Dx[1];
+    const T m3 = U0 * Dy[0] + U1 * Dy[1] + U2 * Dy[2] + U3 * Dy[3];
+    const T m9 = (T)(kU(0) * kW(0)) * Dy[0] + (T)(kU(1) * kW(1)) * Dy[1]
+               + (T)(kU(2) * kW(2)) * Dy[2] + (T)(kU(3) * kW(3)) * Dy[3];
+    const T m11 = (T)(kU(0) * kV(0)) * Dy[0] + (T)(kU(1) * kV(1)) * Dy[1]
+                + (T)(kU(2) * kV(2)) * Dy[2] + (T)(kU(3) * kV(3)) * Dy[3];
+    const T m13 = -((T)(kU(0) * kV(0)) * Dy[0] + (T)(kU(1) * kV(1)) * Dy[1]);
+    const T m6 = (T)kV(0) * QX[0] + (T)kV(1) * QX[1];
+    const T m16 = (T)(kV(0) * kW(0)) * QX[0] + (T)(kV(1) * kW(1)) * QX[1];
+    const T m7 = (T)(0.5 * kV(2)) * QX[2] + (T)(0.5 * kV(3)) * QX[3];
+    const T m15 = (T)(0.5 * kV(2) * kW(2)) * QX[2] + (T)(0.5 * kV(3) * kW(3)) * QX[3];
+
+    // ---- equilibrium moments (Appendix), P = (e - j^2/rho)/b, R = 1 ------
+    const T rho = m1, jx = m2, jy = m3, e = m4;
+    const T rinv = (T)1 / rho;
+    const T ux = jx * rinv, uy = jy * rinv;
+    const T kx = jx * ux, ky = jy * uy;
+    const T j2r = kx + ky;                       // j^2 / rho
+    const T P = (e - j2r) * k.inv_b;
+    const T Tt = P * rinv;
+    const T twoP = P + P;
+    const T q5 = twoP + j2r;
+    const T q6 = kx - ky;                        // (jx^2 - jy^2)/rho
+    const T q7 = jx * uy;
+    const T e2P = e + twoP;
+    const T q8 = e2P * ux, q9 = e2P * uy;
+    const T h10 = twoP + q5;                     // 4P + j^2/rho
+    const T q10 = h10 * ux, q11 = h10 * uy;
+    const T q12 = (twoP + q6) * ux;
+    const T q13 = (q6 - twoP) * uy;
+    const T u2 = ux * ux + uy * uy;
+    const T q14 = k.c14a * P * Tt + k.c14b * Tt * j2r + j2r * u2;
+    const T g15 = k.c15 * P + j2r;
+    const T q15 = g15 * ux * uy;
+    const T q16 = g15 * (ux * ux - uy * uy);
+    rho_in = rho;
+    P_in = P;
+
+    // ---- relaxation Delta_k = sigma_k (m_k - m^eq_k), k = 5..16 ---------
+    const T d5 = k.sig[0] * (m5 - q5), d6 = k.sig[1] * (m6 - q6), d7 = k.sig[2] * (m7 - q7);
+    const T d8 = k.sig[3] * (m8 - q8), d9 = k.sig[4] * (m9 - q9);
+    const T d10 = k.sig[5] * (m10 - q10), d11 = k.sig[6] * (m11 - q11);
+    const T d12 = k.sig[7] * (m12 - q12), d13 = k.sig[8] * (m13 - q13);
+    const T d14 = k.sig[9] * (m14 - q14), d15 = k.sig[10] * (m15 - q15);
+    const T d16 = k.sig[11] * (m16 - q16);
+
+    // ---- inverse blocks (scaled) and inverse butterflies: dt*Omega -------
+#pragma unroll
+    for (int g = 0; g < 4; ++g) {
+        const T cS = k.kS[g][0] * d5 + k.kS[g][1] * d14;
+        const T cX = k.kD[g][0] * d8 + k.kD[g][1] * d10 + k.kD[g][2] * d12;
+        const T cY = k.kD[g][0] * d9 + k.kD[g][1] * d11 - k.kD[g][2] * d13;
+        T om[4];
+        if (g < 2) {
+            const T cQ = k.kQ[g][0] * d6 + k.kQ[g][1] * d16;
+            om[0] = cS + cX + cQ;
+            om[2] = cS - cX + cQ;
+            om[1] = cS + cY - cQ;
+            om[3] = cS - cY - cQ;
+        } else {
+            const T cXY = k.kX[g - 2][0] * d7 + k.kX[g - 2][1] * d15;
+            om[0] = cS + cX + cY + cXY;
+            om[1] = cS - cX + cY - cXY;
+            om[2] = cS - cX - cY + cXY;
+            om[3] = cS + cX - cY - cXY;
+        }
+        // ---- Lax-Wendroff advection along each moving axis + Euler ------
+        const T p = k.lwp[g], qq = k.lwq[g];
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+            const int i = 4 * g + m;
+            const T fc = f[i];
+            T adv;
+            if (g < 2) {
+                // +x: p on x-1; -x: p on x+1; +y: p on y-1; -y: p on y+1
+                if (m == 0) adv = p * (F(i, XM) - fc) + qq * (F(i, XP) - fc);
+                else if (m == 2) adv = qq * (F(i, XM) - fc) + p * (F(i, XP) - fc);
+                else if (m == 1) adv = p * (F(i, YM) - fc) + qq * (F(i, YP) - fc);
+                else adv = qq * (F(i, YM) - fc) + p * (F(i, YP) - fc);
+            } else {
+                const bool posx = (m == 0 || m == 3), posy = (m == 0 || m == 1);
+                const T ax = posx ? p * (F(i, XM) - fc) + qq * (F(i, XP) - fc)
+                                  : qq * (F(i, XM) - fc) + p * (F(i, XP) - fc);
+                const T ay = posy ? p * (F(i, YM) - fc) + qq * (F(i, YP) - fc)
+                                  : qq * (F(i, YM) - fc) + p * (F(i, YP) - fc);
+                adv = ax + ay;
+            }
+            out[i] = fc + (adv + om[m]);
+        }
+    }
+}
+
+#endif  // __CUDACC__
+
+}  // namespace mrt

@@ -1,0 +1,380 @@
+// step_kernels.cu - the fused MRT-FDLB time step (Eq. 3: moments, relaxation
+// toward the Appendix equilibria, inverse transform, Lax-Wendroff advection
+// and forward-Euler update in one pass over the state).
+//
+// Two kernels compute the same cell update (model.cuh):
+//
+//  * step_tma: a CTA owns a strip of TMA_W = 128 columns and a chunk of rows.
+//    One elected thread streams the rows of all 16 planes (plus a 16-byte
+//    halo on each side for the x neighbours) from HBM into a ring of shared
+//    memory slots with 3-D cp.async.bulk.tensor loads completing on
+//    mbarriers; every thread computes one cell per row from rows r-1, r, r+1
+//    of the ring and stores its 16 outputs with coalesced row stores.  Each
+//    f value is read from HBM once (halo columns and the two chunk-boundary
+//    rows are L2 hits), so the traffic is the 16 reads + 16 writes per cell
+//    of the algorithm.
+//  * step_direct: one thread per cell reading its stencil from global memory;
+//    the simple form, used for cross-checks.
+//
+// Both optionally accumulate the conserved totals (rho, jx, jy, e) of the
+// output state: FP32 moments summed per thread with an error-free two-sum
+// (FP64 moments in the FP64 instantiation), then reduced per CTA in FP64 and
+// written as one block partial; a fixed-order finalise pass sums the partials.
+#include <cstdint>
+
+#include "internal.h"
+
+namespace mrt {
+
+namespace {
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+                 : "memory");
+}
+
+__device__ __forceinline__ void fence_barrier_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ uint64_t globaltimer_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// A wait that gives up after ~2 s of wall time instead of spinning forever.
+constexpr uint64_t kWaitLimitNs = 2000000000ull;
+
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = globaltimer_ns();
+    while (true) {
+#pragma unroll 1
+        for (int i = 0; i < 64; ++i)
+            if (mbar_try_wait(bar, parity)) return true;
+        if (globaltimer_ns() - t0 > kWaitLimitNs) return false;
+    }
+}
+
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, uint64_t* bar,
+                                            int x, int y, int z) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// Error-free accumulation of FP32 values into (hi, lo); FP64 sums plainly.
+template <class T>
+struct Acc {
+    T hi = 0, lo = 0;
+    __device__ __forceinline__ void add(T v) {
+        const T s = hi + v;
+        const T bb = s - hi;
+        lo += (hi - (s - bb)) + (v - bb);
+        hi = s;
+    }
+    __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+};
+template <>
+struct Acc<double> {
+    double hi = 0;
+    __device__ __forceinline__ void add(double v) { hi += v; }
+    __device__ __forceinline__ double value() const { return hi; }
+};
+
+// CTA-wide FP64 sum of 4 values; thread 0 writes them to dst[0..3].
+__device__ __forceinline__ void block_sum4(double v[4], double* dst) {
+    __shared__ double red[32][4];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nwarps = (blockDim.x * blockDim.y + 31) >> 5;
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+        for (int o = 16; o > 0; o >>= 1) v[q] += __shfl_xor_sync(0xffffffffu, v[q], o);
+    if (lane == 0)
+        for (int q = 0; q < 4; ++q) red[warp][q] = v[q];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int q = 0; q < 4; ++q) {
+            double s = 0.0;
+            for (int w = 0; w < nwarps; ++w) s += red[w][q];
+            dst[q] = s;
+        }
+    }
+}
+
+template <class T>
+__device__ __forceinline__ bool healthy(T rho, T P) {
+    // false for NaN, non-positive or infinite values
+    return rho > (T)0 && P > (T)0 && rho < (T)INFINITY && P < (T)INFINITY;
+}
+
+// Store a cell's 16 outputs and, on periodic axes, the ghost copies the next
+// step reads (column G-1 mirrors x = nx-1, column G+nx mirrors x = 0; row 0
+// mirrors y = ny-1, row ny+1 mirrors y = 0).
+template <class T>
+__device__ __forceinline__ void store_cell(T* __restrict__ out, const Layout& L, int per_x,
+                                           int per_y, int x, int y, const T v[NV]) {
+    const long row = (long)(y + 1) * L.pitch;
+    const long col = L.G + x;
+#pragma unroll
+    for (int i = 0; i < NV; ++i) out[i * L.plane + row + col] = v[i];
+    if (per_x) {
+        if (x == 0) {
+#pragma unroll
+            for (int i = 0; i < NV; ++i) out[i * L.plane + row + L.G + L.nx] = v[i];
+        }
+        if (x == L.nx - 1) {
+#pragma unroll
+            for (int i = 0; i < NV; ++i) out[i * L.plane + row + L.G - 1] = v[i];
+        }
+    }
+    if (per_y) {
+        if (y == 0) {
+#pragma unroll
+            for (int i = 0; i < NV; ++i) out[i * L.plane + (long)(L.ny + 1) * L.pitch + col] = v[i];
+        }
+        if (y == L.ny - 1) {
+#pragma unroll
+            for (int i = 0; i < NV; ++i) out[i * L.plane + col] = v[i];
+        }
+    }
+}
+
+// --------------------------------------------------------------------------
+// TMA-staged strip kernel.
+// --------------------------------------------------------------------------
+template <class T, bool TOTALS>
+__global__ void __launch_bounds__(TMA_W) step_tma(const __grid_constant__ CUtensorMap map_in,
+                                                  const StepArgs<T> a) {
+    constexpr int NS = tma_stages<T>();
+    constexpr int HALO = tma_halo<T>();
+    constexpr int BOXW = tma_boxw<T>();
+    constexpr uint32_t SLOT_BYTES = (uint32_t)tma_slot_bytes<T>();
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    T* ring = reinterpret_cast<T*>(smem_raw);
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem_raw + NS * SLOT_BYTES);
+
+    const Layout& L = a.L;
+    const int tid = threadIdx.x;
+    const int x0 = blockIdx.x * TMA_W;
+    const int y0 = blockIdx.y * a.rows_per_cta;
+    const int nrows = min(a.rows_per_cta, L.ny - y0);
+    if (nrows <= 0) return;  // whole CTA leaves together
+    const int nload = nrows + 2;           // local rows 0..nrows+1 = padded rows y0..y0+nrows+1
+    const int x = x0 + tid;
+    const bool active = x < L.nx;
+    const int tma_x = L.G + x0 - HALO;     // 16-byte aligned start column of the box
+
+    if (tid == 0) {
+        for (int s = 0; s < NS; ++s) mbar_init(&full[s], 1);
+        fence_barrier_init();
+    }
+    __syncthreads();
+
+    int issued = 0;     // thread 0: rows whose load has been issued
+    int waited0 = 0;    // thread 0: rows it has seen complete
+    if (tid == 0) {
+        const int first = min(NS, nload);
+        for (int l = 0; l < first; ++l) {
+            const int s = l % NS;
+            mbar_arrive_expect_tx(&full[s], SLOT_BYTES);
+            tma_load_3d(ring + (size_t)s * NV * BOXW, &map_in, &full[s], tma_x, y0 + l, 0);
+        }
+        issued = first;
+    }
+
+    auto wait_row = [&](int l) -> bool {
+        const bool ok = mbar_wait_bounded(&full[l % NS], (uint32_t)((l / NS) & 1));
+        if (tid == 0 && ok && l == waited0) waited0 = l + 1;
+        return ok;
+    };
+
+    bool ok = wait_row(0);
+    ok = wait_row(1) && ok;
+    ok = wait_row(2) && ok;
+    bool bad = false;
+    Acc<T> acc[4];
+    const int col = tid + HALO;
+
+    auto drain = [&]() {
+        if (tid == 0) {
+            for (int l = waited0; l < issued; ++l)
+                mbar_wait_bounded(&full[l % NS], (uint32_t)((l / NS) & 1));
+            atomicOr(a.flag, FLAG_TIMEOUT);
+        }
+    };
+    if (__syncthreads_or(!ok)) { drain(); return; }
+
+#pragma unroll 1
+    for (int r = 1; r <= nrows; ++r) {
+        if (active) {
+            const T* sm = ring + (size_t)((r - 1) % NS) * NV * BOXW;
+            const T* sc = ring + (size_t)(r % NS) * NV * BOXW;
+            const T* sp = ring + (size_t)((r + 1) % NS) * NV * BOXW;
+            auto F = [&](int i, int pos) -> T {
+                switch (pos) {
+                    case C: return sc[i * BOXW + col];
+                    case XM: return sc[i * BOXW + col - 1];
+                    case XP: return sc[i * BOXW + col + 1];
+                    case YM: return sm[i * BOXW + col];
+                    default: return sp[i * BOXW + col];
+                }
+            };
+            T out[NV];
+            T rho, P;
+            cell_update<T>(F, a.k, out, rho, P);
+            bad |= !healthy(rho, P);
+            const int y = y0 + r - 1;
+            store_cell<T>(a.out, L, a.per_x, a.per_y, x, y, out);
+            if (TOTALS) {
+                T q0, q1, q2, q3;
+                conserved_moments<T>(out, q0, q1, q2, q3);
+                acc[0].add(q0); acc[1].add(q1); acc[2].add(q2); acc[3].add(q3);
+            }
+        }
+        ok = (r + 2 < nload) ? wait_row(r + 2) : true;
+        // every thread is done with slot (r-1) % NS after this barrier
+        if (__syncthreads_or(!ok)) { drain(); return; }
+        if (tid == 0) {
+            const int l = r - 1 + NS;
+            if (l < nload) {
+                const int s = l % NS;
+                mbar_arrive_expect_tx(&full[s], SLOT_BYTES);
+                tma_load_3d(ring + (size_t)s * NV * BOXW, &map_in, &full[s], tma_x, y0 + l, 0);
+                issued = l + 1;
+            }
+        }
+    }
+
+    if (__syncthreads_or(bad) && tid == 0) atomicOr(a.flag, FLAG_UNSTABLE);
+    if (TOTALS) {
+        double v[4] = {acc[0].value(), acc[1].value(), acc[2].value(), acc[3].value()};
+        block_sum4(v, a.partials + 4 * (size_t)(blockIdx.y * gridDim.x + blockIdx.x));
+    }
+}
+
+// --------------------------------------------------------------------------
+// One thread per cell, stencil straight from global memory.
+// --------------------------------------------------------------------------
+constexpr int DIR_BX = 32, DIR_BY = 8;
+
+template <class T, bool TOTALS>
+__global__ void __launch_bounds__(DIR_BX* DIR_BY) step_direct(const StepArgs<T> a) {
+    const Layout& L = a.L;
+    const int x = blockIdx.x * DIR_BX + threadIdx.x;
+    const int y = blockIdx.y * DIR_BY + threadIdx.y;
+    const bool active = x < L.nx && y < L.ny;
+    bool bad = false;
+    T q[4] = {0, 0, 0, 0};
+    if (active) {
+        const T* __restrict__ in = a.in;
+        const long base = (long)(y + 1) * L.pitch + L.G + x;
+        auto F = [&](int i, int pos) -> T {
+            const long o = i * L.plane + base;
+            switch (pos) {
+                case C: return __ldg(in + o);
+                case XM: return __ldg(in + o - 1);
+                case XP: return __ldg(in + o + 1);
+                case YM: return __ldg(in + o - L.pitch);
+                default: return __ldg(in + o + L.pitch);
+            }
+        };
+        T out[NV];
+        T rho, P;
+        cell_update<T>(F, a.k, out, rho, P);
+        bad = !healthy(rho, P);
+        store_cell<T>(a.out, L, a.per_x, a.per_y, x, y, out);
+        if (TOTALS) conserved_moments<T>(out, q[0], q[1], q[2], q[3]);
+    }
+    if (__syncthreads_or(bad) && threadIdx.x == 0 && threadIdx.y == 0) atomicOr(a.flag, FLAG_UNSTABLE);
+    if (TOTALS) {
+        double v[4] = {(double)q[0], (double)q[1], (double)q[2], (double)q[3]};
+        block_sum4(v, a.partials + 4 * (size_t)(blockIdx.y * gridDim.x + blockIdx.x));
+    }
+}
+
+}  // namespace
+
+template <class T>
+cudaError_t launch_step_tma(const CUtensorMap* map_in, const StepArgs<T>& a, int grid_x,
+                            int grid_y, bool totals, cudaStream_t st) {
+    const size_t smem = tma_smem_bytes<T>();
+    dim3 grid(grid_x, grid_y), block(TMA_W);
+    if (totals) {
+        step_tma<T, true><<<grid, block, smem, st>>>(*map_in, a);
+    } else {
+        step_tma<T, false><<<grid, block, smem, st>>>(*map_in, a);
+    }
+    return cudaGetLastError();
+}
+
+template <class T>
+cudaError_t tma_occupancy(int* blocks_per_sm) {
+    const size_t smem = tma_smem_bytes<T>();
+    cudaError_t e;
+    if ((e = cudaFuncSetAttribute(step_tma<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)smem)) != cudaSuccess)
+        return e;
+    if ((e = cudaFuncSetAttribute(step_tma<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)smem)) != cudaSuccess)
+        return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, step_tma<T, false>,
+                                                         TMA_W, smem);
+}
+
+template <class T>
+void direct_grid(const Layout& L, dim3* grid, dim3* block) {
+    *block = dim3(DIR_BX, DIR_BY);
+    *grid = dim3((L.nx + DIR_BX - 1) / DIR_BX, (L.ny + DIR_BY - 1) / DIR_BY);
+}
+
+template <class T>
+cudaError_t launch_step_direct(const StepArgs<T>& a, bool totals, cudaStream_t st) {
+    dim3 grid, block;
+    direct_grid<T>(a.L, &grid, &block);
+    if (totals) {
+        step_direct<T, true><<<grid, block, 0, st>>>(a);
+    } else {
+        step_direct<T, false><<<grid, block, 0, st>>>(a);
+    }
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_step_tma<float>(const CUtensorMap*, const StepArgs<float>&, int, int,
+                                            bool, cudaStream_t);
+template cudaError_t launch_step_tma<double>(const CUtensorMap*, const StepArgs<double>&, int, int,
+                                             bool, cudaStream_t);
+template cudaError_t launch_step_direct<float>(const StepArgs<float>&, bool, cudaStream_t);
+template cudaError_t launch_step_direct<double>(const StepArgs<double>&, bool, cudaStream_t);
+template cudaError_t tma_occupancy<float>(int*);
+template cudaError_t tma_occupancy<double>(int*);
+template void direct_grid<float>(const Layout&, dim3*, dim3*);
+template void direct_grid<double>(const Layout&, dim3*, dim3*);
+
+}  // namespace mrt

@@ -1,0 +1,43 @@
+"""Shared helpers for the GPU-vs-oracle parity tests."""
+import numpy as np
+
+import oracle
+from paper_1004_5442_gb300 import binding as Bd
+
+
+def run_oracle(w, nsteps=None):
+    g = oracle.create(w.nx, w.ny, w.dx, w.dt, w.b, w.s, w.rho, w.ux, w.uy, w.T, w.bc_x, w.bc_y)
+    oracle.run(g, w.nsteps if nsteps is None else nsteps)
+    return g
+
+
+def run_gpu(w, precision, kernel=Bd.KERNEL_AUTO, nsteps=None):
+    grid = Bd.Grid.from_workload(w, precision=precision, kernel=kernel)
+    grid.step(w.nsteps if nsteps is None else nsteps)
+    return grid
+
+
+def field_errors(got, want):
+    """L-inf and L1 errors of (rho, ux, uy, T), each relative to its field's
+    scale; the two velocity components share the flow-speed scale."""
+    names = ("rho", "ux", "uy", "T")
+    U = max(np.max(np.abs(want[1])), np.max(np.abs(want[2])), 1e-12)
+    Ul1 = np.mean(np.hypot(want[1], want[2])) + 1e-300
+    out = {}
+    for name, a, b in zip(names, got, want):
+        d = np.abs(a - b)
+        if name in ("ux", "uy"):
+            out[name] = (np.max(d) / U, np.mean(d) / max(Ul1, 1e-12 * U))
+        else:
+            out[name] = (np.max(d) / np.max(np.abs(b)), np.mean(d) / np.mean(np.abs(b)))
+    return out
+
+
+def assert_parity(got, want, linf=None, l1=None, label=""):
+    errs = field_errors(got, want)
+    for name, (ei, e1) in errs.items():
+        if linf is not None:
+            assert ei <= linf, f"{label} {name}: Linf {ei:.3e} > {linf:.1e} ({errs})"
+        if l1 is not None:
+            assert e1 <= l1, f"{label} {name}: L1 {e1:.3e} > {l1:.1e} ({errs})"
+    return errs

@@ -1,0 +1,82 @@
+"""Host-side checks of the C ABI that need no GPU: the library loads, exports
+every symbol include/mrtfdlb.h declares, and rejects invalid arguments
+before touching the device."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_1004_5442_gb300 import binding as Bd
+from paper_1004_5442_gb300 import build as B
+from paper_1004_5442_gb300 import workloads as W
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "mrtfdlb.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    B.build()
+    return Bd.load()
+
+
+def _declared():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(mrt_[a-z_]+)\s*\(", text)))
+
+
+def test_header_declarations_are_exported(lib):
+    names = _declared()
+    assert names, "no declarations parsed"
+    assert sorted(Bd.EXPORTED) == names
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+def _params(**kw):
+    w = W.uniform(16, 8)
+    p = Bd.make_params(w.nx, w.ny, w.dx, w.dt, w.gamma, w.s)
+    for k, v in kw.items():
+        setattr(p, k, v)
+    return p, w
+
+
+@pytest.mark.parametrize("field,value", [("nx", 2), ("ny", 1), ("dx", 0.0), ("dt", -1.0),
+                                         ("gamma", 1.0), ("precision", 7), ("bc_x", 3),
+                                         ("kernel", 9), ("Pr", float("nan"))])
+def test_invalid_params_rejected(lib, field, value):
+    p, w = _params(**{field: value})
+    h = ctypes.c_void_p()
+    arr = [np.ascontiguousarray(a) for a in (w.rho, w.ux, w.uy, w.T)]
+    rc = lib.mrt_create(ctypes.byref(p), *(ctypes.c_void_p(a.ctypes.data) for a in arr), 0, None,
+                        ctypes.byref(h))
+    assert rc == Bd.MRT_EINVAL
+    assert lib.mrt_last_error().decode()
+
+
+def test_negative_rate_rejected(lib):
+    p, w = _params()
+    p.s[9] = -1.0
+    h = ctypes.c_void_p()
+    arr = [np.ascontiguousarray(a) for a in (w.rho, w.ux, w.uy, w.T)]
+    rc = lib.mrt_create(ctypes.byref(p), *(ctypes.c_void_p(a.ctypes.data) for a in arr), 0, None,
+                        ctypes.byref(h))
+    assert rc == Bd.MRT_EINVAL and "s_10" in lib.mrt_last_error().decode()
+
+
+def test_null_pointers_rejected(lib):
+    p, w = _params()
+    h = ctypes.c_void_p()
+    assert lib.mrt_create(ctypes.byref(p), None, None, None, None, 0, None, ctypes.byref(h)) == Bd.MRT_EINVAL
+    assert lib.mrt_create(None, None, None, None, None, 0, None, ctypes.byref(h)) == Bd.MRT_EINVAL
+    assert lib.mrt_step(None, 1) == Bd.MRT_EINVAL
+    assert lib.mrt_health(None) == Bd.MRT_EINVAL
+    lib.mrt_destroy(None)
+
+
+def test_status_strings(lib):
+    for code, name in Bd._STATUS.items():
+        assert lib.mrt_status_str(code).decode() == name

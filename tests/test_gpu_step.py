@@ -1,0 +1,261 @@
+"""GPU parity: the CUDA step (through the C ABI) against the FP64 oracle on
+the same seeded inputs.
+
+Tolerances:
+  FP64 GPU vs oracle      1e-12 relative (long shock runs 1e-10): only the
+                          summation order differs (symmetry-adapted blocks on
+                          the GPU, dense 16x16 loops in the oracle).
+  FP32 GPU, smooth flow   L-inf and L1 <= 1e-5 relative per field.
+  FP32 GPU, shocks        L1 <= 1e-4 relative per field.
+Velocity errors are relative to the flow-speed scale of the oracle solution.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import riemann
+from paper_1004_5442_gb300 import binding as Bd
+from paper_1004_5442_gb300 import workloads as W
+from _parity import assert_parity, field_errors, run_gpu, run_oracle
+
+pytestmark = pytest.mark.gpu
+
+KERNELS = [Bd.KERNEL_TMA, Bd.KERNEL_DIRECT]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    Bd.load()
+    yield
+
+
+# --------------------------------------------------------------------------
+# Raw state after one step
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("kernel", KERNELS)
+@pytest.mark.parametrize("bcx,bcy", [(0, 0), (1, 0), (0, 1), (1, 1)])
+def test_one_step_raw_state_fp64(kernel, bcx, bcy):
+    w = W.random_smooth(300, 37, seed=4, amp=0.1, bc_x=bcx, bc_y=bcy)
+    g = run_oracle(w, 1)
+    with run_gpu(w, Bd.FP64, kernel, nsteps=1) as grid:
+        f = grid.get_f()
+    scale = np.max(np.abs(g.f))
+    assert np.max(np.abs(f - g.f)) <= 1e-13 * scale
+
+
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_one_step_raw_state_fp32(kernel):
+    w = W.random_smooth(300, 37, seed=4, amp=0.1, bc_x=1)
+    with Bd.Grid.from_workload(w, precision=Bd.FP32, kernel=kernel) as grid:
+        f0 = grid.get_f().astype(np.float64)
+        grid.step(1)
+        f1 = grid.get_f().astype(np.float64)
+    g = oracle.create(w.nx, w.ny, w.dx, w.dt, w.b, w.s, w.rho, w.ux, w.uy, w.T, w.bc_x, w.bc_y)
+    want = oracle.step(g, f0)  # oracle step from the GPU's FP32 state
+    scale = np.max(np.abs(want))
+    assert np.max(np.abs(f1 - want)) <= 2e-6 * scale
+
+
+# --------------------------------------------------------------------------
+# Macroscopic parity over many steps
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_smooth_periodic_parity(kernel):
+    w = W.random_smooth(300, 37, seed=9, amp=0.1, nsteps=200)
+    want = oracle.macro(run_oracle(w))
+    with run_gpu(w, Bd.FP64, kernel) as grid:
+        assert_parity(grid.macro(), want, linf=1e-12, label="fp64")
+    with run_gpu(w, Bd.FP32, kernel) as grid:
+        assert_parity(grid.macro(), want, linf=1e-5, l1=1e-5, label="fp32")
+
+
+def test_sod_tube_parity():
+    """Sod shock tube, 400 x 4, gamma 1.4, Pr 0.71, CFL 0.1, 2000 steps."""
+    w = W.sod_tube()
+    want = oracle.macro(run_oracle(w))
+    with run_gpu(w, Bd.FP64) as grid:
+        assert_parity(grid.macro(), want, linf=1e-10, label="fp64")
+    with run_gpu(w, Bd.FP32) as grid:
+        assert_parity(grid.macro(), want, l1=1e-4, label="fp32")
+
+
+@pytest.fixture(scope="module")
+def strong_shock_oracle():
+    w = W.strong_shock()           # 2048 x 8, 10000 steps
+    return w, oracle.macro(run_oracle(w))
+
+
+@pytest.mark.parametrize("prec", [Bd.FP32, Bd.FP64])
+def test_strong_shock_parity(strong_shock_oracle, prec):
+    """(rho, u, p) = (5, 0, 100) | (1, 0, 1), 2048 x 8, Pr 1, CFL 0.05,
+    10000 steps: parity with the oracle and the exact shock position."""
+    w, want = strong_shock_oracle
+    with run_gpu(w, prec) as grid:
+        got = grid.macro()
+        tot = grid.totals()
+    if prec == Bd.FP64:
+        assert_parity(got, want, linf=1e-9, label="fp64")
+    else:
+        assert_parity(got, want, l1=1e-4, label="fp32")
+    L, R = w.extra["left"], w.extra["right"]
+    st = riemann.star_state(L, R, w.gamma)
+    x = (np.arange(w.nx) + 0.5) * w.dx
+    xs = riemann.shock_position(x, got[0][0], st.rho_r, R[0])
+    assert abs(xs - (0.5 + st.shock_r * w.nsteps * w.dt)) < 2 * w.dx
+    assert np.all(np.isfinite(tot))
+
+
+def test_kelvin_helmholtz_reduced_parity():
+    w = W.kelvin_helmholtz(n=256, nsteps=1000)
+    want = oracle.macro(run_oracle(w))
+    with run_gpu(w, Bd.FP32) as grid:
+        assert_parity(grid.macro(), want, linf=1e-5, l1=1e-5, label="kh fp32")
+
+
+def test_vortex_parity():
+    w = W.smooth_vortex(n=128, nsteps=500)
+    want = oracle.macro(run_oracle(w))
+    with run_gpu(w, Bd.FP32) as grid:
+        assert_parity(grid.macro(), want, linf=1e-5, l1=1e-5, label="vortex fp32")
+    with run_gpu(w, Bd.FP64) as grid:
+        assert_parity(grid.macro(), want, linf=1e-12, label="vortex fp64")
+
+
+@pytest.mark.parametrize("nx,ny", [(3, 3), (4, 5), (129, 3), (127, 130), (257, 9)])
+@pytest.mark.parametrize("bcx,bcy", [(0, 0), (1, 1), (1, 0)])
+def test_edge_sizes(nx, ny, bcx, bcy):
+    w = W.random_smooth(nx, ny, seed=nx + ny, amp=0.05, bc_x=bcx, bc_y=bcy, nsteps=15)
+    want = oracle.macro(run_oracle(w))
+    for kernel in KERNELS:
+        with run_gpu(w, Bd.FP64, kernel) as grid:
+            assert_parity(grid.macro(), want, linf=1e-12, label=f"fp64 k{kernel}")
+        with run_gpu(w, Bd.FP32, kernel) as grid:
+            assert_parity(grid.macro(), want, linf=1e-5, label=f"fp32 k{kernel}")
+
+
+def test_device_inputs_match_host_inputs():
+    import torch
+    w = W.random_smooth(200, 40, seed=3, amp=0.05, nsteps=5)
+    with run_gpu(w, Bd.FP32) as a:
+        fa = a.get_f()
+    dev = [torch.tensor(np.ascontiguousarray(v), device="cuda") for v in (w.rho, w.ux, w.uy, w.T)]
+    p = Bd.make_params(w.nx, w.ny, w.dx, w.dt, w.gamma, w.s, w.bc_x, w.bc_y, Bd.FP32)
+    with Bd.Grid(p, *dev) as b:
+        b.step(5)
+        fb = b.get_f()
+    np.testing.assert_array_equal(fa, fb)
+
+
+# --------------------------------------------------------------------------
+# Conserved totals, checkpoint/resume, health
+# --------------------------------------------------------------------------
+def test_totals_match_oracle():
+    w = W.random_smooth(300, 37, seed=5, amp=0.1, nsteps=30)
+    g = run_oracle(w)
+    want = oracle.totals(g)
+    _, _, _, M, _ = oracle.model()
+    absq = np.array([np.sum(np.abs(np.tensordot(M[k], g.f, 1))) * w.dx ** 2 for k in range(4)])
+    with run_gpu(w, Bd.FP64) as grid:
+        fused = grid.totals()
+        grid.set_f(grid.get_f())         # forces the standalone reduction
+        alone = grid.totals()
+    assert np.all(np.abs(fused - want) <= 1e-13 * absq)
+    assert np.all(np.abs(alone - fused) <= 1e-14 * absq)
+    with run_gpu(w, Bd.FP32) as grid:
+        t32 = grid.totals()
+    assert np.all(np.abs(t32 - want) <= 1e-5 * absq)
+
+
+def test_fp64_gpu_conserves_to_roundoff():
+    w = W.random_smooth(300, 37, seed=6, amp=0.1)
+    with Bd.Grid.from_workload(w, precision=Bd.FP64) as grid:
+        f = grid.get_f()
+        _, _, _, M, _ = oracle.model()
+        absq = np.array([np.sum(np.abs(np.tensordot(M[k], f, 1))) * w.dx ** 2 for k in range(4)])
+        grid.step(1)
+        t0 = grid.totals()
+        for _ in range(10):
+            grid.step(1)
+            t = grid.totals()
+            assert np.all(np.abs(t - t0) <= 1e-13 * absq)
+
+
+@pytest.mark.parametrize("prec", [Bd.FP32, Bd.FP64])
+def test_checkpoint_resume_bit_identical(prec):
+    w = W.kelvin_helmholtz(n=192, nsteps=0)
+    with Bd.Grid.from_workload(w, precision=prec) as a:
+        a.step(7)
+        ckpt = a.get_f()
+        a.step(9)
+        fa = a.get_f()
+    with Bd.Grid.from_workload(w, precision=prec) as b:
+        b.set_f(ckpt)
+        b.step(9)
+        fb = b.get_f()
+    np.testing.assert_array_equal(fa, fb)
+
+
+@pytest.mark.parametrize("bad", ["rho", "T"])
+def test_nonpositive_initial_state_rejected(bad):
+    w = W.uniform(40, 12)
+    arr = {k: np.ascontiguousarray(getattr(w, k)).copy() for k in ("rho", "ux", "uy", "T")}
+    arr[bad][3, 5] = -0.1
+    p = Bd.make_params(w.nx, w.ny, w.dx, w.dt, w.gamma, w.s)
+    with pytest.raises(Bd.MrtError) as ei:
+        Bd.Grid(p, arr["rho"], arr["ux"], arr["uy"], arr["T"])
+    assert ei.value.code == Bd.MRT_EINVAL
+
+
+def test_health_flag_trips_on_blow_up():
+    w = W.random_smooth(64, 16, seed=1, amp=0.2)
+    s = np.full(16, 2.5 / w.dt)         # sigma = 2.5 > 1: outside the stable interval
+    p = Bd.make_params(w.nx, w.ny, w.dx, w.dt, w.gamma, s, 0, 0, Bd.FP32)
+    with Bd.Grid(p, w.rho, w.ux, w.uy, w.T) as g:
+        assert g.health() == Bd.MRT_OK
+        g.step(400)
+        assert g.health() == Bd.MRT_EUNSTABLE
+        with pytest.raises(Bd.MrtError):
+            g.totals()
+
+
+# --------------------------------------------------------------------------
+# Full size, bench launch configuration: sampled windows
+# --------------------------------------------------------------------------
+def _window_oracle_step(w, f_full, y0, x0, n):
+    """One oracle step on an (n+2)^2 periodic window around [y0:y0+n, x0:x0+n];
+    the interior depends only on the window, so it is exact there."""
+    ys = (np.arange(y0 - 1, y0 + n + 1)) % w.ny
+    xs = (np.arange(x0 - 1, x0 + n + 1)) % w.nx
+    fw = np.ascontiguousarray(f_full[:, ys][:, :, xs].astype(np.float64))
+    g = oracle.Grid(n + 2, n + 2, w.dx, w.dt, w.b, w.s, oracle.BC_PERIODIC, oracle.BC_PERIODIC)
+    g.f = fw
+    g.gx = np.zeros((16, 2, n + 2))
+    g.gy = np.zeros((16, 2, n + 2))
+    return oracle.step(g, fw)[:, 1:-1, 1:-1]
+
+
+def test_full_size_kh_sampled_windows():
+    """4096^2 Kelvin-Helmholtz in FP32 with the TMA kernel (the benchmark's
+    configuration): after 3 steps, 12 seeded 48^2 windows (including the
+    periodic corners and strip/chunk seams) of step 3 -> 4 match the oracle."""
+    w = W.kelvin_helmholtz(n=4096, nsteps=0)
+    rng = np.random.default_rng(0)
+    n = 48
+    corners = [(0, 0), (w.ny - n, w.nx - n), (0, w.nx - n), (w.ny - n, 0), (2000, 128 * 16 - 24)]
+    wins = corners + [(int(rng.integers(0, w.ny - n)), int(rng.integers(0, w.nx - n))) for _ in range(7)]
+    with Bd.Grid.from_workload(w, precision=Bd.FP32, kernel=Bd.KERNEL_TMA) as grid:
+        assert grid.info()["kernel"] == Bd.KERNEL_TMA
+        grid.step(3)
+        f3 = grid.get_f()
+        grid.step(1)
+        f4 = grid.get_f()
+        tot = grid.totals()
+    for (y0, x0) in wins:
+        want = _window_oracle_step(w, f3, y0, x0, n)
+        got = f4[:, y0:y0 + n, x0:x0 + n].astype(np.float64)
+        scale = np.max(np.abs(want))
+        assert np.max(np.abs(got - want)) <= 2e-6 * scale, (y0, x0)
+    assert np.all(np.isfinite(tot)) and abs(tot[0] - 1.0) < 1e-6
