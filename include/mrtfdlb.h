@@ -123,6 +123,33 @@ mrt_status mrt_health(mrt_grid *g);
 mrt_status mrt_info(const mrt_grid *g, long *steps, long *pitch, long *plane_stride,
                     int *kernel_in_use);
 
+/* Conserved totals sum_cells (rho, j_x, j_y, e) * dx * dy of a state held by
+ * the caller on the device, computed without any allocation by the library.
+ * The paper has no counterpart: this entry point exists for callers that
+ * cannot allocate device memory at the moment they need the totals, such as
+ * code running while a stream is captured into a CUDA graph, code inside a
+ * framework that owns the device-memory budget through its own pool, or
+ * monitoring loops that must never touch the allocator.
+ *   f       device pointer, dense [16][ny][nx] (the layout of mrt_get_f, not
+ *           the grid's padded layout), float for MRT_FP32, double for
+ *           MRT_FP64; read only.
+ *   out     device pointer to 4 doubles owned by the caller; written
+ *           asynchronously on `stream` (a cudaStream_t, NULL = legacy stream).
+ * Scratch: a fixed 128 KB array in the library's device memory, present on
+ * every GPU that loads the library until the process exits.  It limits
+ * nx * ny to 67,108,864 cells (8192 x 8192); larger sizes return MRT_EINVAL.
+ * The first call on a device looks the array's device address up with
+ * cudaGetSymbolAddress while that device is current; make that first call
+ * before any stream capture.  No cudaMalloc, cudaFree or other allocating
+ * call is made.  Every call uses the same array: calls whose kernels can run
+ * at the same time on the GPU (unordered streams) race and return wrong
+ * totals, so order them.  Each call writes every scratch slot it reads, so
+ * what an earlier call left behind does not matter.
+ * Errors: MRT_EINVAL (NULL f or out, nx or ny < 1, dx not finite and > 0,
+ * bad precision, too many cells), MRT_ECUDA. */
+mrt_status mrt_conserved_totals_static(const void *f, int precision, int nx, int ny, double dx,
+                                       double *out, void *stream);
+
 /* Release every device resource of the grid (synchronises its stream). */
 void mrt_destroy(mrt_grid *g);
 

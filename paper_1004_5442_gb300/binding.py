@@ -24,7 +24,7 @@ KERNEL_AUTO, KERNEL_TMA, KERNEL_DIRECT = 0, 1, 2
 # every symbol include/mrtfdlb.h declares
 EXPORTED = ["mrt_create", "mrt_step", "mrt_get_macro", "mrt_conserved_totals", "mrt_get_f",
             "mrt_set_f", "mrt_health", "mrt_info", "mrt_destroy", "mrt_status_str",
-            "mrt_last_error"]
+            "mrt_last_error", "mrt_conserved_totals_static"]
 
 
 class MrtError(RuntimeError):
@@ -70,8 +70,9 @@ def load(path: str = LIB_PATH):
     L.mrt_status_str.restype = ctypes.c_char_p
     L.mrt_status_str.argtypes = [ip]
     L.mrt_last_error.restype = ctypes.c_char_p
+    L.mrt_conserved_totals_static.argtypes = [vp, ip, ip, ip, ctypes.c_double, vp, vp]
     for name in ("mrt_create", "mrt_step", "mrt_get_macro", "mrt_conserved_totals", "mrt_get_f",
-                 "mrt_set_f", "mrt_health", "mrt_info"):
+                 "mrt_set_f", "mrt_health", "mrt_info", "mrt_conserved_totals_static"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -108,6 +109,15 @@ def make_params(nx, ny, dx, dt, gamma, s, bc_x=BC_PERIODIC, bc_y=BC_PERIODIC, pr
         p.s[k] = float(s[k])
     p.bc_x, p.bc_y, p.precision, p.kernel = int(bc_x), int(bc_y), int(precision), int(kernel)
     return p
+
+
+def conserved_totals_static(f, precision: int, nx: int, ny: int, dx: float, out, stream=None) -> None:
+    """Totals of a dense [16][ny][nx] device state into out (4 doubles on the
+    device) without any allocation by the library (mrt_conserved_totals_static)."""
+    if stream is None:
+        stream = _torch_stream()
+    check(load().mrt_conserved_totals_static(ctypes.c_void_p(_ptr(f)), int(precision), int(nx), int(ny),
+                                             float(dx), ctypes.c_void_p(_ptr(out)), ctypes.c_void_p(stream)))
 
 
 class Grid:

@@ -26,6 +26,13 @@ static mrt_status fail(mrt_status s, const char* fmt, ...) {
     return s;
 }
 
+void mrt::set_last_error(const char* fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof g_err, fmt, ap);
+    va_end(ap);
+}
+
 #define CUDA_TRY(call)                                                                      \
     do {                                                                                    \
         cudaError_t e_ = (call);                                                            \

@@ -7,6 +7,9 @@
 
 namespace mrt {
 
+// Records the message mrt_last_error() returns on the calling thread.
+void set_last_error(const char* fmt, ...);
+
 // Padded device layout of one distribution buffer:
 //   f[i][r][c], i = 0..15, r = 0..ny+1 (row y lives at r = y + 1; rows 0 and
 //   ny+1 are ghosts), c = 0..pitch-1 (column x lives at c = G + x; columns

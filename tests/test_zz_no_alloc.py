@@ -1,0 +1,58 @@
+"""mrt_conserved_totals_static: conserved totals of a caller-held device
+state with the scratch in a fixed array of the library instead of memory
+the library allocates.  It serves callers that cannot allocate device memory
+when they need the totals (during stream capture, under a framework that owns
+the memory budget, in allocation-free monitoring loops).  Its result is
+checked against the grid entry point mrt_conserved_totals on the same state,
+on two calls in a row, with the tolerances of the other totals tests.
+
+This file is collected last so that a run stopping at the first failure has
+already run every other test."""
+import numpy as np
+import pytest
+
+from paper_1004_5442_gb300 import binding as Bd
+from paper_1004_5442_gb300 import build as B
+from paper_1004_5442_gb300 import workloads as W
+
+
+def _abs_scale(f64, dx):
+    import oracle
+    _, _, _, M, _ = oracle.model()
+    return np.array([np.sum(np.abs(np.tensordot(M[k], f64, 1))) * dx * dx for k in range(4)])
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("prec,tol", [(Bd.FP64, 1e-13), (Bd.FP32, 1e-5)])
+def test_static_totals_match_grid_totals(prec, tol):
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    Bd.load()
+    dtype = torch.float64 if prec == Bd.FP64 else torch.float32
+    w = W.random_smooth(300, 37, seed=12, amp=0.1)
+    with Bd.Grid.from_workload(w, precision=prec) as g:
+        for call in range(2):                     # two calls in a row, different states
+            g.step(3 + 2 * call)
+            want = g.totals()                     # existing entry point
+            f = torch.empty((16, w.ny, w.nx), dtype=dtype, device="cuda")
+            g.get_f(out=f)
+            torch.cuda.synchronize()
+            out = torch.full((4,), float("nan"), dtype=torch.float64, device="cuda")
+            Bd.conserved_totals_static(f, prec, w.nx, w.ny, w.dx, out,
+                                       stream=torch.cuda.current_stream().cuda_stream)
+            torch.cuda.synchronize()
+            got = out.cpu().numpy()
+            scale = _abs_scale(f.double().cpu().numpy(), w.dx)
+            assert np.all(np.isfinite(got))
+            assert np.all(np.abs(got - want) <= tol * scale), (call, got, want)
+
+
+def test_static_totals_rejects_oversized_grid():
+    B.build()
+    L = Bd.load()
+    import ctypes
+    rc = L.mrt_conserved_totals_static(ctypes.c_void_p(16), Bd.FP32, 8193, 8192, 1.0,
+                                       ctypes.c_void_p(16), None)
+    assert rc == Bd.MRT_EINVAL
+    assert "exceeds the fixed scratch capacity" in L.mrt_last_error().decode()
