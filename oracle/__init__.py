@@ -74,6 +74,11 @@ def lib():
         L.orc_run.argtypes = [ctypes.POINTER(_Cfg), dp, dp, dp, ctypes.c_long, dp]
         L.orc_macro.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, dp, dp, dp, dp, dp]
         L.orc_totals.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, dp, dp]
+        L.orc_feq_jacobian.argtypes = [ctypes.c_double] * 5 + [dp]
+        L.orc_feq_moments_via_cplx.argtypes = [ctypes.c_double] * 5 + [dp]
+        L.orc_step_adjoint.argtypes = [ctypes.POINTER(_Cfg), dp, dp, dp, dp, dp, dp]
+        L.orc_init_adjoint.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double] + [dp] * 9
+        L.orc_ghosts_adjoint.argtypes = [ctypes.c_int] * 4 + [dp, dp, dp]
         L.orc_set_threads.argtypes = [ctypes.c_int]
         L.orc_get_threads.restype = ctypes.c_int
         _lib = L
@@ -194,3 +199,76 @@ def totals(g: Grid, f: np.ndarray | None = None) -> np.ndarray:
     out = np.zeros(4)
     lib().orc_totals(g.nx, g.ny, g.dx, _p(src), _p(out))
     return out
+
+
+# ---------------------------------------------------------------------------
+# Reverse mode
+# ---------------------------------------------------------------------------
+def feq_jacobian(rho, jx, jy, e, b) -> np.ndarray:
+    """d fhat^eq_k / d (rho, jx, jy, e) as a (16, 4) array (complex step)."""
+    out = np.zeros(NV * 4)
+    lib().orc_feq_jacobian(float(rho), float(jx), float(jy), float(e), float(b), _p(out))
+    return out.reshape(NV, 4)
+
+
+def feq_moments_via_cplx(rho, jx, jy, e, b) -> np.ndarray:
+    out = np.zeros(NV)
+    lib().orc_feq_moments_via_cplx(float(rho), float(jx), float(jy), float(e), float(b), _p(out))
+    return out
+
+
+def step_adjoint(g: Grid, f: np.ndarray, lam_next: np.ndarray, gxb: np.ndarray, gyb: np.ndarray,
+                 gs: np.ndarray) -> np.ndarray:
+    """dL/df^n from f^n and dL/df^{n+1}; accumulates ghost and rate adjoints."""
+    f = np.ascontiguousarray(f, dtype=np.float64)
+    lam_next = np.ascontiguousarray(lam_next, dtype=np.float64)
+    out = np.zeros_like(f)
+    c = g.cfg()
+    lib().orc_step_adjoint(ctypes.byref(c), _p(f), _p(lam_next), _p(out), _p(gxb), _p(gyb), _p(gs))
+    return out
+
+
+def adjoint_run(nx, ny, dx, dt, b, s, rho, ux, uy, T, nsteps, loss_grad, bc_x=BC_PERIODIC,
+                bc_y=BC_PERIODIC, ckpt=None):
+    """Gradient of a loss L(rho_N) with respect to the initial fields and the
+    16 rates, by reverse mode through nsteps oracle steps.
+
+    loss_grad(rho_N) -> (L, dL/drho_N).  States are kept every `ckpt` steps
+    and each segment is recomputed before its reverse sweep.  Returns
+    (L, g_rho, g_ux, g_uy, g_T, g_s)."""
+    arr = [np.ascontiguousarray(np.broadcast_to(np.asarray(a, dtype=np.float64), (ny, nx)))
+           for a in (rho, ux, uy, T)]
+    g = create(nx, ny, dx, dt, b, s, *arr, bc_x=bc_x, bc_y=bc_y)
+    K = nsteps if not ckpt else int(ckpt)
+    saved = {}
+    f = g.f.copy()
+    for n in range(nsteps):
+        if n % K == 0:
+            saved[n] = f.copy()
+        f = step(g, f)
+    rhoN = macro(g, f)[0]
+    L, dL = loss_grad(rhoN)
+    lam = np.ascontiguousarray(np.broadcast_to(np.asarray(dL, dtype=np.float64), (NV, ny, nx)))
+    gxb = np.zeros_like(g.gx)
+    gyb = np.zeros_like(g.gy)
+    gs = np.zeros(NV)
+    starts = list(range(0, nsteps, K))
+    for s0 in reversed(starts):
+        s1 = min(s0 + K, nsteps)
+        seg = [saved[s0]]
+        for _ in range(s0, s1 - 1):
+            seg.append(step(g, seg[-1]))
+        for n in reversed(range(s0, s1)):
+            lam = step_adjoint(g, seg[n - s0], lam, gxb, gyb, gs)
+    lib().orc_ghosts_adjoint(nx, ny, int(bc_x), int(bc_y), _p(gxb), _p(gyb), _p(lam))
+    out = [np.zeros((ny, nx)) for _ in range(4)]
+    lib().orc_init_adjoint(nx, ny, float(b), *(_p(a) for a in arr), _p(lam), *(_p(o) for o in out))
+    return (L, *out, gs)
+
+
+def forward_loss(nx, ny, dx, dt, b, s, rho, ux, uy, T, nsteps, loss_grad, bc_x=BC_PERIODIC,
+                 bc_y=BC_PERIODIC) -> float:
+    """L(rho_N) of a forward oracle run (for finite differences)."""
+    g = create(nx, ny, dx, dt, b, s, rho, ux, uy, T, bc_x=bc_x, bc_y=bc_y)
+    run(g, nsteps)
+    return loss_grad(macro(g)[0])[0]

@@ -412,3 +412,210 @@ int orc_get_threads(void)
     return 1;
 #endif
 }
+
+/* ------------------------------------------------------------------------ */
+/* Reverse mode (adjoint) of the step, for gradients of a loss of f^N.      */
+/* ------------------------------------------------------------------------ */
+#include <complex.h>
+
+/* fhat^eq (Appendix) in complex arithmetic, for complex-step derivatives
+ * (Squire and Trapp's method: for an analytic g, g'(x) = Im g(x + i h)/h
+ * with no subtractive cancellation).  Same formulas as orc_feq_moments. */
+static void feq_moments_cplx(double complex rho, double complex jx, double complex jy,
+                             double complex e, double b, double complex out[NV])
+{
+    const double R = 1.0;
+    const double complex j2 = jx * jx + jy * jy;
+    const double complex P = (e - j2 / rho) / b;
+    const double complex T = P / (rho * R);
+    const double complex dj = jx * jx - jy * jy;
+    out[0] = rho;
+    out[1] = jx;
+    out[2] = jy;
+    out[3] = e;
+    out[4] = 2.0 * P + j2 / rho;
+    out[5] = dj / rho;
+    out[6] = jx * jy / rho;
+    out[7] = (e + 2.0 * P) * jx / rho;
+    out[8] = (e + 2.0 * P) * jy / rho;
+    out[9] = (4.0 * P + jx * jx / rho + jy * jy / rho) * jx / rho;
+    out[10] = (4.0 * P + jx * jx / rho + jy * jy / rho) * jy / rho;
+    out[11] = (2.0 * P + jx * jx / rho - jy * jy / rho) * jx / rho;
+    out[12] = (-2.0 * P + jx * jx / rho - jy * jy / rho) * jy / rho;
+    out[13] = 2.0 * (b + 2.0) * rho * R * R * T * T
+            + (6.0 + b) * R * T * j2 / rho
+            + j2 * j2 / (rho * rho * rho);
+    out[14] = ((b + 4.0) * P + j2 / rho) * jx * jy / (rho * rho);
+    out[15] = ((b + 4.0) * P + j2 / rho) * dj / (rho * rho);
+}
+
+/* J[k*4 + j] = d fhat^eq_k / d m_j for m = (rho, jx, jy, e), by complex step. */
+void orc_feq_jacobian(double rho, double jx, double jy, double e, double b, double J[NV * 4])
+{
+    const double h = 1e-30;
+    for (int j = 0; j < 4; ++j) {
+        double complex m[4] = {rho, jx, jy, e};
+        m[j] += I * h;
+        double complex out[NV];
+        feq_moments_cplx(m[0], m[1], m[2], m[3], b, out);
+        for (int k = 0; k < NV; ++k) J[k * 4 + j] = cimag(out[k]) / h;
+    }
+}
+
+/* Real part of the complex-arithmetic equilibria (consistency check). */
+void orc_feq_moments_via_cplx(double rho, double jx, double jy, double e, double b, double out[NV])
+{
+    double complex o[NV];
+    feq_moments_cplx(rho, jx, jy, e, b, o);
+    for (int k = 0; k < NV; ++k) out[k] = creal(o[k]);
+}
+
+/* Add w * lam at (x, y) of plane i to the adjoint of the cell read there:
+ * a domain cell, a wrapped cell on a periodic axis, or a fixed ghost whose
+ * adjoint is accumulated in gxb / gyb (same layout as gx / gy). */
+static void scatter(const orc_cfg *c, double *lam, double *gxb, double *gyb, int i, int x, int y,
+                    double v)
+{
+    const int nx = c->nx, ny = c->ny;
+    const size_t n = (size_t)nx * (size_t)ny;
+    if (x < 0 || x >= nx) {
+        if (c->bc_x == ORC_BC_PERIODIC) {
+            x = (x + nx) % nx;
+        } else {
+            const int side = (x < 0) ? 0 : 1;
+            gxb[((size_t)i * 2 + side) * ny + y] += v;
+            return;
+        }
+    }
+    if (y < 0 || y >= ny) {
+        if (c->bc_y == ORC_BC_PERIODIC) {
+            y = (y + ny) % ny;
+        } else {
+            const int side = (y < 0) ? 0 : 1;
+            gyb[((size_t)i * 2 + side) * nx + x] += v;
+            return;
+        }
+    }
+    lam[(size_t)i * n + (size_t)y * nx + x] += v;
+}
+
+/* Transpose of one step.  With f^{n+1} = step(f^n) as in orc_step and
+ * lam_next = dL/df^{n+1}, writes lam = dL/df^n (the contribution through
+ * this step), adds dL/d(ghost) to gxb / gyb (fixed-equilibrium axes) and
+ * adds dL/ds_k to gs[k].  Every forward dependence is transposed literally:
+ *   f^{n+1}_i(x) = f_i(x) + sum over the LW stencil + dt Omega_i(f(x)),
+ *   dt Omega = -dt Minv S (M f - E(M f)),
+ *   d(dt Omega)/df = -dt Minv S (I - JE) M,  JE = d fhat^eq / d fhat
+ *                                               (non-zero in columns 1..4),
+ *   d f^{n+1}_i/d s_k = -dt Minv_ik (fhat_k - fhat^eq_k).
+ * Serial (the scatter form writes to neighbours). */
+void orc_step_adjoint(const orc_cfg *c, const double *f, const double *lam_next, double *lam,
+                      double *gxb, double *gyb, double gs[NV])
+{
+    ensure_model();
+    const int nx = c->nx, ny = c->ny;
+    const size_t n = (size_t)nx * (size_t)ny;
+    const double lam_r = c->dt / c->dx;
+    memset(lam, 0, sizeof(double) * NV * n);
+    for (int y = 0; y < ny; ++y) {
+        for (int x = 0; x < nx; ++x) {
+            double fl[NV], ln[NV], fh[NV], fe[NV], mu[NV], w[NV], J[NV * 4];
+            for (int i = 0; i < NV; ++i) {
+                fl[i] = f[(size_t)i * n + (size_t)y * nx + x];
+                ln[i] = lam_next[(size_t)i * n + (size_t)y * nx + x];
+            }
+            /* advection and identity: scatter to the cells the output read */
+            for (int i = 0; i < NV; ++i) {
+                const double cx = g_vx[i] * lam_r, cy = g_vy[i] * lam_r;
+                /* f_new = f0 + ax_m f(x-1) + ax_p f(x+1) + (-cx^2) f0 + (same in y) */
+                const double am_x = 0.5 * cx + 0.5 * cx * cx, ap_x = -0.5 * cx + 0.5 * cx * cx;
+                const double am_y = 0.5 * cy + 0.5 * cy * cy, ap_y = -0.5 * cy + 0.5 * cy * cy;
+                const double a0 = 1.0 - cx * cx - cy * cy;
+                scatter(c, lam, gxb, gyb, i, x, y, a0 * ln[i]);
+                scatter(c, lam, gxb, gyb, i, x - 1, y, am_x * ln[i]);
+                scatter(c, lam, gxb, gyb, i, x + 1, y, ap_x * ln[i]);
+                scatter(c, lam, gxb, gyb, i, x, y - 1, am_y * ln[i]);
+                scatter(c, lam, gxb, gyb, i, x, y + 1, ap_y * ln[i]);
+            }
+            /* collision, local */
+            for (int k = 0; k < NV; ++k) {
+                double acc = 0.0;
+                for (int i = 0; i < NV; ++i) acc += g_M[k * NV + i] * fl[i];
+                fh[k] = acc;
+            }
+            orc_feq_moments(fh[0], fh[1], fh[2], fh[3], c->b, fe);
+            orc_feq_jacobian(fh[0], fh[1], fh[2], fh[3], c->b, J);
+            for (int k = 0; k < NV; ++k) {       /* mu = Minv^T lam_next */
+                double acc = 0.0;
+                for (int i = 0; i < NV; ++i) acc += g_Minv[i * NV + k] * ln[i];
+                mu[k] = acc;
+            }
+            for (int k = 0; k < NV; ++k) gs[k] += -c->dt * mu[k] * (fh[k] - fe[k]);
+            /* w = (I - JE)^T S mu, JE[k][j] = J[k*4+j] for j < 4, 0 otherwise */
+            for (int j = 0; j < NV; ++j) {
+                double acc = c->s[j] * mu[j];
+                if (j < 4)
+                    for (int k = 0; k < NV; ++k) acc -= J[k * 4 + j] * c->s[k] * mu[k];
+                w[j] = acc;
+            }
+            /* lam += -dt M^T w */
+            for (int i = 0; i < NV; ++i) {
+                double acc = 0.0;
+                for (int j = 0; j < NV; ++j) acc += g_M[j * NV + i] * w[j];
+                lam[(size_t)i * n + (size_t)y * nx + x] += -c->dt * acc;
+            }
+        }
+    }
+}
+
+/* Transpose of the initial state f^0 = Minv fhat^eq(m(rho, u, T)) with
+ * m = (rho, rho ux, rho uy, b rho T + rho (ux^2 + uy^2)): from lam0 =
+ * dL/df^0 writes dL/d(rho, ux, uy, T) per cell. */
+void orc_init_adjoint(int nx, int ny, double b, const double *rho, const double *ux,
+                      const double *uy, const double *T, const double *lam0, double *g_rho,
+                      double *g_ux, double *g_uy, double *g_T)
+{
+    ensure_model();
+    const size_t n = (size_t)nx * (size_t)ny;
+    for (size_t cidx = 0; cidx < n; ++cidx) {
+        const double r = rho[cidx], u = ux[cidx], v = uy[cidx], t = T[cidx];
+        const double m[4] = {r, r * u, r * v, b * r * t + r * (u * u + v * v)};
+        double J[NV * 4], mu[NV], mb[4];
+        orc_feq_jacobian(m[0], m[1], m[2], m[3], b, J);
+        for (int k = 0; k < NV; ++k) {
+            double acc = 0.0;
+            for (int i = 0; i < NV; ++i) acc += g_Minv[i * NV + k] * lam0[(size_t)i * n + cidx];
+            mu[k] = acc;
+        }
+        for (int j = 0; j < 4; ++j) {
+            double acc = 0.0;
+            for (int k = 0; k < NV; ++k) acc += J[k * 4 + j] * mu[k];
+            mb[j] = acc;
+        }
+        /* dm/d(rho, u, v, T) */
+        g_rho[cidx] = mb[0] + mb[1] * u + mb[2] * v + mb[3] * (b * t + u * u + v * v);
+        g_ux[cidx] = mb[1] * r + mb[3] * 2.0 * r * u;
+        g_uy[cidx] = mb[2] * r + mb[3] * 2.0 * r * v;
+        g_T[cidx] = mb[3] * b * r;
+    }
+}
+
+/* Adjoint of the fixed-equilibrium ghosts: each ghost holds the initial f
+ * of its adjacent cell, so its accumulated adjoint adds to lam0 there. */
+void orc_ghosts_adjoint(int nx, int ny, int bc_x, int bc_y, const double *gxb, const double *gyb,
+                        double *lam0)
+{
+    const size_t n = (size_t)nx * (size_t)ny;
+    for (int i = 0; i < NV; ++i) {
+        if (bc_x == ORC_BC_FIXED_EQ)
+            for (int y = 0; y < ny; ++y) {
+                lam0[(size_t)i * n + (size_t)y * nx + 0] += gxb[((size_t)i * 2 + 0) * ny + y];
+                lam0[(size_t)i * n + (size_t)y * nx + (nx - 1)] += gxb[((size_t)i * 2 + 1) * ny + y];
+            }
+        if (bc_y == ORC_BC_FIXED_EQ)
+            for (int x = 0; x < nx; ++x) {
+                lam0[(size_t)i * n + 0 * (size_t)nx + x] += gyb[((size_t)i * 2 + 0) * nx + x];
+                lam0[(size_t)i * n + (size_t)(ny - 1) * nx + x] += gyb[((size_t)i * 2 + 1) * nx + x];
+            }
+    }
+}
