@@ -52,6 +52,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--tile", type=int, default=0, help="TMA kernel variant (0 = library default)")
+    ap.add_argument("--sweep-tiles", action="store_true", help="time every TMA variant, print one line each")
     return ap.parse_args()
 
 
@@ -236,8 +238,10 @@ def run_ours(args):
     cells = w.nx * w.ny
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
-        grid = Bd.Grid.from_workload(w, precision=Bd.FP32, kernel=Bd.KERNEL_TMA, stream=stream.cuda_stream)
-    assert grid.info()["kernel"] == Bd.KERNEL_TMA
+        grid = Bd.Grid.from_workload(w, precision=Bd.FP32, kernel=Bd.KERNEL_TMA, stream=stream.cuda_stream,
+                                     tile=args.tile)
+    info = grid.info()
+    assert info["kernel"] == Bd.KERNEL_TMA
     # warm-up
     grid.step(max(args.warmup, 3))
     torch.cuda.synchronize()
@@ -270,6 +274,7 @@ def run_ours(args):
             "data": "synthetic",
             "config": {"workload": f"kelvin_helmholtz_{w.nx}x{w.ny}_fp32", "nx": w.nx, "ny": w.ny,
                        "gamma": w.gamma, "Pr": w.Pr, "cfl": 0.1, "precision": "fp32", "kernel": "tma",
+                       "tile": info["tile"],
                        "l2": "state 2 x %.2f GB > 129 MB L2, no flush" % (16 * cells * 4 / 1e9),
                        "parallelism": f"replicas{world}"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
@@ -334,8 +339,38 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def sweep_tiles(args):
+    """Time every compiled TMA variant on the workload (tuning aid)."""
+    import torch
+    from paper_1004_5442_gb300 import build as B
+    B.build()
+    from paper_1004_5442_gb300 import binding as Bd
+    from paper_1004_5442_gb300 import workloads as W
+    w = W.kelvin_helmholtz(n=args.n, nsteps=0)
+    for prec in (Bd.FP32, Bd.FP64):
+        for tile in (1, 2, 3, 4):
+            g = Bd.Grid.from_workload(w, precision=prec, kernel=Bd.KERNEL_TMA, tile=tile)
+            g.step(max(args.warmup, 3))
+            k = args.steps if prec == Bd.FP32 else max(5, args.steps // 10)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            g.step(k)
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / k
+            bpc = 128 if prec == Bd.FP32 else 256
+            print(json.dumps({"tile": tile, "precision": "fp32" if prec == Bd.FP32 else "fp64",
+                              "ms_per_step": ms, "cell_updates_per_s": w.cells / (ms * 1e-3),
+                              "hbm_gbs": bpc * w.cells / (ms * 1e-3) / 1e9}), flush=True)
+            g.close()
+
+
 def main():
     args = parse()
+    if args.sweep_tiles:
+        sweep_tiles(args)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:

@@ -75,6 +75,9 @@ typedef struct mrt_params {
     int bc_x, bc_y;     /* mrt_bc per axis */
     int precision;      /* mrt_precision of the stored f and of the arithmetic */
     int kernel;         /* mrt_kernel */
+    int tile;           /* TMA kernel variant: 0 = default for the precision,
+                           1..4 = ring depth / store path / CTAs-per-SM choices
+                           (see mrt_info); other values give MRT_EINVAL */
 } mrt_params;
 
 typedef struct mrt_grid mrt_grid;
@@ -118,10 +121,11 @@ mrt_status mrt_set_f(mrt_grid *g, const void *f, int on_device);
  * MRT_ETIMEOUT (a device-side wait ran out) or MRT_ECUDA. */
 mrt_status mrt_health(mrt_grid *g);
 
-/* Information about a grid: steps taken so far, and the element pitch and
- * plane stride of its padded device layout (for diagnostics). */
+/* Information about a grid: steps taken so far, the element pitch and plane
+ * stride of its padded device layout, the step kernel and TMA tile variant
+ * in use (any pointer may be NULL). */
 mrt_status mrt_info(const mrt_grid *g, long *steps, long *pitch, long *plane_stride,
-                    int *kernel_in_use);
+                    int *kernel_in_use, int *tile_in_use);
 
 /* Conserved totals sum_cells (rho, j_x, j_y, e) * dx * dy of a state held by
  * the caller on the device, computed without any allocation by the library.

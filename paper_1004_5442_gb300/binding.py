@@ -41,7 +41,7 @@ class Params(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("dx", ctypes.c_double),
                 ("dt", ctypes.c_double), ("gamma", ctypes.c_double), ("Pr", ctypes.c_double),
                 ("s", ctypes.c_double * 16), ("bc_x", ctypes.c_int), ("bc_y", ctypes.c_int),
-                ("precision", ctypes.c_int), ("kernel", ctypes.c_int)]
+                ("precision", ctypes.c_int), ("kernel", ctypes.c_int), ("tile", ctypes.c_int)]
 
 
 _lib = None
@@ -64,7 +64,8 @@ def load(path: str = LIB_PATH):
     L.mrt_set_f.argtypes = [vp, vp, ip]
     L.mrt_health.argtypes = [vp]
     L.mrt_info.argtypes = [vp, ctypes.POINTER(ctypes.c_long), ctypes.POINTER(ctypes.c_long),
-                           ctypes.POINTER(ctypes.c_long), ctypes.POINTER(ctypes.c_int)]
+                           ctypes.POINTER(ctypes.c_long), ctypes.POINTER(ctypes.c_int),
+                           ctypes.POINTER(ctypes.c_int)]
     L.mrt_destroy.argtypes = [vp]
     L.mrt_destroy.restype = None
     L.mrt_status_str.restype = ctypes.c_char_p
@@ -102,12 +103,13 @@ def _torch_stream():
 
 
 def make_params(nx, ny, dx, dt, gamma, s, bc_x=BC_PERIODIC, bc_y=BC_PERIODIC, precision=FP32,
-                Pr=0.0, kernel=KERNEL_AUTO) -> Params:
+                Pr=0.0, kernel=KERNEL_AUTO, tile=0) -> Params:
     p = Params()
     p.nx, p.ny, p.dx, p.dt, p.gamma, p.Pr = int(nx), int(ny), float(dx), float(dt), float(gamma), float(Pr)
     for k in range(16):
         p.s[k] = float(s[k])
     p.bc_x, p.bc_y, p.precision, p.kernel = int(bc_x), int(bc_y), int(precision), int(kernel)
+    p.tile = int(tile)
     return p
 
 
@@ -145,8 +147,8 @@ class Grid:
         self._h = h
 
     @classmethod
-    def from_workload(cls, w, precision=FP32, kernel=KERNEL_AUTO, stream=None):
-        p = make_params(w.nx, w.ny, w.dx, w.dt, w.gamma, w.s, w.bc_x, w.bc_y, precision, 0.0, kernel)
+    def from_workload(cls, w, precision=FP32, kernel=KERNEL_AUTO, stream=None, tile=0):
+        p = make_params(w.nx, w.ny, w.dx, w.dt, w.gamma, w.s, w.bc_x, w.bc_y, precision, 0.0, kernel, tile)
         return cls(p, w.rho, w.ux, w.uy, w.T, stream=stream)
 
     @property
@@ -185,11 +187,11 @@ class Grid:
 
     def info(self) -> dict:
         steps, pitch, plane = ctypes.c_long(), ctypes.c_long(), ctypes.c_long()
-        kern = ctypes.c_int()
+        kern, tile = ctypes.c_int(), ctypes.c_int()
         check(load().mrt_info(self._h, ctypes.byref(steps), ctypes.byref(pitch), ctypes.byref(plane),
-                              ctypes.byref(kern)))
+                              ctypes.byref(kern), ctypes.byref(tile)))
         return {"steps": steps.value, "pitch": pitch.value, "plane": plane.value,
-                "kernel": kern.value}
+                "kernel": kern.value, "tile": tile.value}
 
     def close(self) -> None:
         if getattr(self, "_h", None) is not None and self._h.value:

@@ -343,7 +343,9 @@ struct mrt_grid {
     double* macro_tmp = nullptr;     // 4 fields, for host readout
     long steps = 0;
     int kernel = MRT_KERNEL_DIRECT;  // in use
-    CUtensorMap maps[2];
+    CUtensorMap maps[2];       // loads: whole padded rows, box with halo
+    CUtensorMap maps_out[2];   // stores: x extent ends before the right ghost
+    int tile = 0;
     int tma_grid_x = 0, tma_grid_y = 0, rows_per_cta = 0;
     Coef<double> kd;
     Coef<float> kf;
@@ -367,17 +369,23 @@ static mrt_status make_maps(mrt_grid* g) {
     EncodeTiledFn enc = get_encode();
     if (!enc) return fail(MRT_ECUDA, "cuTensorMapEncodeTiled entry point unavailable");
     const int boxw = g->fp64 ? tma_boxw<double>() : tma_boxw<float>();
+    const CUtensorMapDataType dt = g->fp64 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
     for (int b = 0; b < 2; ++b) {
-        cuuint64_t dims[3] = {(cuuint64_t)g->L.pitch, (cuuint64_t)(g->L.ny + 2), 16};
-        cuuint64_t strides[2] = {(cuuint64_t)(g->L.pitch * g->elem),
-                                 (cuuint64_t)(g->L.plane * g->elem)};
-        cuuint32_t box[3] = {(cuuint32_t)boxw, 1, 16};
+        cuuint64_t strides[2] = {(cuuint64_t)(g->L.pitch * g->elem), (cuuint64_t)(g->L.plane * g->elem)};
         cuuint32_t estr[3] = {1, 1, 1};
-        CUresult r = enc(&g->maps[b], g->fp64 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
-                         3, g->f[b], dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+        cuuint64_t dims[3] = {(cuuint64_t)g->L.pitch, (cuuint64_t)(g->L.ny + 2), 16};
+        cuuint32_t box[3] = {(cuuint32_t)boxw, 1, 16};
+        CUresult r = enc(&g->maps[b], dt, 3, g->f[b], dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                          CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-        if (r != CUDA_SUCCESS) return fail(MRT_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+        if (r != CUDA_SUCCESS) return fail(MRT_ECUDA, "cuTensorMapEncodeTiled (load) failed (%d)", (int)r);
+        // store map: the kernel issues row stores only for whole 128-column
+        // strips, which end at or before column G + nx
+        cuuint64_t odims[3] = {(cuuint64_t)(g->L.G + g->L.nx), (cuuint64_t)(g->L.ny + 2), 16};
+        cuuint32_t obox[3] = {(cuuint32_t)TMA_W, 1, 16};
+        r = enc(&g->maps_out[b], dt, 3, g->f[b], odims, strides, obox, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) return fail(MRT_ECUDA, "cuTensorMapEncodeTiled (store) failed (%d)", (int)r);
     }
     return MRT_OK;
 }
@@ -397,6 +405,7 @@ static mrt_status validate(const mrt_params* p) {
     if (p->bc_y != MRT_BC_PERIODIC && p->bc_y != MRT_BC_FIXED_EQ) return fail(MRT_EINVAL, "bad bc_y");
     if (p->precision != MRT_FP32 && p->precision != MRT_FP64) return fail(MRT_EINVAL, "bad precision");
     if (p->kernel < MRT_KERNEL_AUTO || p->kernel > MRT_KERNEL_DIRECT) return fail(MRT_EINVAL, "bad kernel");
+    if (p->tile < 0 || p->tile >= NUM_TILES) return fail(MRT_EINVAL, "bad tile %d", p->tile);
     return MRT_OK;
 }
 
@@ -491,7 +500,8 @@ extern "C" mrt_status mrt_create(const mrt_params* params, const double* rho, co
     int parts = 0;
     if (kernel == MRT_KERNEL_TMA) {
         int occ = 0, sms = 0;
-        e = g->fp64 ? tma_occupancy<double>(&occ) : tma_occupancy<float>(&occ);
+        g->tile = params->tile ? params->tile : (g->fp64 ? default_tile<double>() : default_tile<float>());
+        e = g->fp64 ? tma_occupancy<double>(g->tile, &occ) : tma_occupancy<float>(g->tile, &occ);
         if (e != cudaSuccess) return bail(fail(MRT_ECUDA, "occupancy query: %s", cudaGetErrorString(e)));
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, g->device);
         if (occ < 1) occ = 1;
@@ -572,7 +582,8 @@ static mrt_status step_impl(mrt_grid* g, long nsteps) {
         cudaError_t e;
         int parts;
         if (g->kernel == MRT_KERNEL_TMA) {
-            e = launch_step_tma<T>(&g->maps[g->cur], a, g->tma_grid_x, g->tma_grid_y, totals, g->stream);
+            e = launch_step_tma<T>(g->tile, &g->maps[g->cur], &g->maps_out[g->cur ^ 1], a, g->tma_grid_x,
+                                   g->tma_grid_y, totals, g->stream);
             parts = g->tma_grid_x * g->tma_grid_y;
         } else {
             e = launch_step_direct<T>(a, totals, g->stream);
@@ -712,12 +723,13 @@ extern "C" mrt_status mrt_health(mrt_grid* g) {
 }
 
 extern "C" mrt_status mrt_info(const mrt_grid* g, long* steps, long* pitch, long* plane_stride,
-                               int* kernel_in_use) {
+                               int* kernel_in_use, int* tile_in_use) {
     if (!g) return fail(MRT_EINVAL, "grid is NULL");
     if (steps) *steps = g->steps;
     if (pitch) *pitch = g->L.pitch;
     if (plane_stride) *plane_stride = g->L.plane;
     if (kernel_in_use) *kernel_in_use = g->kernel;
+    if (tile_in_use) *tile_in_use = g->tile;
     return MRT_OK;
 }
 

@@ -114,9 +114,18 @@ __device__ __forceinline__ void conserved_moments(const T f[NV], T& rho, T& jx, 
     e = (T)kW(0) * S[0] + (T)kW(1) * S[1] + (T)kW(2) * S[2] + (T)kW(3) * S[3];
 }
 
+template <class T>
+__device__ __forceinline__ T recip(T x) { return (T)1 / x; }
+template <>
+__device__ __forceinline__ float recip<float>(float x) { return __fdividef(1.0f, x); }
+
 // One cell of one time step (Eq. 3, forward Euler + Lax-Wendroff):
 // reads the stencil through F(i, pos), writes f^{n+1} to out and returns
 // the cell's input rho and P for the health check.
+//
+// The Lax-Wendroff terms are accumulated as multiply-adds of neighbour
+// differences onto the collision increment, so a uniform state is left
+// exactly unchanged by the advection in any precision.
 template <class T, class Fetch>
 __device__ __forceinline__ void cell_update(const Fetch& F, const Coef<T>& k, T out[NV],
                                             T& rho_in, T& P_in) {
@@ -136,32 +145,29 @@ __device__ __forceinline__ void cell_update(const Fetch& F, const Coef<T>& k, T 
         if (g < 2) { Dx[g] = d02; Dy[g] = d13; }
         else { Dx[g] = d02 - d13; Dy[g] = d02 + d13; }
     }
-    const T U0 = (T)kU(0), U1 = (T)kU(1), U2 = (T)kU(2), U3 = (T)kU(3);
+    // eta^2 = 25/4 on group 0 only, so W_g = V_g except W_0 = V_0 + 25/4.
+    constexpr double E2 = 6.25;
     const T m1 = (S[0] + S[1]) + (S[2] + S[3]);
-    const T m4 = (T)kW(0) * S[0] + (T)kW(1) * S[1] + (T)kW(2) * S[2] + (T)kW(3) * S[3];
     const T m5 = (T)kV(0) * S[0] + (T)kV(1) * S[1] + (T)kV(2) * S[2] + (T)kV(3) * S[3];
+    const T m4 = (T)E2 * S[0] + m5;
     const T m14 = (T)(kV(0) * kW(0)) * S[0] + (T)(kV(1) * kW(1)) * S[1]
                 + (T)(kV(2) * kW(2)) * S[2] + (T)(kV(3) * kW(3)) * S[3];
-    const T m2 = U0 * Dx[0] + U1 * Dx[1] + U2 * Dx[2] + U3 * Dx[3];
-    const T m8 = (T)(kU(0) * kW(0)) * Dx[0] + (T)(kU(1) * kW(1)) * Dx[1]
-               + (T)(kU(2) * kW(2)) * Dx[2] + (T)(kU(3) * kW(3)) * Dx[3];
-    const T m10 = (T)(kU(0) * kV(0)) * Dx[0] + (T)(kU(1) * kV(1)) * Dx[1]
-                + (T)(kU(2) * kV(2)) * Dx[2] + (T)(kU(3) * kV(3)) * Dx[3];
-    const T m12 = (T)(kU(0) * kV(0)) * Dx[0] + (T)(kU(1) * kV(1)) * Dx[1];
-    const T m3 = U0 * Dy[0] + U1 * Dy[1] + U2 * Dy[2] + U3 * Dy[3];
-    const T m9 = (T)(kU(0) * kW(0)) * Dy[0] + (T)(kU(1) * kW(1)) * Dy[1]
-               + (T)(kU(2) * kW(2)) * Dy[2] + (T)(kU(3) * kW(3)) * Dy[3];
-    const T m11 = (T)(kU(0) * kV(0)) * Dy[0] + (T)(kU(1) * kV(1)) * Dy[1]
-                + (T)(kU(2) * kV(2)) * Dy[2] + (T)(kU(3) * kV(3)) * Dy[3];
-    const T m13 = -((T)(kU(0) * kV(0)) * Dy[0] + (T)(kU(1) * kV(1)) * Dy[1]);
-    const T m6 = (T)kV(0) * QX[0] + (T)kV(1) * QX[1];
-    const T m16 = (T)(kV(0) * kW(0)) * QX[0] + (T)(kV(1) * kW(1)) * QX[1];
-    const T m7 = (T)(0.5 * kV(2)) * QX[2] + (T)(0.5 * kV(3)) * QX[3];
-    const T m15 = (T)(0.5 * kV(2) * kW(2)) * QX[2] + (T)(0.5 * kV(3) * kW(3)) * QX[3];
+    const T m2 = (T)kU(0) * Dx[0] + (T)kU(1) * Dx[1] + (T)kU(2) * Dx[2] + (T)kU(3) * Dx[3];
+    const T m12 = (T)(kU(1) * kV(1)) * Dx[1] + Dx[0];                 // u^3 on the axis groups
+    const T m10 = (T)(kU(3) * kV(3)) * Dx[3] + ((T)(kU(2) * kV(2)) * Dx[2] + m12);
+    const T m8 = (T)E2 * Dx[0] + m10;
+    const T m3 = (T)kU(0) * Dy[0] + (T)kU(1) * Dy[1] + (T)kU(2) * Dy[2] + (T)kU(3) * Dy[3];
+    const T n13 = (T)(kU(1) * kV(1)) * Dy[1] + Dy[0];                 // -m13
+    const T m11 = (T)(kU(3) * kV(3)) * Dy[3] + ((T)(kU(2) * kV(2)) * Dy[2] + n13);
+    const T m9 = (T)E2 * Dy[0] + m11;
+    const T m6 = (T)kV(1) * QX[1] + QX[0];
+    const T m16 = (T)(kV(1) * kW(1)) * QX[1] + (T)(kV(0) * kW(0)) * QX[0];
+    const T m7 = (T)(0.5 * kV(3)) * QX[3] + (T)(0.5 * kV(2)) * QX[2];
+    const T m15 = (T)(0.5 * kV(3) * kW(3)) * QX[3] + (T)(0.5 * kV(2) * kW(2)) * QX[2];
 
     // ---- equilibrium moments (Appendix), P = (e - j^2/rho)/b, R = 1 ------
     const T rho = m1, jx = m2, jy = m3, e = m4;
-    const T rinv = (T)1 / rho;
+    const T rinv = recip<T>(rho);
     const T ux = jx * rinv, uy = jy * rinv;
     const T kx = jx * ux, ky = jy * uy;
     const T j2r = kx + ky;                       // j^2 / rho
@@ -176,11 +182,11 @@ __device__ __forceinline__ void cell_update(const Fetch& F, const Coef<T>& k, T 
     const T h10 = twoP + q5;                     // 4P + j^2/rho
     const T q10 = h10 * ux, q11 = h10 * uy;
     const T q12 = (twoP + q6) * ux;
-    const T q13 = (q6 - twoP) * uy;
+    const T nq13 = (twoP - q6) * uy;             // -q13
     const T u2 = ux * ux + uy * uy;
-    const T q14 = k.c14a * P * Tt + k.c14b * Tt * j2r + j2r * u2;
+    const T q14 = Tt * (k.c14a * P + k.c14b * j2r) + j2r * u2;
     const T g15 = k.c15 * P + j2r;
-    const T q15 = g15 * ux * uy;
+    const T q15 = g15 * (ux * uy);
     const T q16 = g15 * (ux * ux - uy * uy);
     rho_in = rho;
     P_in = P;
@@ -189,52 +195,71 @@ __device__ __forceinline__ void cell_update(const Fetch& F, const Coef<T>& k, T 
     const T d5 = k.sig[0] * (m5 - q5), d6 = k.sig[1] * (m6 - q6), d7 = k.sig[2] * (m7 - q7);
     const T d8 = k.sig[3] * (m8 - q8), d9 = k.sig[4] * (m9 - q9);
     const T d10 = k.sig[5] * (m10 - q10), d11 = k.sig[6] * (m11 - q11);
-    const T d12 = k.sig[7] * (m12 - q12), d13 = k.sig[8] * (m13 - q13);
+    const T d12 = k.sig[7] * (m12 - q12), nd13 = k.sig[8] * (n13 - nq13);   // -Delta_13
     const T d14 = k.sig[9] * (m14 - q14), d15 = k.sig[10] * (m15 - q15);
     const T d16 = k.sig[11] * (m16 - q16);
 
-    // ---- inverse blocks (scaled) and inverse butterflies: dt*Omega -------
+    // ---- inverse blocks (scaled), inverse butterflies, then advection ----
 #pragma unroll
     for (int g = 0; g < 4; ++g) {
         const T cS = k.kS[g][0] * d5 + k.kS[g][1] * d14;
         const T cX = k.kD[g][0] * d8 + k.kD[g][1] * d10 + k.kD[g][2] * d12;
-        const T cY = k.kD[g][0] * d9 + k.kD[g][1] * d11 - k.kD[g][2] * d13;
-        T om[4];
+        const T cY = k.kD[g][0] * d9 + k.kD[g][1] * d11 + k.kD[g][2] * nd13;
+        const T p = k.lwp[g], qq = k.lwq[g];
+        const int i0 = 4 * g;
         if (g < 2) {
             const T cQ = k.kQ[g][0] * d6 + k.kQ[g][1] * d16;
-            om[0] = cS + cX + cQ;
-            om[2] = cS - cX + cQ;
-            om[1] = cS + cY - cQ;
-            om[3] = cS - cY - cQ;
+            const T sp = cS + cQ, sm = cS - cQ;
+            // +x: p on x-1, q on x+1; -x mirrored; +y / -y likewise along y
+            {
+                const T fc = f[i0 + 0];
+                T t = qq * (F(i0 + 0, XP) - fc) + (sp + cX);
+                out[i0 + 0] = fc + (p * (F(i0 + 0, XM) - fc) + t);
+            }
+            {
+                const T fc = f[i0 + 2];
+                T t = p * (F(i0 + 2, XP) - fc) + (sp - cX);
+                out[i0 + 2] = fc + (qq * (F(i0 + 2, XM) - fc) + t);
+            }
+            {
+                const T fc = f[i0 + 1];
+                T t = qq * (F(i0 + 1, YP) - fc) + (sm + cY);
+                out[i0 + 1] = fc + (p * (F(i0 + 1, YM) - fc) + t);
+            }
+            {
+                const T fc = f[i0 + 3];
+                T t = p * (F(i0 + 3, YP) - fc) + (sm - cY);
+                out[i0 + 3] = fc + (qq * (F(i0 + 3, YM) - fc) + t);
+            }
         } else {
             const T cXY = k.kX[g - 2][0] * d7 + k.kX[g - 2][1] * d15;
-            om[0] = cS + cX + cY + cXY;
-            om[1] = cS - cX + cY - cXY;
-            om[2] = cS - cX - cY + cXY;
-            om[3] = cS + cX - cY - cXY;
-        }
-        // ---- Lax-Wendroff advection along each moving axis + Euler ------
-        const T p = k.lwp[g], qq = k.lwq[g];
-#pragma unroll
-        for (int m = 0; m < 4; ++m) {
-            const int i = 4 * g + m;
-            const T fc = f[i];
-            T adv;
-            if (g < 2) {
-                // +x: p on x-1; -x: p on x+1; +y: p on y-1; -y: p on y+1
-                if (m == 0) adv = p * (F(i, XM) - fc) + qq * (F(i, XP) - fc);
-                else if (m == 2) adv = qq * (F(i, XM) - fc) + p * (F(i, XP) - fc);
-                else if (m == 1) adv = p * (F(i, YM) - fc) + qq * (F(i, YP) - fc);
-                else adv = qq * (F(i, YM) - fc) + p * (F(i, YP) - fc);
-            } else {
-                const bool posx = (m == 0 || m == 3), posy = (m == 0 || m == 1);
-                const T ax = posx ? p * (F(i, XM) - fc) + qq * (F(i, XP) - fc)
-                                  : qq * (F(i, XM) - fc) + p * (F(i, XP) - fc);
-                const T ay = posy ? p * (F(i, YM) - fc) + qq * (F(i, YP) - fc)
-                                  : qq * (F(i, YM) - fc) + p * (F(i, YP) - fc);
-                adv = ax + ay;
+            const T t1 = cS + cXY, t2 = cS - cXY, s1 = cX + cY, s2 = cX - cY;
+            // |c_x| = |c_y| on a diagonal: pair the x and y neighbours that
+            // carry the same weight, (a + b - 2 f) is exact for a uniform state
+            {   // (+,+): p on x-1, y-1; q on x+1, y+1
+                const T fc = f[i0 + 0];
+                const T a = (F(i0 + 0, XM) + F(i0 + 0, YM)) - (fc + fc);
+                const T b = (F(i0 + 0, XP) + F(i0 + 0, YP)) - (fc + fc);
+                out[i0 + 0] = fc + (p * a + (qq * b + (t1 + s1)));
             }
-            out[i] = fc + (adv + om[m]);
+            {   // (-,+): q on x-1, p on x+1; p on y-1, q on y+1
+                const T fc = f[i0 + 1];
+                const T a = (F(i0 + 1, XP) + F(i0 + 1, YM)) - (fc + fc);
+                const T b = (F(i0 + 1, XM) + F(i0 + 1, YP)) - (fc + fc);
+                out[i0 + 1] = fc + (p * a + (qq * b + (t2 - s2)));
+            }
+            {   // (-,-): q on x-1, y-1; p on x+1, y+1
+                const T fc = f[i0 + 2];
+                const T a = (F(i0 + 2, XP) + F(i0 + 2, YP)) - (fc + fc);
+                const T b = (F(i0 + 2, XM) + F(i0 + 2, YM)) - (fc + fc);
+                out[i0 + 2] = fc + (p * a + (qq * b + (t1 - s1)));
+            }
+            {   // (+,-): p on x-1, q on x+1; q on y-1, p on y+1
+                const T fc = f[i0 + 3];
+                const T a = (F(i0 + 3, XM) + F(i0 + 3, YP)) - (fc + fc);
+                const T b = (F(i0 + 3, XP) + F(i0 + 3, YM)) - (fc + fc);
+                out[i0 + 3] = fc + (p * a + (qq * b + (t2 + s2)));
+            }
         }
     }
 }

@@ -9,10 +9,12 @@
 //    halo on each side for the x neighbours) from HBM into a ring of shared
 //    memory slots with 3-D cp.async.bulk.tensor loads completing on
 //    mbarriers; every thread computes one cell per row from rows r-1, r, r+1
-//    of the ring and stores its 16 outputs with coalesced row stores.  Each
-//    f value is read from HBM once (halo columns and the two chunk-boundary
-//    rows are L2 hits), so the traffic is the 16 reads + 16 writes per cell
-//    of the algorithm.
+//    of the ring.  The 16 outputs of a row go either straight to global
+//    memory (one coalesced store per plane and thread) or into a shared
+//    memory row that the elected thread writes back with one 3-D TMA store.
+//    Each f value is read from HBM once (halo columns and the two
+//    chunk-boundary rows are L2 hits), so the traffic is the 16 reads + 16
+//    writes per cell of the algorithm.
 //  * step_direct: one thread per cell reading its stencil from global memory;
 //    the simple form, used for cross-checks.
 //
@@ -166,19 +168,37 @@ __device__ __forceinline__ void store_cell(T* __restrict__ out, const Layout& L,
     }
 }
 
+__device__ __forceinline__ void tma_store_3d(const CUtensorMap* map, const void* src, int x, int y, int z) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.global.shared::cta.bulk_group [%0, {%1, %2, %3}], [%4];" ::"l"(
+            reinterpret_cast<uint64_t>(map)),
+        "r"(x), "r"(y), "r"(z), "r"(smem_u32(src))
+        : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_read_all() {
+    asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+}
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+__device__ __forceinline__ void fence_async_shared() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
 // --------------------------------------------------------------------------
 // TMA-staged strip kernel.
 // --------------------------------------------------------------------------
-template <class T, bool TOTALS>
-__global__ void __launch_bounds__(TMA_W) step_tma(const __grid_constant__ CUtensorMap map_in,
-                                                  const StepArgs<T> a) {
-    constexpr int NS = tma_stages<T>();
+template <class T, bool TOTALS, int NS, bool TSTORE, int MINB>
+__global__ void __launch_bounds__(TMA_W, MINB) step_tma(const __grid_constant__ CUtensorMap map_in,
+                                                        const __grid_constant__ CUtensorMap map_out,
+                                                        const StepArgs<T> a) {
     constexpr int HALO = tma_halo<T>();
     constexpr int BOXW = tma_boxw<T>();
     constexpr uint32_t SLOT_BYTES = (uint32_t)tma_slot_bytes<T>();
+    constexpr uint32_t OUT_BYTES = TSTORE ? (uint32_t)tma_out_slot_bytes<T>() : 0u;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     T* ring = reinterpret_cast<T*>(smem_raw);
-    uint64_t* full = reinterpret_cast<uint64_t*>(smem_raw + NS * SLOT_BYTES);
+    T* outbuf = reinterpret_cast<T*>(smem_raw + NS * SLOT_BYTES);
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem_raw + NS * SLOT_BYTES + 2 * OUT_BYTES);
 
     const Layout& L = a.L;
     const int tid = threadIdx.x;
@@ -189,7 +209,12 @@ __global__ void __launch_bounds__(TMA_W) step_tma(const __grid_constant__ CUtens
     const int nload = nrows + 2;           // local rows 0..nrows+1 = padded rows y0..y0+nrows+1
     const int x = x0 + tid;
     const bool active = x < L.nx;
-    const int tma_x = L.G + x0 - HALO;     // 16-byte aligned start column of the box
+    const int tma_x = L.G + x0 - HALO;     // 16-byte aligned start column of the load box
+    // Row stores by TMA only for whole strips: a TMA store that ends inside a
+    // 16-byte chunk can write that whole chunk, which for a ragged last strip
+    // holds the right ghost column.  The ragged strip copies its staged row
+    // out per thread instead.
+    const bool tstore = TSTORE && (x0 + TMA_W <= L.nx);
 
     if (tid == 0) {
         for (int s = 0; s < NS; ++s) mbar_init(&full[s], 1);
@@ -226,6 +251,7 @@ __global__ void __launch_bounds__(TMA_W) step_tma(const __grid_constant__ CUtens
         if (tid == 0) {
             for (int l = waited0; l < issued; ++l)
                 mbar_wait_bounded(&full[l % NS], (uint32_t)((l / NS) & 1));
+            if (tstore) bulk_wait_all();
             atomicOr(a.flag, FLAG_TIMEOUT);
         }
     };
@@ -233,6 +259,8 @@ __global__ void __launch_bounds__(TMA_W) step_tma(const __grid_constant__ CUtens
 
 #pragma unroll 1
     for (int r = 1; r <= nrows; ++r) {
+        const int y = y0 + r - 1;
+        T* ob = outbuf + (size_t)(r & 1) * NV * TMA_W;
         if (active) {
             const T* sm = ring + (size_t)((r - 1) % NS) * NV * BOXW;
             const T* sc = ring + (size_t)(r % NS) * NV * BOXW;
@@ -249,19 +277,33 @@ __global__ void __launch_bounds__(TMA_W) step_tma(const __grid_constant__ CUtens
             T out[NV];
             T rho, P;
             cell_update<T>(F, a.k, out, rho, P);
-            bad |= !healthy(rho, P);
-            const int y = y0 + r - 1;
-            store_cell<T>(a.out, L, a.per_x, a.per_y, x, y, out);
+            bad |= !(rho > (T)0) | !(P > (T)0);
+            if (TSTORE) {
+#pragma unroll
+                for (int i = 0; i < NV; ++i) ob[i * TMA_W + tid] = out[i];
+            } else {
+                store_cell<T>(a.out, L, a.per_x, a.per_y, x, y, out);
+            }
             if (TOTALS) {
                 T q0, q1, q2, q3;
                 conserved_moments<T>(out, q0, q1, q2, q3);
                 acc[0].add(q0); acc[1].add(q1); acc[2].add(q2); acc[3].add(q3);
             }
         }
+        if (tstore) {
+            fence_async_shared();              // make this thread's row visible to the TMA engine
+            if (tid == 0) bulk_wait_read_all();  // the store from the other out slot has read it
+        }
         ok = (r + 2 < nload) ? wait_row(r + 2) : true;
-        // every thread is done with slot (r-1) % NS after this barrier
+        // every thread is done with slot (r-1) % NS, and the out row is complete
         if (__syncthreads_or(!ok)) { drain(); return; }
         if (tid == 0) {
+            if (tstore) {
+                tma_store_3d(&map_out, ob, L.G + x0, y + 1, 0);
+                if (a.per_y && y == 0) tma_store_3d(&map_out, ob, L.G + x0, L.ny + 1, 0);
+                if (a.per_y && y == L.ny - 1) tma_store_3d(&map_out, ob, L.G + x0, 0, 0);
+                bulk_commit();
+            }
             const int l = r - 1 + NS;
             if (l < nload) {
                 const int s = l % NS;
@@ -270,7 +312,29 @@ __global__ void __launch_bounds__(TMA_W) step_tma(const __grid_constant__ CUtens
                 issued = l + 1;
             }
         }
+        // after the elected thread has queued its copies
+        if (TSTORE) {
+            if (!tstore && active) {
+                // ragged strip: this thread's column of the staged row, plus
+                // the periodic ghost rows
+                const long c0 = (long)(y + 1) * L.pitch + L.G + x;
+#pragma unroll 4
+                for (int i = 0; i < NV; ++i) {
+                    const T v = ob[i * TMA_W + tid];
+                    a.out[i * L.plane + c0] = v;
+                    if (a.per_y && y == 0) a.out[i * L.plane + (long)(L.ny + 1) * L.pitch + L.G + x] = v;
+                    if (a.per_y && y == L.ny - 1) a.out[i * L.plane + L.G + x] = v;
+                }
+            }
+            if (a.per_x && (x == 0 || x == L.nx - 1)) {
+                // periodic ghost columns are single values: plain stores
+                const long gc = (long)(y + 1) * L.pitch + (x == 0 ? L.G + L.nx : L.G - 1);
+#pragma unroll 4
+                for (int i = 0; i < NV; ++i) a.out[i * L.plane + gc] = ob[i * TMA_W + tid];
+            }
+        }
     }
+    if (tstore && tid == 0) bulk_wait_all();
 
     if (__syncthreads_or(bad) && tid == 0) atomicOr(a.flag, FLAG_UNSTABLE);
     if (TOTALS) {
@@ -319,33 +383,55 @@ __global__ void __launch_bounds__(DIR_BX* DIR_BY) step_direct(const StepArgs<T> 
     }
 }
 
+template <class T, int NS, bool TSTORE, int MINB>
+struct TmaKernels {
+    static cudaError_t launch(const CUtensorMap* mi, const CUtensorMap* mo, const StepArgs<T>& a, dim3 grid,
+                              size_t smem, bool totals, cudaStream_t st) {
+        if (totals)
+            step_tma<T, true, NS, TSTORE, MINB><<<grid, TMA_W, smem, st>>>(*mi, *mo, a);
+        else
+            step_tma<T, false, NS, TSTORE, MINB><<<grid, TMA_W, smem, st>>>(*mi, *mo, a);
+        return cudaGetLastError();
+    }
+    static cudaError_t occupancy(size_t smem, int* occ) {
+        cudaError_t e;
+        if ((e = cudaFuncSetAttribute(step_tma<T, true, NS, TSTORE, MINB>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
+            return e;
+        if ((e = cudaFuncSetAttribute(step_tma<T, false, NS, TSTORE, MINB>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
+            return e;
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, step_tma<T, false, NS, TSTORE, MINB>, TMA_W, smem);
+    }
+};
+
+// FP64 rings are capped at 4 rows (16.9 KB per row).
+template <class T, int NS> constexpr int ring_depth() { return sizeof(T) == 8 && NS > 4 ? 4 : NS; }
+
+template <class T, class Fn>
+cudaError_t with_tile(int tile, Fn&& fn) {
+    switch (tile) {
+        case 1: return fn(TmaKernels<T, ring_depth<T, 6>(), false, 4>());
+        case 2: return fn(TmaKernels<T, ring_depth<T, 4>(), true, (sizeof(T) == 8 ? 2 : 4)>());
+        case 3: return fn(TmaKernels<T, ring_depth<T, 6>(), true, (sizeof(T) == 8 ? 2 : 3)>());
+        case 4: return fn(TmaKernels<T, ring_depth<T, 5>(), true, (sizeof(T) == 8 ? 2 : 3)>());
+        default: return cudaErrorInvalidValue;
+    }
+}
+
 }  // namespace
 
 template <class T>
-cudaError_t launch_step_tma(const CUtensorMap* map_in, const StepArgs<T>& a, int grid_x,
-                            int grid_y, bool totals, cudaStream_t st) {
-    const size_t smem = tma_smem_bytes<T>();
-    dim3 grid(grid_x, grid_y), block(TMA_W);
-    if (totals) {
-        step_tma<T, true><<<grid, block, smem, st>>>(*map_in, a);
-    } else {
-        step_tma<T, false><<<grid, block, smem, st>>>(*map_in, a);
-    }
-    return cudaGetLastError();
+cudaError_t launch_step_tma(int tile, const CUtensorMap* map_in, const CUtensorMap* map_out, const StepArgs<T>& a,
+                            int grid_x, int grid_y, bool totals, cudaStream_t st) {
+    const size_t smem = tma_smem_bytes<T>(tile);
+    return with_tile<T>(tile, [&](auto k) { return k.launch(map_in, map_out, a, dim3(grid_x, grid_y), smem, totals, st); });
 }
 
 template <class T>
-cudaError_t tma_occupancy(int* blocks_per_sm) {
-    const size_t smem = tma_smem_bytes<T>();
-    cudaError_t e;
-    if ((e = cudaFuncSetAttribute(step_tma<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)smem)) != cudaSuccess)
-        return e;
-    if ((e = cudaFuncSetAttribute(step_tma<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)smem)) != cudaSuccess)
-        return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, step_tma<T, false>,
-                                                         TMA_W, smem);
+cudaError_t tma_occupancy(int tile, int* blocks_per_sm) {
+    const size_t smem = tma_smem_bytes<T>(tile);
+    return with_tile<T>(tile, [&](auto k) { return k.occupancy(smem, blocks_per_sm); });
 }
 
 template <class T>
@@ -366,14 +452,14 @@ cudaError_t launch_step_direct(const StepArgs<T>& a, bool totals, cudaStream_t s
     return cudaGetLastError();
 }
 
-template cudaError_t launch_step_tma<float>(const CUtensorMap*, const StepArgs<float>&, int, int,
-                                            bool, cudaStream_t);
-template cudaError_t launch_step_tma<double>(const CUtensorMap*, const StepArgs<double>&, int, int,
-                                             bool, cudaStream_t);
+template cudaError_t launch_step_tma<float>(int, const CUtensorMap*, const CUtensorMap*,
+                                            const StepArgs<float>&, int, int, bool, cudaStream_t);
+template cudaError_t launch_step_tma<double>(int, const CUtensorMap*, const CUtensorMap*,
+                                             const StepArgs<double>&, int, int, bool, cudaStream_t);
 template cudaError_t launch_step_direct<float>(const StepArgs<float>&, bool, cudaStream_t);
 template cudaError_t launch_step_direct<double>(const StepArgs<double>&, bool, cudaStream_t);
-template cudaError_t tma_occupancy<float>(int*);
-template cudaError_t tma_occupancy<double>(int*);
+template cudaError_t tma_occupancy<float>(int, int*);
+template cudaError_t tma_occupancy<double>(int, int*);
 template void direct_grid<float>(const Layout&, dim3*, dim3*);
 template void direct_grid<double>(const Layout&, dim3*, dim3*);
 

@@ -11,8 +11,8 @@ def run_oracle(w, nsteps=None):
     return g
 
 
-def run_gpu(w, precision, kernel=Bd.KERNEL_AUTO, nsteps=None):
-    grid = Bd.Grid.from_workload(w, precision=precision, kernel=kernel)
+def run_gpu(w, precision, kernel=Bd.KERNEL_AUTO, nsteps=None, tile=0):
+    grid = Bd.Grid.from_workload(w, precision=precision, kernel=kernel, tile=tile)
     grid.step(w.nsteps if nsteps is None else nsteps)
     return grid
 

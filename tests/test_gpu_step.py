@@ -21,6 +21,8 @@ from _parity import assert_parity, field_errors, run_gpu, run_oracle
 pytestmark = pytest.mark.gpu
 
 KERNELS = [Bd.KERNEL_TMA, Bd.KERNEL_DIRECT]
+# (kernel, tile): every compiled TMA variant and the direct kernel
+VARIANTS = [(Bd.KERNEL_TMA, t) for t in (1, 2, 3, 4)] + [(Bd.KERNEL_DIRECT, 0)]
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -35,21 +37,22 @@ def _cuda():
 # --------------------------------------------------------------------------
 # Raw state after one step
 # --------------------------------------------------------------------------
-@pytest.mark.parametrize("kernel", KERNELS)
+@pytest.mark.parametrize("kernel,tile", VARIANTS)
 @pytest.mark.parametrize("bcx,bcy", [(0, 0), (1, 0), (0, 1), (1, 1)])
-def test_one_step_raw_state_fp64(kernel, bcx, bcy):
+def test_one_step_raw_state_fp64(kernel, tile, bcx, bcy):
     w = W.random_smooth(300, 37, seed=4, amp=0.1, bc_x=bcx, bc_y=bcy)
     g = run_oracle(w, 1)
-    with run_gpu(w, Bd.FP64, kernel, nsteps=1) as grid:
+    with run_gpu(w, Bd.FP64, kernel, nsteps=1, tile=tile) as grid:
         f = grid.get_f()
     scale = np.max(np.abs(g.f))
     assert np.max(np.abs(f - g.f)) <= 1e-13 * scale
 
 
-@pytest.mark.parametrize("kernel", KERNELS)
-def test_one_step_raw_state_fp32(kernel):
-    w = W.random_smooth(300, 37, seed=4, amp=0.1, bc_x=1)
-    with Bd.Grid.from_workload(w, precision=Bd.FP32, kernel=kernel) as grid:
+@pytest.mark.parametrize("kernel,tile", VARIANTS)
+@pytest.mark.parametrize("bcx,bcy", [(0, 0), (1, 1)])
+def test_one_step_raw_state_fp32(kernel, tile, bcx, bcy):
+    w = W.random_smooth(300, 37, seed=4, amp=0.1, bc_x=bcx, bc_y=bcy)
+    with Bd.Grid.from_workload(w, precision=Bd.FP32, kernel=kernel, tile=tile) as grid:
         f0 = grid.get_f().astype(np.float64)
         grid.step(1)
         f1 = grid.get_f().astype(np.float64)
@@ -62,14 +65,15 @@ def test_one_step_raw_state_fp32(kernel):
 # --------------------------------------------------------------------------
 # Macroscopic parity over many steps
 # --------------------------------------------------------------------------
-@pytest.mark.parametrize("kernel", KERNELS)
-def test_smooth_periodic_parity(kernel):
+@pytest.mark.parametrize("kernel,tile", VARIANTS)
+def test_smooth_periodic_parity(kernel, tile):
     w = W.random_smooth(300, 37, seed=9, amp=0.1, nsteps=200)
     want = oracle.macro(run_oracle(w))
-    with run_gpu(w, Bd.FP64, kernel) as grid:
+    with run_gpu(w, Bd.FP64, kernel, tile=tile) as grid:
         assert_parity(grid.macro(), want, linf=1e-12, label="fp64")
-    with run_gpu(w, Bd.FP32, kernel) as grid:
-        assert_parity(grid.macro(), want, linf=1e-5, l1=1e-5, label="fp32")
+    with run_gpu(w, Bd.FP32, kernel, tile=tile) as grid:
+        errs = assert_parity(grid.macro(), want, linf=1e-5, l1=1e-5, label="fp32")
+    print("fp32 smooth 300x37 200 steps", kernel, tile, errs)
 
 
 def test_sod_tube_parity():
@@ -79,7 +83,8 @@ def test_sod_tube_parity():
     with run_gpu(w, Bd.FP64) as grid:
         assert_parity(grid.macro(), want, linf=1e-10, label="fp64")
     with run_gpu(w, Bd.FP32) as grid:
-        assert_parity(grid.macro(), want, l1=1e-4, label="fp32")
+        errs = assert_parity(grid.macro(), want, l1=1e-4, label="fp32")
+    print("fp32 sod", errs)
 
 
 @pytest.fixture(scope="module")
@@ -97,9 +102,10 @@ def test_strong_shock_parity(strong_shock_oracle, prec):
         got = grid.macro()
         tot = grid.totals()
     if prec == Bd.FP64:
-        assert_parity(got, want, linf=1e-9, label="fp64")
+        errs = assert_parity(got, want, linf=1e-9, label="fp64")
     else:
-        assert_parity(got, want, l1=1e-4, label="fp32")
+        errs = assert_parity(got, want, l1=1e-4, label="fp32")
+    print("strong shock", prec, errs)
     L, R = w.extra["left"], w.extra["right"]
     st = riemann.star_state(L, R, w.gamma)
     x = (np.arange(w.nx) + 0.5) * w.dx
@@ -112,14 +118,16 @@ def test_kelvin_helmholtz_reduced_parity():
     w = W.kelvin_helmholtz(n=256, nsteps=1000)
     want = oracle.macro(run_oracle(w))
     with run_gpu(w, Bd.FP32) as grid:
-        assert_parity(grid.macro(), want, linf=1e-5, l1=1e-5, label="kh fp32")
+        errs = assert_parity(grid.macro(), want, linf=1e-5, l1=1e-5, label="kh fp32")
+    print("fp32 kh 256^2 1000 steps", errs)
 
 
 def test_vortex_parity():
     w = W.smooth_vortex(n=128, nsteps=500)
     want = oracle.macro(run_oracle(w))
     with run_gpu(w, Bd.FP32) as grid:
-        assert_parity(grid.macro(), want, linf=1e-5, l1=1e-5, label="vortex fp32")
+        errs = assert_parity(grid.macro(), want, linf=1e-5, l1=1e-5, label="vortex fp32")
+    print("fp32 vortex 128^2 500 steps", errs)
     with run_gpu(w, Bd.FP64) as grid:
         assert_parity(grid.macro(), want, linf=1e-12, label="vortex fp64")
 
@@ -129,11 +137,11 @@ def test_vortex_parity():
 def test_edge_sizes(nx, ny, bcx, bcy):
     w = W.random_smooth(nx, ny, seed=nx + ny, amp=0.05, bc_x=bcx, bc_y=bcy, nsteps=15)
     want = oracle.macro(run_oracle(w))
-    for kernel in KERNELS:
-        with run_gpu(w, Bd.FP64, kernel) as grid:
-            assert_parity(grid.macro(), want, linf=1e-12, label=f"fp64 k{kernel}")
-        with run_gpu(w, Bd.FP32, kernel) as grid:
-            assert_parity(grid.macro(), want, linf=1e-5, label=f"fp32 k{kernel}")
+    for kernel, tile in VARIANTS:
+        with run_gpu(w, Bd.FP64, kernel, tile=tile) as grid:
+            assert_parity(grid.macro(), want, linf=1e-12, label=f"fp64 k{kernel} t{tile}")
+        with run_gpu(w, Bd.FP32, kernel, tile=tile) as grid:
+            assert_parity(grid.macro(), want, linf=1e-5, label=f"fp32 k{kernel} t{tile}")
 
 
 def test_device_inputs_match_host_inputs():
@@ -247,7 +255,7 @@ def test_full_size_kh_sampled_windows():
     corners = [(0, 0), (w.ny - n, w.nx - n), (0, w.nx - n), (w.ny - n, 0), (2000, 128 * 16 - 24)]
     wins = corners + [(int(rng.integers(0, w.ny - n)), int(rng.integers(0, w.nx - n))) for _ in range(7)]
     with Bd.Grid.from_workload(w, precision=Bd.FP32, kernel=Bd.KERNEL_TMA) as grid:
-        assert grid.info()["kernel"] == Bd.KERNEL_TMA
+        assert grid.info()["kernel"] == Bd.KERNEL_TMA and grid.info()["tile"] == 2
         grid.step(3)
         f3 = grid.get_f()
         grid.step(1)
