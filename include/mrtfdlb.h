@@ -127,6 +127,42 @@ mrt_status mrt_health(mrt_grid *g);
 mrt_status mrt_info(const mrt_grid *g, long *steps, long *pitch, long *plane_stride,
                     int *kernel_in_use, int *tile_in_use);
 
+/* Reverse mode (adjoint) of the method, for gradients of a loss L(rho_N) of
+ * the density after N steps with respect to the initial fields and the 16
+ * relaxation rates.  The transpose of one step (Eq. 3, forward Euler +
+ * Lax-Wendroff) is, per cell, with lam = dL/df^{n+1} and mu = M^-T lam:
+ *   dL/df^n     = lam + Adv^T(lam) - M^T (I - J)^T S mu,
+ *   dL/dsigma_k += -mu_k (fhat_k - fhat^eq_k)      (sigma_k = s_k dt),
+ * where J = d fhat^eq / d fhat (Appendix equilibria, non-zero only through
+ * rho, j, e) and Adv^T is the Lax-Wendroff stencil with c -> -c.  Fixed
+ * ghosts hold the initial f of their cells, so their adjoints are added to
+ * dL/df^0 there; f^0 = M^-1 fhat^eq(rho, u, T) is differentiated last.
+ *
+ * mrt_adjoint_record: sets f = f^eq(rho0, ux0, uy0, T0) (fields [ny][nx]
+ * doubles, on the device if on_device), runs nsteps >= 1 steps keeping f
+ * every ckpt_every >= 1 steps on the device (memory: ceil(nsteps/ckpt_every)
+ * + ckpt_every + 2 states), and leaves f^N in the grid.  Synchronises once.
+ *
+ * mrt_adjoint_backward: after a record, from dL/drho_N ([ny][nx] doubles)
+ * writes dL/drho_0, dL/dux_0, dL/duy_0, dL/dT_0 ([ny][nx] doubles; any may
+ * be NULL) and g_s[16] = dL/ds_1..16 (host; g_s[0..3] = 0: those rates act
+ * on conserved moments).  Each segment of ckpt_every steps is recomputed
+ * from its checkpoint before its reverse sweep.  Gradients are with respect
+ * to the 16 rates as used (after the Pr rule of mrt_params).  Synchronises.
+ *
+ * mrt_adjoint_step: one reverse step on caller states f^n and lam_next =
+ * dL/df^{n+1} ([16][ny][nx], grid precision), writing lam = dL/df^n and
+ * adding dL/ds_k of this step to g_s (fixed-ghost adjoints are not
+ * returned).  Allocates its own temporaries; synchronises.
+ * Errors: MRT_EINVAL (null pointers, bad counts, backward before record),
+ * MRT_ENOMEM, MRT_ECUDA. */
+mrt_status mrt_adjoint_record(mrt_grid *g, const double *rho0, const double *ux0, const double *uy0,
+                              const double *T0, int on_device, long nsteps, int ckpt_every);
+mrt_status mrt_adjoint_backward(mrt_grid *g, const double *dL_drhoN, int on_device, double *g_rho0,
+                                double *g_ux0, double *g_uy0, double *g_T0, double g_s[16]);
+mrt_status mrt_adjoint_step(mrt_grid *g, const void *f, const void *lam_next, void *lam, int on_device,
+                            double g_s[16]);
+
 /* Conserved totals sum_cells (rho, j_x, j_y, e) * dx * dy of a state held by
  * the caller on the device, computed without any allocation by the library.
  * The paper has no counterpart: this entry point exists for callers that

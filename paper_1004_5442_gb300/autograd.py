@@ -1,0 +1,50 @@
+"""torch.autograd.Function over a run of the fused MRT-FDLB step.
+
+``mrt_run(rho0, ux0, uy0, T0, s, params, nsteps, ckpt_every)`` returns the
+density after ``nsteps`` steps as a CUDA tensor; its backward runs the CUDA
+reverse sweep (mrt_adjoint_backward: checkpointed recomputation + transposed
+step) and returns gradients for the four initial fields and the 16 rates.
+Only marshalling happens here: every step of the forward and the reverse
+sweep runs in the CUDA library.
+"""
+from __future__ import annotations
+
+import numpy as np
+import torch
+
+from . import binding as Bd
+
+
+class MRTRun(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, rho0, ux0, uy0, T0, s, params, nsteps, ckpt_every):
+        p = Bd.make_params(params["nx"], params["ny"], params["dx"], params["dt"], params["gamma"],
+                           s.detach().cpu().numpy().astype(np.float64), params.get("bc_x", 0),
+                           params.get("bc_y", 0), params.get("precision", Bd.FP32), 0.0,
+                           params.get("kernel", Bd.KERNEL_AUTO), params.get("tile", 0))
+        fields = [t.detach().to(dtype=torch.float64).contiguous() for t in (rho0, ux0, uy0, T0)]
+        grid = Bd.Grid(p, *fields)
+        grid.adjoint_record(*fields, nsteps, ckpt_every)
+        rhoN = torch.empty_like(fields[0])
+        grid.macro([rhoN, torch.empty_like(rhoN), torch.empty_like(rhoN), torch.empty_like(rhoN)])
+        ctx.grid = grid
+        ctx.save_for_backward(s)
+        return rhoN
+
+    @staticmethod
+    def backward(ctx, g_rhoN):
+        grid = ctx.grid
+        (s,) = ctx.saved_tensors
+        g = g_rhoN.detach().to(dtype=torch.float64).contiguous()
+        outs = [torch.empty_like(g) for _ in range(4)]
+        torch.cuda.current_stream().synchronize()
+        *_, gs = grid.adjoint_backward(g, outs)
+        grid.close()
+        ctx.grid = None
+        g_s = torch.as_tensor(gs, dtype=s.dtype, device=s.device)
+        return outs[0], outs[1], outs[2], outs[3], g_s, None, None, None
+
+
+def mrt_run(rho0, ux0, uy0, T0, s, params: dict, nsteps: int, ckpt_every: int = 50):
+    """rho after nsteps steps from f^eq(rho0, u0, T0), differentiable in all inputs."""
+    return MRTRun.apply(rho0, ux0, uy0, T0, s, params, nsteps, ckpt_every)

@@ -24,7 +24,8 @@ KERNEL_AUTO, KERNEL_TMA, KERNEL_DIRECT = 0, 1, 2
 # every symbol include/mrtfdlb.h declares
 EXPORTED = ["mrt_create", "mrt_step", "mrt_get_macro", "mrt_conserved_totals", "mrt_get_f",
             "mrt_set_f", "mrt_health", "mrt_info", "mrt_destroy", "mrt_status_str",
-            "mrt_last_error", "mrt_conserved_totals_static"]
+            "mrt_last_error", "mrt_conserved_totals_static", "mrt_adjoint_record",
+            "mrt_adjoint_backward", "mrt_adjoint_step"]
 
 
 class MrtError(RuntimeError):
@@ -72,8 +73,12 @@ def load(path: str = LIB_PATH):
     L.mrt_status_str.argtypes = [ip]
     L.mrt_last_error.restype = ctypes.c_char_p
     L.mrt_conserved_totals_static.argtypes = [vp, ip, ip, ip, ctypes.c_double, vp, vp]
+    L.mrt_adjoint_record.argtypes = [vp, vp, vp, vp, vp, ip, ctypes.c_long, ip]
+    L.mrt_adjoint_backward.argtypes = [vp, vp, ip, vp, vp, vp, vp, dp]
+    L.mrt_adjoint_step.argtypes = [vp, vp, vp, vp, ip, dp]
     for name in ("mrt_create", "mrt_step", "mrt_get_macro", "mrt_conserved_totals", "mrt_get_f",
-                 "mrt_set_f", "mrt_health", "mrt_info", "mrt_conserved_totals_static"):
+                 "mrt_set_f", "mrt_health", "mrt_info", "mrt_conserved_totals_static",
+                 "mrt_adjoint_record", "mrt_adjoint_backward", "mrt_adjoint_step"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -181,6 +186,41 @@ class Grid:
         if isinstance(f, np.ndarray):
             f = np.ascontiguousarray(f, dtype=np.float64 if self.fp64 else np.float32)
         check(load().mrt_set_f(self._h, ctypes.c_void_p(_ptr(f)), _on_device(f)))
+
+    def adjoint_record(self, rho0, ux0, uy0, T0, nsteps: int, ckpt_every: int) -> None:
+        """Set f = f^eq(fields), run nsteps keeping checkpoints (mrt_adjoint_record)."""
+        arrs = [rho0, ux0, uy0, T0]
+        on_dev = _on_device(arrs[0])
+        if not on_dev:
+            arrs = [np.ascontiguousarray(np.broadcast_to(np.asarray(a, dtype=np.float64), (self.ny, self.nx)))
+                    for a in arrs]
+        check(load().mrt_adjoint_record(self._h, *(ctypes.c_void_p(_ptr(a)) for a in arrs), on_dev,
+                                        int(nsteps), int(ckpt_every)))
+
+    def adjoint_backward(self, dL_drhoN, outs=None):
+        """(g_rho0, g_ux0, g_uy0, g_T0, g_s[16]) from dL/drho_N (mrt_adjoint_backward)."""
+        on_dev = _on_device(dL_drhoN)
+        if not on_dev:
+            dL_drhoN = np.ascontiguousarray(dL_drhoN, dtype=np.float64)
+        if outs is None:
+            outs = [np.empty((self.ny, self.nx)) for _ in range(4)]
+        gs = np.zeros(16)
+        check(load().mrt_adjoint_backward(self._h, ctypes.c_void_p(_ptr(dL_drhoN)), on_dev,
+                                          *(ctypes.c_void_p(_ptr(o)) for o in outs),
+                                          gs.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+        return (*outs, gs)
+
+    def adjoint_step(self, f, lam_next):
+        """One reverse step on host states: returns (dL/df^n, dL/ds of this step)."""
+        dt = np.float64 if self.fp64 else np.float32
+        f = np.ascontiguousarray(f, dtype=dt)
+        lam_next = np.ascontiguousarray(lam_next, dtype=dt)
+        lam = np.empty_like(f)
+        gs = np.zeros(16)
+        check(load().mrt_adjoint_step(self._h, ctypes.c_void_p(_ptr(f)), ctypes.c_void_p(_ptr(lam_next)),
+                                      ctypes.c_void_p(_ptr(lam)), 0,
+                                      gs.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+        return lam, gs
 
     def health(self) -> int:
         return int(load().mrt_health(self._h))

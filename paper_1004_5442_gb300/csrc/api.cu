@@ -321,37 +321,6 @@ int grid_for(long n, int threads, int cap = 4096) {
 // ---------------------------------------------------------------------------
 // Grid object
 // ---------------------------------------------------------------------------
-typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
-                                  const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
-                                  const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
-                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-
-struct mrt_grid {
-    mrt_params p;
-    int fp64;
-    size_t elem;
-    Layout L;
-    void* f[2] = {nullptr, nullptr};
-    int cur = 0;
-    int device = 0;
-    cudaStream_t stream = nullptr;
-    unsigned* flag = nullptr;        // device flag word
-    double* partials = nullptr;      // 4 doubles per CTA
-    int max_parts = 0;
-    double* totals_dev = nullptr;    // 4 doubles
-    bool totals_fresh = false;
-    double* macro_tmp = nullptr;     // 4 fields, for host readout
-    long steps = 0;
-    int kernel = MRT_KERNEL_DIRECT;  // in use
-    CUtensorMap maps[2];       // loads: whole padded rows, box with halo
-    CUtensorMap maps_out[2];   // stores: x extent ends before the right ghost
-    int tile = 0;
-    int tma_grid_x = 0, tma_grid_y = 0, rows_per_cta = 0;
-    Coef<double> kd;
-    Coef<float> kf;
-    double b;
-};
-
 static EncodeTiledFn get_encode() {
     static EncodeTiledFn fn = nullptr;
     if (!fn) {
@@ -365,27 +334,32 @@ static EncodeTiledFn get_encode() {
     return fn;
 }
 
-static mrt_status make_maps(mrt_grid* g) {
+mrt_status mrt_encode_maps(const mrt_grid* g, void* buf, CUtensorMap* in, CUtensorMap* out) {
     EncodeTiledFn enc = get_encode();
     if (!enc) return fail(MRT_ECUDA, "cuTensorMapEncodeTiled entry point unavailable");
     const int boxw = g->fp64 ? tma_boxw<double>() : tma_boxw<float>();
     const CUtensorMapDataType dt = g->fp64 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+    cuuint64_t strides[2] = {(cuuint64_t)(g->L.pitch * g->elem), (cuuint64_t)(g->L.plane * g->elem)};
+    cuuint32_t estr[3] = {1, 1, 1};
+    cuuint64_t dims[3] = {(cuuint64_t)g->L.pitch, (cuuint64_t)(g->L.ny + 2), 16};
+    cuuint32_t box[3] = {(cuuint32_t)boxw, 1, 16};
+    CUresult r = enc(in, dt, 3, buf, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                     CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return fail(MRT_ECUDA, "cuTensorMapEncodeTiled (load) failed (%d)", (int)r);
+    // store map: the kernel issues row stores only for whole 128-column
+    // strips, which end at or before column G + nx
+    cuuint64_t odims[3] = {(cuuint64_t)(g->L.G + g->L.nx), (cuuint64_t)(g->L.ny + 2), 16};
+    cuuint32_t obox[3] = {(cuuint32_t)TMA_W, 1, 16};
+    r = enc(out, dt, 3, buf, odims, strides, obox, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return fail(MRT_ECUDA, "cuTensorMapEncodeTiled (store) failed (%d)", (int)r);
+    return MRT_OK;
+}
+
+static mrt_status make_maps(mrt_grid* g) {
     for (int b = 0; b < 2; ++b) {
-        cuuint64_t strides[2] = {(cuuint64_t)(g->L.pitch * g->elem), (cuuint64_t)(g->L.plane * g->elem)};
-        cuuint32_t estr[3] = {1, 1, 1};
-        cuuint64_t dims[3] = {(cuuint64_t)g->L.pitch, (cuuint64_t)(g->L.ny + 2), 16};
-        cuuint32_t box[3] = {(cuuint32_t)boxw, 1, 16};
-        CUresult r = enc(&g->maps[b], dt, 3, g->f[b], dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                         CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-        if (r != CUDA_SUCCESS) return fail(MRT_ECUDA, "cuTensorMapEncodeTiled (load) failed (%d)", (int)r);
-        // store map: the kernel issues row stores only for whole 128-column
-        // strips, which end at or before column G + nx
-        cuuint64_t odims[3] = {(cuuint64_t)(g->L.G + g->L.nx), (cuuint64_t)(g->L.ny + 2), 16};
-        cuuint32_t obox[3] = {(cuuint32_t)TMA_W, 1, 16};
-        r = enc(&g->maps_out[b], dt, 3, g->f[b], odims, strides, obox, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-        if (r != CUDA_SUCCESS) return fail(MRT_ECUDA, "cuTensorMapEncodeTiled (store) failed (%d)", (int)r);
+        mrt_status st = mrt_encode_maps(g, g->f[b], &g->maps[b], &g->maps_out[b]);
+        if (st != MRT_OK) return st;
     }
     return MRT_OK;
 }
@@ -421,6 +395,7 @@ static void release(mrt_grid* g) {
     cudaFree(g->partials);
     cudaFree(g->totals_dev);
     cudaFree(g->macro_tmp);
+    mrt_tape_free(g->tape);
     if (prev >= 0) cudaSetDevice(prev);
     delete g;
 }
@@ -455,7 +430,6 @@ extern "C" mrt_status mrt_create(const mrt_params* params, const double* rho, co
     if (st != MRT_OK) return st;
     if (!out || !rho || !ux || !uy || !T) return fail(MRT_EINVAL, "null pointer argument");
     *out = nullptr;
-    const long n = (long)params->nx * params->ny;
     mrt_grid* g = new (std::nothrow) mrt_grid();
     if (!g) return fail(MRT_ENOMEM, "host allocation failed");
     g->p = *params;
@@ -526,44 +500,90 @@ extern "C" mrt_status mrt_create(const mrt_params* params, const double* rho, co
     if ((e = cudaMalloc(&g->partials, 4 * sizeof(double) * (size_t)g->max_parts)) != cudaSuccess)
         return bail(fail(MRT_ENOMEM, "cudaMalloc partials: %s", cudaGetErrorString(e)));
 
-    // initial fields on the device
-    const double* d_in[4] = {rho, ux, uy, T};
-    double* staged = nullptr;
-    if (!fields_on_device) {
-        if ((e = cudaMalloc(&staged, 4 * sizeof(double) * (size_t)n)) != cudaSuccess)
-            return bail(fail(MRT_ENOMEM, "cudaMalloc staging: %s", cudaGetErrorString(e)));
-        for (int q = 0; q < 4; ++q) {
-            const double* src = q == 0 ? rho : q == 1 ? ux : q == 2 ? uy : T;
-            if ((e = cudaMemcpyAsync(staged + q * n, src, n * sizeof(double), cudaMemcpyHostToDevice,
-                                     g->stream)) != cudaSuccess) {
-                cudaFree(staged);
-                return bail(fail(MRT_ECUDA, "upload: %s", cudaGetErrorString(e)));
-            }
-            d_in[q] = staged + q * n;
-        }
-    }
-    st = g->fp64 ? do_init<double>(g, d_in[0], d_in[1], d_in[2], d_in[3])
-                 : do_init<float>(g, d_in[0], d_in[1], d_in[2], d_in[3]);
-    if (staged) {
-        cudaStreamSynchronize(g->stream);
-        cudaFree(staged);
-    }
-    if (st != MRT_OK) return bail(st);
     if (kernel == MRT_KERNEL_TMA) {
         st = make_maps(g);
         if (st != MRT_OK) return bail(st);
     }
-    {
-        // the initial state is validated by the init kernel through the flag
-        unsigned h = 0;
-        if ((e = cudaMemcpyAsync(&h, g->flag, sizeof h, cudaMemcpyDeviceToHost, g->stream)) != cudaSuccess ||
-            (e = cudaStreamSynchronize(g->stream)) != cudaSuccess)
-            return bail(fail(MRT_ECUDA, "init: %s", cudaGetErrorString(e)));
-        if (h & FLAG_UNSTABLE) return bail(fail(MRT_EINVAL, "initial state: rho and T must be finite and > 0"));
-    }
+    st = mrt_reinit(g, rho, ux, uy, T, fields_on_device);
+    if (st != MRT_OK) return bail(st);
     *out = g;
     return MRT_OK;
 }
+
+mrt_status mrt_fail(mrt_status s, const char* fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof g_err, fmt, ap);
+    va_end(ap);
+    return s;
+}
+
+mrt_status mrt_reinit(mrt_grid* g, const double* rho, const double* ux, const double* uy, const double* T,
+                      int on_device) {
+    if (!rho || !ux || !uy || !T) return fail(MRT_EINVAL, "null field pointer");
+    const long n = (long)g->L.nx * g->L.ny;
+    cudaError_t e;
+    const double* d_in[4] = {rho, ux, uy, T};
+    double* staged = nullptr;
+    if (!on_device) {
+        if ((e = cudaMalloc(&staged, 4 * sizeof(double) * (size_t)n)) != cudaSuccess)
+            return fail(MRT_ENOMEM, "cudaMalloc staging: %s", cudaGetErrorString(e));
+        for (int q = 0; q < 4; ++q) {
+            if ((e = cudaMemcpyAsync(staged + q * n, d_in[q], n * sizeof(double), cudaMemcpyHostToDevice,
+                                     g->stream)) != cudaSuccess) {
+                cudaFree(staged);
+                return fail(MRT_ECUDA, "upload: %s", cudaGetErrorString(e));
+            }
+            d_in[q] = staged + q * n;
+        }
+    }
+    CUDA_TRY(cudaMemsetAsync(g->flag, 0, sizeof(unsigned), g->stream));
+    mrt_status st = g->fp64 ? do_init<double>(g, d_in[0], d_in[1], d_in[2], d_in[3])
+                            : do_init<float>(g, d_in[0], d_in[1], d_in[2], d_in[3]);
+    // the initial state is validated by the init kernel through the flag
+    unsigned h = 0;
+    if (st == MRT_OK) {
+        if ((e = cudaMemcpyAsync(&h, g->flag, sizeof h, cudaMemcpyDeviceToHost, g->stream)) != cudaSuccess ||
+            (e = cudaStreamSynchronize(g->stream)) != cudaSuccess)
+            st = fail(MRT_ECUDA, "init: %s", cudaGetErrorString(e));
+    } else {
+        cudaStreamSynchronize(g->stream);
+    }
+    if (staged) cudaFree(staged);
+    if (st != MRT_OK) return st;
+    if (h & FLAG_UNSTABLE) return fail(MRT_EINVAL, "initial state: rho and T must be finite and > 0");
+    g->cur = 0;
+    g->steps = 0;
+    g->totals_fresh = false;
+    return MRT_OK;
+}
+
+// One step from buffer `in` to buffer `out` (padded layout, same grid), with
+// the TMA maps of those buffers when the TMA kernel is in use.
+template <class T>
+mrt_status step_between(mrt_grid* g, const void* in, void* out, const CUtensorMap* map_in,
+                        const CUtensorMap* map_out, bool totals) {
+    StepArgs<T> a;
+    a.L = g->L;
+    a.per_x = g->p.bc_x == MRT_BC_PERIODIC;
+    a.per_y = g->p.bc_y == MRT_BC_PERIODIC;
+    a.rows_per_cta = g->rows_per_cta;
+    a.partials = g->partials;
+    a.flag = g->flag;
+    if constexpr (sizeof(T) == 8) a.k = g->kd; else a.k = g->kf;
+    a.in = static_cast<const T*>(in);
+    a.out = static_cast<T*>(out);
+    cudaError_t e = g->kernel == MRT_KERNEL_TMA
+        ? launch_step_tma<T>(g->tile, map_in, map_out, a, g->tma_grid_x, g->tma_grid_y, totals, g->stream)
+        : launch_step_direct<T>(a, totals, g->stream);
+    if (e != cudaSuccess) return fail(MRT_ECUDA, "step launch: %s", cudaGetErrorString(e));
+    return MRT_OK;
+}
+template mrt_status step_between<float>(mrt_grid*, const void*, void*, const CUtensorMap*, const CUtensorMap*, bool);
+template mrt_status step_between<double>(mrt_grid*, const void*, void*, const CUtensorMap*, const CUtensorMap*, bool);
+
+mrt_status mrt_reinit(mrt_grid* g, const double* rho, const double* ux, const double* uy, const double* T,
+                      int on_device);
 
 template <class T>
 static mrt_status step_impl(mrt_grid* g, long nsteps) {
@@ -665,6 +685,8 @@ extern "C" mrt_status mrt_conserved_totals(mrt_grid* g, double out[4]) {
     return MRT_OK;
 }
 
+mrt_status mrt_refresh_periodic_ghosts(mrt_grid* g, void* buf);
+
 static mrt_status copy_f(mrt_grid* g, void* f, int on_device, bool to_grid) {
     const size_t rowb = (size_t)g->L.nx * g->elem;
     const size_t dpitch = (size_t)g->L.pitch * g->elem;
@@ -695,20 +717,25 @@ extern "C" mrt_status mrt_set_f(mrt_grid* g, const void* f, int on_device) {
     if (st != MRT_OK) return st;
     // periodic ghosts follow the new state; fixed-equilibrium ghosts keep the
     // boundary values set at creation
-    const int per_x = g->p.bc_x == MRT_BC_PERIODIC, per_y = g->p.bc_y == MRT_BC_PERIODIC;
-    if (per_x || per_y) {
-        if (g->fp64) {
-            double* fd = static_cast<double*>(g->f[g->cur]);
-            if (per_x) ghost_cols_kernel<double><<<grid_for(16L * g->L.ny, 256), 256, 0, g->stream>>>(g->L, 1, fd);
-            if (per_y) ghost_rows_kernel<double><<<grid_for(16L * g->L.nx, 256), 256, 0, g->stream>>>(g->L, 1, fd);
-        } else {
-            float* ff = static_cast<float*>(g->f[g->cur]);
-            if (per_x) ghost_cols_kernel<float><<<grid_for(16L * g->L.ny, 256), 256, 0, g->stream>>>(g->L, 1, ff);
-            if (per_y) ghost_rows_kernel<float><<<grid_for(16L * g->L.nx, 256), 256, 0, g->stream>>>(g->L, 1, ff);
-        }
-        CUDA_TRY(cudaGetLastError());
-    }
+    st = mrt_refresh_periodic_ghosts(g, g->f[g->cur]);
+    if (st != MRT_OK) return st;
     g->totals_fresh = false;
+    return MRT_OK;
+}
+
+// Periodic ghost columns / rows of a padded buffer from its own data.
+mrt_status mrt_refresh_periodic_ghosts(mrt_grid* g, void* buf) {
+    const int per_x = g->p.bc_x == MRT_BC_PERIODIC, per_y = g->p.bc_y == MRT_BC_PERIODIC;
+    if (g->fp64) {
+        double* fd = static_cast<double*>(buf);
+        if (per_x) ghost_cols_kernel<double><<<grid_for(16L * g->L.ny, 256), 256, 0, g->stream>>>(g->L, 1, fd);
+        if (per_y) ghost_rows_kernel<double><<<grid_for(16L * g->L.nx, 256), 256, 0, g->stream>>>(g->L, 1, fd);
+    } else {
+        float* ff = static_cast<float*>(buf);
+        if (per_x) ghost_cols_kernel<float><<<grid_for(16L * g->L.ny, 256), 256, 0, g->stream>>>(g->L, 1, ff);
+        if (per_y) ghost_rows_kernel<float><<<grid_for(16L * g->L.nx, 256), 256, 0, g->stream>>>(g->L, 1, ff);
+    }
+    CUDA_TRY(cudaGetLastError());
     return MRT_OK;
 }
 

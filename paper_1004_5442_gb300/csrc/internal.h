@@ -3,6 +3,7 @@
 #include <cuda.h>
 #include <cuda_runtime.h>
 
+#include "../../include/mrtfdlb.h"
 #include "model.cuh"
 
 namespace mrt {
@@ -58,14 +59,16 @@ struct TileCfg {
     int minb;
     const char* name;
 };
-constexpr int NUM_TILES = 5;
-// tile 0 is "automatic"; 1..4 are explicit
+constexpr int NUM_TILES = 6;
+// tile 0 is "automatic"; 1..5 are explicit.  Tile 5 keeps row r-1 of the
+// y-moving planes in registers so more of the ring is in flight.
 inline TileCfg tile_cfg(int tile) {
     switch (tile) {
         case 1: return {6, 0, 4, "ring6-stg-4cta"};
         case 2: return {4, 1, 4, "ring4-tma-4cta"};
         case 3: return {6, 1, 3, "ring6-tma-3cta"};
-        default: return {5, 1, 3, "ring5-tma-3cta"};
+        case 4: return {5, 1, 3, "ring5-tma-3cta"};
+        default: return {4, 1, 4, "ring4-tma-4cta-ywin"};
     }
 }
 template <class T> constexpr int default_tile() { return sizeof(T) == 4 ? 2 : 1; }
@@ -89,4 +92,101 @@ cudaError_t tma_occupancy(int tile, int* blocks_per_sm);
 template <class T>
 void direct_grid(const Layout& L, dim3* grid, dim3* block);
 
+
+// Reverse-sweep arguments (adjoint_kernels.cu).
+template <class T>
+struct AdjArgs {
+    Layout L;
+    int per_x, per_y;
+    const T* lam_in;       // dL/df^{n+1}, padded layout; fixed ghosts hold 0
+    const T* f;            // f^n, padded layout (centre values only)
+    T* lam_out;            // dL/df^n
+    double* gxb;           // fixed x-ghost adjoints [16][2][ny] (unused if periodic)
+    double* gyb;           // fixed y-ghost adjoints [16][2][nx]
+    double* gpart;         // per-block rate partials [nblocks][12], accumulated
+    Coef<T> k;
+};
+
+template <class T>
+void adjoint_grid(const Layout& L, dim3* grid, dim3* block);
+template <class T>
+cudaError_t launch_adjoint_step(const AdjArgs<T>& a, cudaStream_t st);
+template <class T>
+cudaError_t launch_lam_from_drho(const Layout& L, const double* drho, T* lam, cudaStream_t st);
+template <class T>
+cudaError_t launch_ghost_adjoint(const Layout& L, int fix_x, int fix_y, const double* gxb, const double* gyb,
+                                 T* lam, cudaStream_t st);
+template <class T>
+cudaError_t launch_init_adjoint(const Layout& L, const InitCoef& ic, const Coef<double>& kd, const T* lam,
+                                const double* rho, const double* ux, const double* uy, const double* Tf,
+                                double* g_rho, double* g_ux, double* g_uy, double* g_T, cudaStream_t st);
+cudaError_t launch_sum_partials(const double* gpart, int nparts, double* out, cudaStream_t st);
+
 }  // namespace mrt
+
+// ---------------------------------------------------------------------------
+// Grid object shared by the API translation units.
+// ---------------------------------------------------------------------------
+
+// Checkpoint tape of a recorded forward run (mrt_adjoint_record).
+struct mrt_tape {
+    long nsteps = 0;
+    int K = 0;                  // steps between checkpoints
+    int nck = 0;                // checkpoints: f at steps 0, K, 2K, ...
+    size_t state_bytes = 0;     // one padded buffer
+    void* ck = nullptr;         // nck buffers
+    void* seg = nullptr;        // K buffers for a recomputed segment
+    CUtensorMap* seg_in = nullptr;   // load maps of the segment buffers
+    CUtensorMap* seg_out = nullptr;  // store maps of the segment buffers
+    void* lam[2] = {nullptr, nullptr};
+    double* gxb = nullptr;
+    double* gyb = nullptr;
+    double* gpart = nullptr;
+    int nparts = 0;
+    double* scratch = nullptr;  // 8 fields of nx*ny doubles + 12 sums
+};
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                  const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                  const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+struct mrt_grid {
+    mrt_params p;
+    int fp64;
+    size_t elem;
+    mrt::Layout L;
+    void* f[2] = {nullptr, nullptr};
+    int cur = 0;
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    unsigned* flag = nullptr;        // device flag word
+    double* partials = nullptr;      // 4 doubles per CTA
+    int max_parts = 0;
+    double* totals_dev = nullptr;    // 4 doubles
+    bool totals_fresh = false;
+    double* macro_tmp = nullptr;     // 4 fields, for host readout
+    long steps = 0;
+    int kernel = MRT_KERNEL_DIRECT;  // in use
+    CUtensorMap maps[2];       // loads: whole padded rows, box with halo
+    CUtensorMap maps_out[2];   // stores: x extent ends before the right ghost
+    int tile = 0;
+    int tma_grid_x = 0, tma_grid_y = 0, rows_per_cta = 0;
+    mrt::Coef<double> kd;
+    mrt::Coef<float> kf;
+    double b;
+    mrt_tape* tape = nullptr;
+};
+
+
+// Encode the load and store tensor maps of one padded buffer.
+mrt_status mrt_encode_maps(const mrt_grid* g, void* buf, CUtensorMap* in, CUtensorMap* out);
+void mrt_tape_free(mrt_tape* t);
+
+template <class T>
+mrt_status step_between(mrt_grid* g, const void* in, void* out, const CUtensorMap* map_in,
+                        const CUtensorMap* map_out, bool totals);
+// Recompute f = f^eq(rho, u, T) into buffer 0 (and both buffers' ghosts),
+// as at creation; inputs on the device if on_device.
+mrt_status mrt_reinit(mrt_grid* g, const double* rho, const double* ux, const double* uy, const double* T,
+                      int on_device);
+mrt_status mrt_fail(mrt_status s, const char* fmt, ...);

@@ -187,7 +187,13 @@ __device__ __forceinline__ void fence_async_shared() {
 // --------------------------------------------------------------------------
 // TMA-staged strip kernel.
 // --------------------------------------------------------------------------
-template <class T, bool TOTALS, int NS, bool TSTORE, int MINB>
+// YWIN: the 12 planes that move along y keep row r-1 in registers, so only
+// rows r and r+1 must be resident and the ring holds NS-2 rows in flight.
+template <bool YWIN> __device__ __forceinline__ constexpr bool moves_y(int i) {
+    return (i >= 8) || (i & 1);
+}
+
+template <class T, bool TOTALS, int NS, bool TSTORE, int MINB, bool YWIN>
 __global__ void __launch_bounds__(TMA_W, MINB) step_tma(const __grid_constant__ CUtensorMap map_in,
                                                         const __grid_constant__ CUtensorMap map_out,
                                                         const StepArgs<T> a) {
@@ -242,10 +248,20 @@ __global__ void __launch_bounds__(TMA_W, MINB) step_tma(const __grid_constant__ 
 
     bool ok = wait_row(0);
     ok = wait_row(1) && ok;
-    ok = wait_row(2) && ok;
+    if (!YWIN) ok = wait_row(2) && ok;
     bool bad = false;
     Acc<T> acc[4];
     const int col = tid + HALO;
+    T ym[NV], fc[NV];  // YWIN: rows r-1 (y-moving planes) and r at this column
+    if (YWIN && ok) {
+        const T* s0 = ring;
+        const T* s1 = ring + (size_t)(1 % NS) * NV * BOXW;
+#pragma unroll
+        for (int i = 0; i < NV; ++i) {
+            if (moves_y<YWIN>(i)) ym[i] = s0[i * BOXW + col];
+            fc[i] = s1[i * BOXW + col];
+        }
+    }
 
     auto drain = [&]() {
         if (tid == 0) {
@@ -256,27 +272,48 @@ __global__ void __launch_bounds__(TMA_W, MINB) step_tma(const __grid_constant__ 
         }
     };
     if (__syncthreads_or(!ok)) { drain(); return; }
+    if (YWIN && tid == 0 && NS < nload) {
+        // row 0 now lives in registers: its slot takes row NS
+        mbar_arrive_expect_tx(&full[0], SLOT_BYTES);
+        tma_load_3d(ring, &map_in, &full[0], tma_x, y0 + NS, 0);
+        issued = NS + 1;
+    }
 
 #pragma unroll 1
     for (int r = 1; r <= nrows; ++r) {
         const int y = y0 + r - 1;
         T* ob = outbuf + (size_t)(r & 1) * NV * TMA_W;
-        if (active) {
+        if (YWIN) {
+            ok = wait_row(r + 1);  // a failed wait is acted on at the barrier below
+        }
+        if (active && ok) {
             const T* sm = ring + (size_t)((r - 1) % NS) * NV * BOXW;
             const T* sc = ring + (size_t)(r % NS) * NV * BOXW;
             const T* sp = ring + (size_t)((r + 1) % NS) * NV * BOXW;
+            T yp[NV];
+            if (YWIN) {
+#pragma unroll
+                for (int i = 0; i < NV; ++i) yp[i] = sp[i * BOXW + col];
+            }
             auto F = [&](int i, int pos) -> T {
                 switch (pos) {
-                    case C: return sc[i * BOXW + col];
+                    case C: return YWIN ? fc[i] : sc[i * BOXW + col];
                     case XM: return sc[i * BOXW + col - 1];
                     case XP: return sc[i * BOXW + col + 1];
-                    case YM: return sm[i * BOXW + col];
-                    default: return sp[i * BOXW + col];
+                    case YM: return YWIN ? ym[i] : sm[i * BOXW + col];
+                    default: return YWIN ? yp[i] : sp[i * BOXW + col];
                 }
             };
             T out[NV];
             T rho, P;
             cell_update<T>(F, a.k, out, rho, P);
+            if (YWIN) {
+#pragma unroll
+                for (int i = 0; i < NV; ++i) {
+                    if (moves_y<YWIN>(i)) ym[i] = fc[i];
+                    fc[i] = yp[i];
+                }
+            }
             bad |= !(rho > (T)0) | !(P > (T)0);
             if (TSTORE) {
 #pragma unroll
@@ -294,8 +331,9 @@ __global__ void __launch_bounds__(TMA_W, MINB) step_tma(const __grid_constant__ 
             fence_async_shared();              // make this thread's row visible to the TMA engine
             if (tid == 0) bulk_wait_read_all();  // the store from the other out slot has read it
         }
-        ok = (r + 2 < nload) ? wait_row(r + 2) : true;
-        // every thread is done with slot (r-1) % NS, and the out row is complete
+        if (!YWIN) ok = (r + 2 < nload) ? wait_row(r + 2) : true;
+        // every thread is done with the slot released below, and the out row
+        // is complete
         if (__syncthreads_or(!ok)) { drain(); return; }
         if (tid == 0) {
             if (tstore) {
@@ -304,7 +342,8 @@ __global__ void __launch_bounds__(TMA_W, MINB) step_tma(const __grid_constant__ 
                 if (a.per_y && y == L.ny - 1) tma_store_3d(&map_out, ob, L.G + x0, 0, 0);
                 bulk_commit();
             }
-            const int l = r - 1 + NS;
+            // without YWIN row r-1 is the oldest row still read; with it, row r
+            const int l = YWIN ? r + NS : r - 1 + NS;
             if (l < nload) {
                 const int s = l % NS;
                 mbar_arrive_expect_tx(&full[s], SLOT_BYTES);
@@ -383,25 +422,25 @@ __global__ void __launch_bounds__(DIR_BX* DIR_BY) step_direct(const StepArgs<T> 
     }
 }
 
-template <class T, int NS, bool TSTORE, int MINB>
+template <class T, int NS, bool TSTORE, int MINB, bool YWIN = false>
 struct TmaKernels {
     static cudaError_t launch(const CUtensorMap* mi, const CUtensorMap* mo, const StepArgs<T>& a, dim3 grid,
                               size_t smem, bool totals, cudaStream_t st) {
         if (totals)
-            step_tma<T, true, NS, TSTORE, MINB><<<grid, TMA_W, smem, st>>>(*mi, *mo, a);
+            step_tma<T, true, NS, TSTORE, MINB, YWIN><<<grid, TMA_W, smem, st>>>(*mi, *mo, a);
         else
-            step_tma<T, false, NS, TSTORE, MINB><<<grid, TMA_W, smem, st>>>(*mi, *mo, a);
+            step_tma<T, false, NS, TSTORE, MINB, YWIN><<<grid, TMA_W, smem, st>>>(*mi, *mo, a);
         return cudaGetLastError();
     }
     static cudaError_t occupancy(size_t smem, int* occ) {
         cudaError_t e;
-        if ((e = cudaFuncSetAttribute(step_tma<T, true, NS, TSTORE, MINB>,
+        if ((e = cudaFuncSetAttribute(step_tma<T, true, NS, TSTORE, MINB, YWIN>,
                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
             return e;
-        if ((e = cudaFuncSetAttribute(step_tma<T, false, NS, TSTORE, MINB>,
+        if ((e = cudaFuncSetAttribute(step_tma<T, false, NS, TSTORE, MINB, YWIN>,
                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
             return e;
-        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, step_tma<T, false, NS, TSTORE, MINB>, TMA_W, smem);
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, step_tma<T, false, NS, TSTORE, MINB, YWIN>, TMA_W, smem);
     }
 };
 
@@ -415,6 +454,7 @@ cudaError_t with_tile(int tile, Fn&& fn) {
         case 2: return fn(TmaKernels<T, ring_depth<T, 4>(), true, (sizeof(T) == 8 ? 2 : 4)>());
         case 3: return fn(TmaKernels<T, ring_depth<T, 6>(), true, (sizeof(T) == 8 ? 2 : 3)>());
         case 4: return fn(TmaKernels<T, ring_depth<T, 5>(), true, (sizeof(T) == 8 ? 2 : 3)>());
+        case 5: return fn(TmaKernels<T, ring_depth<T, 4>(), true, (sizeof(T) == 8 ? 2 : 4), true>());
         default: return cudaErrorInvalidValue;
     }
 }

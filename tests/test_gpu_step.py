@@ -22,7 +22,7 @@ pytestmark = pytest.mark.gpu
 
 KERNELS = [Bd.KERNEL_TMA, Bd.KERNEL_DIRECT]
 # (kernel, tile): every compiled TMA variant and the direct kernel
-VARIANTS = [(Bd.KERNEL_TMA, t) for t in (1, 2, 3, 4)] + [(Bd.KERNEL_DIRECT, 0)]
+VARIANTS = [(Bd.KERNEL_TMA, t) for t in (1, 2, 3, 4, 5)] + [(Bd.KERNEL_DIRECT, 0)]
 
 
 @pytest.fixture(scope="module", autouse=True)
