@@ -52,6 +52,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--tile", type=int, default=0, help="TMA kernel variant (0 = library default)")
     ap.add_argument("--sweep-tiles", action="store_true", help="time every TMA variant, print one line each")
     return ap.parse_args()
@@ -304,6 +305,11 @@ def run_ours(args):
                         "hbm_achieved_gbs": BYTES_PER_CELL_F64 * cells / per64 / 1e9,
                         "hbm_frac": BYTES_PER_CELL_F64 * cells / per64 / 1e9 / peak, "bound": "alu (FP64)"}
 
+    # adjoint / forward cost (smooth vortex 512^2, 500 FP32 steps, checkpoints
+    # every 50; and the 4096^2 workload for the HBM-bound ratio)
+    if not args.no_adjoint:
+        line["adjoint"] = adjoint_costs(Bd, W, torch, stream)
+
     # end to end through the C ABI with pinned host buffers
     if not args.no_e2e:
         host = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in (w.rho, w.ux, w.uy, w.T)]
@@ -337,6 +343,40 @@ def run_ours(args):
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def adjoint_costs(Bd, W, torch, stream):
+    """Forward vs recorded-forward vs reverse-sweep time per step."""
+    out = {}
+    cases = [("smooth_vortex_512x512_fp32", W.smooth_vortex(n=512, nsteps=500), 500, 50),
+             ("kelvin_helmholtz_4096x4096_fp32", W.kelvin_helmholtz(n=4096, nsteps=40), 40, 10)]
+    for name, w, nsteps, ck in cases:
+        g = Bd.Grid.from_workload(w, precision=Bd.FP32, stream=stream.cuda_stream)
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
+        g.step(5)
+        torch.cuda.synchronize()
+        e[0].record(stream)
+        g.step(nsteps)
+        e[1].record(stream)
+        torch.cuda.synchronize()
+        e[2].record(stream)
+        g.adjoint_record(w.rho, w.ux, w.uy, w.T, nsteps, ck)
+        e[3].record(stream)
+        torch.cuda.synchronize()
+        dL = np.full((w.ny, w.nx), w.dx * w.dx)
+        e[4].record(stream)
+        g.adjoint_backward(dL)
+        e[5].record(stream)
+        torch.cuda.synchronize()
+        g.close()
+        fwd = e[0].elapsed_time(e[1]) / nsteps
+        rec = e[2].elapsed_time(e[3]) / nsteps
+        bwd = e[4].elapsed_time(e[5]) / nsteps
+        out[name] = {"steps": nsteps, "ckpt_every": ck, "forward_ms_per_step": fwd,
+                     "record_ms_per_step": rec, "backward_ms_per_step": bwd,
+                     "backward_over_forward": bwd / fwd,
+                     "note": "backward = segment recompute + reverse step + ghost/init adjoints + rate sums"}
+    return out
 
 
 def sweep_tiles(args):

@@ -78,15 +78,17 @@ __global__ void __launch_bounds__(ABX* ABY) adjoint_step_kernel(AdjArgs<T> a) {
             }
         }
     }
-    // block sum of the 12 rate partials, accumulated into this block's slot
+    // block sum of the 12 rate partials, accumulated into this block's slot:
+    // within a warp in the state precision (32 terms), across warps and steps
+    // in FP64
     __shared__ double red[ABX * ABY / 32][12];
     const int t = threadIdx.y * ABX + threadIdx.x;
     const int lane = t & 31, warp = t >> 5;
 #pragma unroll
     for (int j = 0; j < 12; ++j) {
-        double v = (double)gs[j];
+        T v = gs[j];
         for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        if (lane == 0) red[warp][j] = v;
+        if (lane == 0) red[warp][j] = (double)v;
     }
     __syncthreads();
     if (t < 12) {
