@@ -62,6 +62,24 @@ extern "C" mrt_status mrt_adjoint_record(mrt_grid* g, const double* rho0, const 
     dim3 agrid, ablock;
     if (g->fp64) adjoint_grid<double>(g->L, &agrid, &ablock); else adjoint_grid<float>(g->L, &agrid, &ablock);
     t->nparts = (int)(agrid.x * agrid.y);
+    if (g->kernel == MRT_KERNEL_TMA) {
+        // TMA reverse step: its own occupancy decides the row chunks
+        int occ = 0, sms = 0;
+        cudaError_t e = g->fp64 ? adjoint_tma_setup<double>(&occ) : adjoint_tma_setup<float>(&occ);
+        if (e != cudaSuccess) return mrt_fail(MRT_ECUDA, "adjoint occupancy: %s", cudaGetErrorString(e));
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, g->device);
+        if (occ < 1) occ = 1;
+        const int strips = (g->L.nx + TMA_W - 1) / TMA_W;
+        // as many row chunks as fit in one wave of resident CTAs
+        long chunks = ((long)sms * occ) / strips;
+        if (chunks < 1) chunks = 1;
+        t->adj_rows = (int)((g->L.ny + chunks - 1) / chunks);
+        if (t->adj_rows < 1) t->adj_rows = 1;
+        t->adj_gx = strips;
+        t->adj_gy = (g->L.ny + t->adj_rows - 1) / t->adj_rows;
+        t->adj_tma = 1;
+        t->nparts = std::max(t->nparts, t->adj_gx * t->adj_gy);
+    }
     A_TRY(cudaMalloc(&t->ck, t->state_bytes * (size_t)t->nck));
     A_TRY(cudaMalloc(&t->seg, t->state_bytes * (size_t)t->K));
     A_TRY(cudaMalloc(&t->lam[0], t->state_bytes));
@@ -91,6 +109,11 @@ extern "C" mrt_status mrt_adjoint_record(mrt_grid* g, const double* rho0, const 
     for (int j = 0; j < t->K; ++j)
         A_TRY(cudaMemcpyAsync(buf_at(t->seg, t->state_bytes, j), g->f[g->cur], t->state_bytes,
                               cudaMemcpyDeviceToDevice, g->stream));
+    if (t->adj_tma)
+        for (int b = 0; b < 2; ++b) {
+            st = mrt_encode_maps(g, t->lam[b], &t->lam_in[b], &t->lam_out[b]);
+            if (st != MRT_OK) return st;
+        }
     // adjoint buffers: zero everywhere, so fixed ghosts read as zero
     A_TRY(cudaMemsetAsync(t->lam[0], 0, t->state_bytes, g->stream));
     A_TRY(cudaMemsetAsync(t->lam[1], 0, t->state_bytes, g->stream));
@@ -149,7 +172,11 @@ static mrt_status backward_impl(mrt_grid* g, const double* drho, double* outs[4]
             a.lam_in = static_cast<const T*>(t->lam[cur]);
             a.f = reinterpret_cast<const T*>(buf_at(t->seg, t->state_bytes, j));
             a.lam_out = static_cast<T*>(t->lam[cur ^ 1]);
-            A_TRY(launch_adjoint_step<T>(a, g->stream));
+            if (t->adj_tma)
+                A_TRY(launch_adjoint_tma<T>(&t->lam_in[cur], &t->seg_in[j], &t->lam_out[cur ^ 1], a, t->adj_gx,
+                                            t->adj_gy, t->adj_rows, g->stream));
+            else
+                A_TRY(launch_adjoint_step<T>(a, g->stream));
             cur ^= 1;
         }
     }

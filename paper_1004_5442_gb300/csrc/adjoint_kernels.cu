@@ -9,6 +9,7 @@
 //   sum_partials   fixed-order sum of the per-block rate partials
 #include "adjoint.cuh"
 #include "internal.h"
+#include "tma.cuh"
 
 namespace mrt {
 namespace {
@@ -95,6 +96,186 @@ __global__ void __launch_bounds__(ABX* ABY) adjoint_step_kernel(AdjArgs<T> a) {
         double s = 0;
         for (int w = 0; w < ABX * ABY / 32; ++w) s += red[w][t];
         a.gpart[(long)(blockIdx.y * gridDim.x + blockIdx.x) * 12 + t] += s;
+    }
+}
+
+// --------------------------------------------------------------------------
+// TMA-staged reverse step: the strip structure of step_tma with two rings,
+// lam^{n+1} rows with a halo (rows r-1, r, r+1 are read) and f^n rows
+// (row r only), and the output row written back by one TMA store for whole
+// strips.  Rate partials stay in registers over the CTA's rows.
+// --------------------------------------------------------------------------
+constexpr int ADJ_NSL = 4;   // lam ring rows
+constexpr int ADJ_NSF = 2;   // f ring rows
+
+template <class T>
+constexpr size_t adj_tma_smem() {
+    return (ADJ_NSL + ADJ_NSF) * tma_slot_bytes<T>() + 2 * tma_out_slot_bytes<T>() + 128;
+}
+
+template <class T>
+__global__ void __launch_bounds__(TMA_W) adjoint_tma_kernel(const __grid_constant__ CUtensorMap map_lam,
+                                                            const __grid_constant__ CUtensorMap map_f,
+                                                            const __grid_constant__ CUtensorMap map_out,
+                                                            const AdjArgs<T> a, int rows_per_cta) {
+    using namespace tma;
+    constexpr int HALO = tma_halo<T>();
+    constexpr int BOXW = tma_boxw<T>();
+    constexpr uint32_t SLOT_BYTES = (uint32_t)tma_slot_bytes<T>();
+    constexpr uint32_t OUT_BYTES = (uint32_t)tma_out_slot_bytes<T>();
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    T* lring = reinterpret_cast<T*>(smem_raw);
+    T* fring = reinterpret_cast<T*>(smem_raw + ADJ_NSL * SLOT_BYTES);
+    T* outbuf = reinterpret_cast<T*>(smem_raw + (ADJ_NSL + ADJ_NSF) * SLOT_BYTES);
+    uint64_t* fullL = reinterpret_cast<uint64_t*>(smem_raw + (ADJ_NSL + ADJ_NSF) * SLOT_BYTES + 2 * OUT_BYTES);
+    uint64_t* fullF = fullL + ADJ_NSL;
+
+    const Layout& L = a.L;
+    const int tid = threadIdx.x;
+    const int x0 = blockIdx.x * TMA_W;
+    const int y0 = blockIdx.y * rows_per_cta;
+    const int nrows = min(rows_per_cta, L.ny - y0);
+    if (nrows <= 0) return;
+    const int nload = nrows + 2;  // lam rows y0..y0+nrows+1 (padded); f rows y0+1..y0+nrows
+    const int x = x0 + tid;
+    const bool active = x < L.nx;
+    const int tma_x = L.G + x0 - HALO;
+    const bool tstore = x0 + TMA_W <= L.nx;
+
+    if (tid == 0) {
+        for (int s = 0; s < ADJ_NSL; ++s) mbar_init(&fullL[s], 1);
+        for (int s = 0; s < ADJ_NSF; ++s) mbar_init(&fullF[s], 1);
+        fence_barrier_init();
+    }
+    __syncthreads();
+    auto issue_l = [&](int l) {
+        const int s = l % ADJ_NSL;
+        mbar_arrive_expect_tx(&fullL[s], SLOT_BYTES);
+        tma_load_3d(lring + (size_t)s * NV * BOXW, &map_lam, &fullL[s], tma_x, y0 + l, 0);
+    };
+    auto issue_f = [&](int j) {  // f row j = local row j+1
+        const int s = j % ADJ_NSF;
+        mbar_arrive_expect_tx(&fullF[s], SLOT_BYTES);
+        tma_load_3d(fring + (size_t)s * NV * BOXW, &map_f, &fullF[s], tma_x, y0 + 1 + j, 0);
+    };
+    int issuedL = 0, issuedF = 0, waitedL = 0, waitedF = 0;  // thread 0 bookkeeping
+    if (tid == 0) {
+        issuedL = min(ADJ_NSL, nload);
+        for (int l = 0; l < issuedL; ++l) issue_l(l);
+        issuedF = min(ADJ_NSF, nrows);
+        for (int j = 0; j < issuedF; ++j) issue_f(j);
+    }
+    auto wait_l = [&](int l) -> bool {
+        const bool ok = mbar_wait_bounded(&fullL[l % ADJ_NSL], (uint32_t)((l / ADJ_NSL) & 1));
+        if (tid == 0 && ok && l == waitedL) waitedL = l + 1;
+        return ok;
+    };
+    auto wait_f = [&](int j) -> bool {
+        const bool ok = mbar_wait_bounded(&fullF[j % ADJ_NSF], (uint32_t)((j / ADJ_NSF) & 1));
+        if (tid == 0 && ok && j == waitedF) waitedF = j + 1;
+        return ok;
+    };
+    auto drain = [&]() {
+        if (tid == 0) {
+            for (int l = waitedL; l < issuedL; ++l) mbar_wait_bounded(&fullL[l % ADJ_NSL], (uint32_t)((l / ADJ_NSL) & 1));
+            for (int j = waitedF; j < issuedF; ++j) mbar_wait_bounded(&fullF[j % ADJ_NSF], (uint32_t)((j / ADJ_NSF) & 1));
+            bulk_wait_all();
+        }
+    };
+    bool ok = wait_l(0);
+    ok = wait_l(1) && ok;
+    ok = wait_l(2) && ok;
+    if (__syncthreads_or(!ok)) { drain(); return; }
+
+    T gs[12];
+#pragma unroll
+    for (int j = 0; j < 12; ++j) gs[j] = 0;
+    const int col = tid + HALO;
+#pragma unroll 1
+    for (int r = 1; r <= nrows; ++r) {
+        const int y = y0 + r - 1;
+        T* ob = outbuf + (size_t)(r & 1) * NV * TMA_W;
+        ok = wait_f(r - 1);
+        if (active && ok) {
+            const T* sm = lring + (size_t)((r - 1) % ADJ_NSL) * NV * BOXW;
+            const T* sc = lring + (size_t)(r % ADJ_NSL) * NV * BOXW;
+            const T* sp = lring + (size_t)((r + 1) % ADJ_NSL) * NV * BOXW;
+            const T* sf = fring + (size_t)((r - 1) % ADJ_NSF) * NV * BOXW;
+            auto LF = [&](int i, int pos) -> T {
+                switch (pos) {
+                    case C: return sc[i * BOXW + col];
+                    case XM: return sc[i * BOXW + col - 1];
+                    case XP: return sc[i * BOXW + col + 1];
+                    case YM: return sm[i * BOXW + col];
+                    default: return sp[i * BOXW + col];
+                }
+            };
+            T f[NV];
+#pragma unroll
+            for (int i = 0; i < NV; ++i) f[i] = sf[i * BOXW + col];
+            T out[NV];
+            cell_adjoint<T>(LF, f, a.k, out, gs);
+#pragma unroll
+            for (int i = 0; i < NV; ++i) ob[i * TMA_W + tid] = out[i];
+            if (!a.per_x && (x == 0 || x == L.nx - 1)) {
+                const int side = x == 0 ? 0 : 1;
+                for (int i = 0; i < NV; ++i)
+                    a.gxb[((long)i * 2 + side) * L.ny + y] += (double)(lw_weight<T>(a.k, i, side == 0 ? XM : XP) * LF(i, C));
+            }
+            if (!a.per_y && (y == 0 || y == L.ny - 1)) {
+                const int side = y == 0 ? 0 : 1;
+                for (int i = 0; i < NV; ++i)
+                    a.gyb[((long)i * 2 + side) * L.nx + x] += (double)(lw_weight<T>(a.k, i, side == 0 ? YM : YP) * LF(i, C));
+            }
+        }
+        fence_async_shared();
+        if (tid == 0) bulk_wait_read_all();
+        if (r + 2 < nload) ok = wait_l(r + 2) && ok;
+        if (__syncthreads_or(!ok)) { drain(); return; }
+        if (tid == 0) {
+            if (tstore) {
+                tma_store_3d(&map_out, ob, L.G + x0, y + 1, 0);
+                if (a.per_y && y == 0) tma_store_3d(&map_out, ob, L.G + x0, L.ny + 1, 0);
+                if (a.per_y && y == L.ny - 1) tma_store_3d(&map_out, ob, L.G + x0, 0, 0);
+                bulk_commit();
+            }
+            const int l = r - 1 + ADJ_NSL;
+            if (l < nload) { issue_l(l); issuedL = l + 1; }
+            const int j = r - 1 + ADJ_NSF;
+            if (j < nrows) { issue_f(j); issuedF = j + 1; }
+        }
+        if (!tstore && active) {
+            const long c0 = (long)(y + 1) * L.pitch + L.G + x;
+#pragma unroll 4
+            for (int i = 0; i < NV; ++i) {
+                const T v = ob[i * TMA_W + tid];
+                a.lam_out[i * L.plane + c0] = v;
+                if (a.per_y && y == 0) a.lam_out[i * L.plane + (long)(L.ny + 1) * L.pitch + L.G + x] = v;
+                if (a.per_y && y == L.ny - 1) a.lam_out[i * L.plane + L.G + x] = v;
+            }
+        }
+        if (a.per_x && active && (x == 0 || x == L.nx - 1)) {
+            const long gc = (long)(y + 1) * L.pitch + (x == 0 ? L.G + L.nx : L.G - 1);
+#pragma unroll 4
+            for (int i = 0; i < NV; ++i) a.lam_out[i * L.plane + gc] = ob[i * TMA_W + tid];
+        }
+    }
+    if (tid == 0) bulk_wait_all();
+
+    // CTA sum of the rate partials into this CTA's slot
+    __shared__ double red[TMA_W / 32][12];
+    const int lane = tid & 31, warp = tid >> 5;
+#pragma unroll
+    for (int j = 0; j < 12; ++j) {
+        T v = gs[j];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) red[warp][j] = (double)v;
+    }
+    __syncthreads();
+    if (tid < 12) {
+        double s = 0;
+        for (int w = 0; w < TMA_W / 32; ++w) s += red[w][tid];
+        a.gpart[(long)(blockIdx.y * gridDim.x + blockIdx.x) * 12 + tid] += s;
     }
 }
 
@@ -251,12 +432,31 @@ cudaError_t launch_init_adjoint(const Layout& L, const InitCoef& ic, const Coef<
     return cudaGetLastError();
 }
 
+template <class T>
+cudaError_t adjoint_tma_setup(int* blocks_per_sm) {
+    const size_t smem = adj_tma_smem<T>();
+    cudaError_t e = cudaFuncSetAttribute(adjoint_tma_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, adjoint_tma_kernel<T>, TMA_W, smem);
+}
+
+template <class T>
+cudaError_t launch_adjoint_tma(const CUtensorMap* map_lam, const CUtensorMap* map_f, const CUtensorMap* map_out,
+                               const AdjArgs<T>& a, int grid_x, int grid_y, int rows_per_cta, cudaStream_t st) {
+    adjoint_tma_kernel<T><<<dim3(grid_x, grid_y), TMA_W, adj_tma_smem<T>(), st>>>(*map_lam, *map_f, *map_out, a,
+                                                                                  rows_per_cta);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_sum_partials(const double* gpart, int nparts, double* out, cudaStream_t st) {
     sum_partials_kernel<<<1, 256, 0, st>>>(gpart, nparts, out);
     return cudaGetLastError();
 }
 
 #define INST(T)                                                                                                 \
+    template cudaError_t adjoint_tma_setup<T>(int*);                                                            \
+    template cudaError_t launch_adjoint_tma<T>(const CUtensorMap*, const CUtensorMap*, const CUtensorMap*,      \
+                                               const AdjArgs<T>&, int, int, int, cudaStream_t);                 \
     template void adjoint_grid<T>(const Layout&, dim3*, dim3*);                                                 \
     template cudaError_t launch_adjoint_step<T>(const AdjArgs<T>&, cudaStream_t);                               \
     template cudaError_t launch_lam_from_drho<T>(const Layout&, const double*, T*, cudaStream_t);               \

@@ -481,7 +481,8 @@ extern "C" mrt_status mrt_create(const mrt_params* params, const double* rho, co
         if (occ < 1) occ = 1;
         const int strips = (params->nx + TMA_W - 1) / TMA_W;
         const long resident = (long)sms * occ;
-        long chunks = (resident + strips - 1) / strips;
+        // as many row chunks as fit in one wave of resident CTAs
+        long chunks = resident / strips;
         if (chunks < 1) chunks = 1;
         int rows = (int)((params->ny + chunks - 1) / chunks);
         if (rows < 1) rows = 1;

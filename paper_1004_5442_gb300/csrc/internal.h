@@ -71,7 +71,7 @@ inline TileCfg tile_cfg(int tile) {
         default: return {4, 1, 4, "ring4-tma-4cta-ywin"};
     }
 }
-template <class T> constexpr int default_tile() { return sizeof(T) == 4 ? 2 : 1; }
+template <class T> constexpr int default_tile() { return sizeof(T) == 4 ? 4 : 1; }
 
 template <class T>
 inline size_t tma_smem_bytes(int tile) {
@@ -121,6 +121,11 @@ cudaError_t launch_init_adjoint(const Layout& L, const InitCoef& ic, const Coef<
                                 const double* rho, const double* ux, const double* uy, const double* Tf,
                                 double* g_rho, double* g_ux, double* g_uy, double* g_T, cudaStream_t st);
 cudaError_t launch_sum_partials(const double* gpart, int nparts, double* out, cudaStream_t st);
+template <class T>
+cudaError_t adjoint_tma_setup(int* blocks_per_sm);
+template <class T>
+cudaError_t launch_adjoint_tma(const CUtensorMap* map_lam, const CUtensorMap* map_f, const CUtensorMap* map_out,
+                               const AdjArgs<T>& a, int grid_x, int grid_y, int rows_per_cta, cudaStream_t st);
 
 }  // namespace mrt
 
@@ -144,6 +149,9 @@ struct mrt_tape {
     double* gpart = nullptr;
     int nparts = 0;
     double* scratch = nullptr;  // 8 fields of nx*ny doubles + 12 sums
+    // TMA reverse step: maps of the two adjoint buffers and its launch shape
+    CUtensorMap lam_in[2], lam_out[2];
+    int adj_tma = 0, adj_gx = 0, adj_gy = 0, adj_rows = 0;
 };
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
                                   const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,

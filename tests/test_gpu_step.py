@@ -255,7 +255,7 @@ def test_full_size_kh_sampled_windows():
     corners = [(0, 0), (w.ny - n, w.nx - n), (0, w.nx - n), (w.ny - n, 0), (2000, 128 * 16 - 24)]
     wins = corners + [(int(rng.integers(0, w.ny - n)), int(rng.integers(0, w.nx - n))) for _ in range(7)]
     with Bd.Grid.from_workload(w, precision=Bd.FP32, kernel=Bd.KERNEL_TMA) as grid:
-        assert grid.info()["kernel"] == Bd.KERNEL_TMA and grid.info()["tile"] == 2
+        assert grid.info()["kernel"] == Bd.KERNEL_TMA and grid.info()["tile"] == 4
         grid.step(3)
         f3 = grid.get_f()
         grid.step(1)
