@@ -37,7 +37,8 @@ sys.path.insert(0, ROOT)
 BYTES_PER_CELL_F32 = 128      # 16 f_i read + 16 written, 4 bytes each
 BYTES_PER_CELL_F64 = 256
 FALLBACK_HBM_GBS = 6800.0
-KERNEL_SOURCES = ["paper_1004_5442_gb300/csrc/step_kernels.cu", "paper_1004_5442_gb300/csrc/model.cuh",
+KERNEL_SOURCES = ["paper_1004_5442_gb300/csrc/step_kernels.cu", "paper_1004_5442_gb300/csrc/step_strip.cuh",
+                  "paper_1004_5442_gb300/csrc/tma.cuh", "paper_1004_5442_gb300/csrc/model.cuh",
                   "paper_1004_5442_gb300/csrc/internal.h"]
 PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "step_tma_f32_kh4096.md")
 
@@ -53,6 +54,8 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--batch-steps", type=int, default=1000, help="timed steps of the 256-instance sweep")
     ap.add_argument("--tile", type=int, default=0, help="TMA kernel variant (0 = library default)")
     ap.add_argument("--sweep-tiles", action="store_true", help="time every TMA variant, print one line each")
     return ap.parse_args()
@@ -310,6 +313,10 @@ def run_ours(args):
     if not args.no_adjoint:
         line["adjoint"] = adjoint_costs(Bd, W, torch, stream)
 
+    # 256 independent tube/ripple instances of uneven size, one launch per step
+    if not args.no_batch:
+        line["batch"] = batch_sweep(Bd, W, torch, args, peak)
+
     # end to end through the C ABI with pinned host buffers
     if not args.no_e2e:
         host = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in (w.rho, w.ux, w.uy, w.T)]
@@ -381,6 +388,47 @@ def adjoint_costs(Bd, W, torch, stream):
                      "note": "device-resident fields and gradients; backward = segment recompute + "
                              "reverse step + ghost/init adjoints + rate sums"}
     return out
+
+
+def batch_sweep(Bd, W, torch, args, peak):
+    """The 256-instance sweep (oracle-screened draws, FP32): autotuned kernel
+    variant and work-item height, then K timed steps of every instance
+    (graph replays on the batch's stream, CUDA events on that stream)."""
+    from paper_1004_5442_gb300 import autotune as AT
+    here = os.path.dirname(os.path.abspath(__file__))
+    with open(os.path.join(here, "tests", "golden", "riemann_instances_screened.json")) as fh:
+        screened = json.load(fh)
+    ws = W.riemann_instances(count=256, accepted=screened["accepted"])
+    cells = sum(w.nx * w.ny for w in ws)
+    t0 = time.perf_counter()
+    tuned = AT.tune_workloads(ws, use_cache=False)
+    tune_s = time.perf_counter() - t0
+    with Bd.Batch(ws) as b:
+        b.tune(tuned["tile"], tuned["rows_per_item"])
+        info = b.info()
+        st = torch.cuda.ExternalStream(b.stream)
+        b.step(3)
+        b.sync()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        k = args.batch_steps
+        e0.record(st)
+        b.step(k)
+        e1.record(st)
+        torch.cuda.synchronize()
+        b.sync()
+        ms = e0.elapsed_time(e1)
+        healthy = sum(b.grid(i).health() == Bd.MRT_OK for i in range(len(ws)))
+    per_s = ms * 1e-3 / k
+    gbs = BYTES_PER_CELL_F32 * cells / per_s / 1e9
+    return {"workload": "riemann_ripple_sweep_256_fp32", "instances": len(ws), "cells": cells,
+            "value": cells / per_s, "unit": "cell-updates/s", "steps": k, "ms_per_step": ms / k,
+            "hbm_achieved_gbs": gbs, "hbm_frac": gbs / peak, "launches_per_step": 1,
+            "tile": info["tile"], "rows_per_item": info["rows_per_item"], "ctas": info["ctas"],
+            "work_items": info["items"], "autotune_s": tune_s,
+            "autotune": [(d["tile"], d["rows_per_item"], round(d["ms_per_step"], 4)) for d in tuned["timings"]],
+            "healthy_after": {"steps": k + 3, "instances_ok": healthy},
+            "screening": {"acceptance_rate": screened["acceptance_rate"],
+                          "rule": "FP64 oracle 1-D pre-run, 1000 steps, rho and T finite and positive"}}
 
 
 def sweep_tiles(args):

@@ -190,6 +190,45 @@ mrt_status mrt_adjoint_step(mrt_grid *g, const void *f, const void *lam_next, vo
 mrt_status mrt_conserved_totals_static(const void *f, int precision, int nx, int ny, double dx,
                                        double *out, void *stream);
 
+/* Batched independent grids (many instances of uneven size, gamma, Pr and
+ * rates advanced together).  Every time step is one kernel launch covering
+ * all instances' work items (instance x 128-column strip x chunk of rows),
+ * balanced by cells over one wave of resident CTAs; two consecutive steps
+ * are captured once in a CUDA graph and replayed.  Each instance is an
+ * ordinary FP32 grid with the TMA step kernel; its handle (mrt_batch_grid)
+ * serves for readout (mrt_get_macro, mrt_get_f, mrt_conserved_totals,
+ * mrt_health) but must not be stepped, re-initialised or destroyed by
+ * itself.  Batch work runs on a stream the batch owns; the readout calls
+ * synchronise it.  The per-instance step constants live in a table of 256
+ * slots per device shared by all live batches.
+ *
+ * mrt_batch_create: n in 1..256 instances; params[i] as for mrt_create
+ * (precision must be MRT_FP32; kernel and tile are overridden), fields
+ * rho[i], ux[i], uy[i], T[i] ([ny_i][nx_i] doubles, on the device if
+ * fields_on_device).  Errors: MRT_EINVAL, MRT_ENOMEM (also when the
+ * constant table is full), MRT_ECUDA.
+ * mrt_batch_step: advance every instance nsteps >= 0 steps (asynchronous).
+ * mrt_batch_tune: choose the kernel variant (tile 2, 4 or 5, as in
+ * mrt_params) and the rows per work item (>= 1); rebuilds the work list and
+ * the graph.  Results do not depend on the choice.
+ * mrt_batch_grid: handle of instance i (synchronises the batch stream).
+ * mrt_batch_info: instances, tile, rows per item, CTAs and work items.
+ * mrt_batch_sync: wait for the batch's work.
+ * mrt_batch_stream: the batch's cudaStream_t (owned by the batch; valid
+ * until mrt_batch_destroy), for events or waits a caller records on it. */
+typedef struct mrt_batch mrt_batch;
+mrt_status mrt_batch_create(int n, const mrt_params *params, const double *const *rho,
+                            const double *const *ux, const double *const *uy, const double *const *T,
+                            int fields_on_device, mrt_batch **out);
+mrt_status mrt_batch_step(mrt_batch *b, long nsteps);
+mrt_status mrt_batch_tune(mrt_batch *b, int tile, int rows_per_item);
+mrt_status mrt_batch_grid(mrt_batch *b, int i, mrt_grid **g);
+mrt_status mrt_batch_info(const mrt_batch *b, int *n, int *tile, int *rows_per_item, int *ctas,
+                          int *items);
+mrt_status mrt_batch_sync(mrt_batch *b);
+mrt_status mrt_batch_stream(const mrt_batch *b, void **stream);
+void mrt_batch_destroy(mrt_batch *b);
+
 /* Release every device resource of the grid (synchronises its stream). */
 void mrt_destroy(mrt_grid *g);
 

@@ -25,7 +25,9 @@ KERNEL_AUTO, KERNEL_TMA, KERNEL_DIRECT = 0, 1, 2
 EXPORTED = ["mrt_create", "mrt_step", "mrt_get_macro", "mrt_conserved_totals", "mrt_get_f",
             "mrt_set_f", "mrt_health", "mrt_info", "mrt_destroy", "mrt_status_str",
             "mrt_last_error", "mrt_conserved_totals_static", "mrt_adjoint_record",
-            "mrt_adjoint_backward", "mrt_adjoint_step"]
+            "mrt_adjoint_backward", "mrt_adjoint_step", "mrt_batch_create", "mrt_batch_step",
+            "mrt_batch_tune", "mrt_batch_grid", "mrt_batch_info", "mrt_batch_sync", "mrt_batch_stream",
+            "mrt_batch_destroy"]
 
 
 class MrtError(RuntimeError):
@@ -76,9 +78,22 @@ def load(path: str = LIB_PATH):
     L.mrt_adjoint_record.argtypes = [vp, vp, vp, vp, vp, ip, ctypes.c_long, ip]
     L.mrt_adjoint_backward.argtypes = [vp, vp, ip, vp, vp, vp, vp, dp]
     L.mrt_adjoint_step.argtypes = [vp, vp, vp, vp, ip, dp]
+    vpp = ctypes.POINTER(ctypes.c_void_p)
+    L.mrt_batch_create.argtypes = [ip, ctypes.POINTER(Params), vpp, vpp, vpp, vpp, ip, ctypes.POINTER(vp)]
+    L.mrt_batch_step.argtypes = [vp, ctypes.c_long]
+    L.mrt_batch_tune.argtypes = [vp, ip, ip]
+    L.mrt_batch_grid.argtypes = [vp, ip, ctypes.POINTER(vp)]
+    ipp = ctypes.POINTER(ctypes.c_int)
+    L.mrt_batch_info.argtypes = [vp, ipp, ipp, ipp, ipp, ipp]
+    L.mrt_batch_sync.argtypes = [vp]
+    L.mrt_batch_stream.argtypes = [vp, ctypes.POINTER(vp)]
+    L.mrt_batch_destroy.argtypes = [vp]
+    L.mrt_batch_destroy.restype = None
     for name in ("mrt_create", "mrt_step", "mrt_get_macro", "mrt_conserved_totals", "mrt_get_f",
                  "mrt_set_f", "mrt_health", "mrt_info", "mrt_conserved_totals_static",
-                 "mrt_adjoint_record", "mrt_adjoint_backward", "mrt_adjoint_step"):
+                 "mrt_adjoint_record", "mrt_adjoint_backward", "mrt_adjoint_step", "mrt_batch_create",
+                 "mrt_batch_step", "mrt_batch_tune", "mrt_batch_grid", "mrt_batch_info", "mrt_batch_sync",
+                 "mrt_batch_stream"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -150,6 +165,15 @@ class Grid:
         check(L.mrt_create(ctypes.byref(params), *(ctypes.c_void_p(_ptr(a)) for a in arrs),
                            on_dev, ctypes.c_void_p(stream), ctypes.byref(h)))
         self._h = h
+
+    @classmethod
+    def view(cls, handle, nx, ny, fp64=False):
+        """A non-owning wrapper of a grid handle (e.g. a batch instance)."""
+        g = cls.__new__(cls)
+        g._h = ctypes.c_void_p(handle)
+        g.nx, g.ny, g.fp64 = nx, ny, fp64
+        g._owned = False
+        return g
 
     @classmethod
     def from_workload(cls, w, precision=FP32, kernel=KERNEL_AUTO, stream=None, tile=0):
@@ -234,8 +258,79 @@ class Grid:
                 "kernel": kern.value, "tile": tile.value}
 
     def close(self) -> None:
+        if not getattr(self, "_owned", True):
+            return
         if getattr(self, "_h", None) is not None and self._h.value:
             load().mrt_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+class Batch:
+    """Independent FP32 grids advanced together (mrt_batch_*)."""
+
+    def __init__(self, workloads, fields_on_device=False):
+        L = load()
+        n = len(workloads)
+        params = (Params * n)()
+        self.shapes = []
+        keep = []
+        ptrs = [(ctypes.c_void_p * n)() for _ in range(4)]
+        for i, w in enumerate(workloads):
+            params[i] = make_params(w.nx, w.ny, w.dx, w.dt, w.gamma, w.s, w.bc_x, w.bc_y, FP32)
+            arrs = [np.ascontiguousarray(np.broadcast_to(np.asarray(a, dtype=np.float64), (w.ny, w.nx)))
+                    for a in (w.rho, w.ux, w.uy, w.T)]
+            keep.append(arrs)
+            for q in range(4):
+                ptrs[q][i] = arrs[q].ctypes.data
+            self.shapes.append((w.nx, w.ny))
+        h = ctypes.c_void_p()
+        check(L.mrt_batch_create(n, params, *(ctypes.cast(p, ctypes.POINTER(ctypes.c_void_p)) for p in ptrs),
+                                 0, ctypes.byref(h)))
+        self._h = h
+        self.n = n
+
+    def step(self, n: int = 1) -> None:
+        check(load().mrt_batch_step(self._h, int(n)))
+
+    def tune(self, tile: int, rows_per_item: int) -> None:
+        check(load().mrt_batch_tune(self._h, int(tile), int(rows_per_item)))
+
+    def sync(self) -> None:
+        check(load().mrt_batch_sync(self._h))
+
+    @property
+    def stream(self) -> int:
+        """Raw cudaStream_t the batch launches on (for events)."""
+        h = ctypes.c_void_p()
+        check(load().mrt_batch_stream(self._h, ctypes.byref(h)))
+        return h.value or 0
+
+    def info(self) -> dict:
+        v = [ctypes.c_int() for _ in range(5)]
+        check(load().mrt_batch_info(self._h, *(ctypes.byref(x) for x in v)))
+        return dict(zip(("n", "tile", "rows_per_item", "ctas", "items"), (x.value for x in v)))
+
+    def grid(self, i: int) -> Grid:
+        h = ctypes.c_void_p()
+        check(load().mrt_batch_grid(self._h, int(i), ctypes.byref(h)))
+        nx, ny = self.shapes[i]
+        return Grid.view(h.value, nx, ny, False)
+
+    def close(self) -> None:
+        if getattr(self, "_h", None) is not None and self._h.value:
+            load().mrt_batch_destroy(self._h)
             self._h = ctypes.c_void_p()
 
     def __del__(self):

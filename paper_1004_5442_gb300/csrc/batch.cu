@@ -1,0 +1,359 @@
+// batch.cu - many independent grids advanced together: every time step is
+// one launch that covers all instances' work items (instance x 128-column
+// strip x chunk of rows), and a pair of steps is captured once in a CUDA
+// graph that mrt_batch_step replays.  Each instance is an ordinary grid
+// (created by mrt_create, so initialisation, ghosts, tensor maps, readout and
+// health are the single-grid ones); the batch adds
+//   - a __constant__ table of the instances' step constants (the
+//     relaxation rates, b, and Lax-Wendroff weights differ per instance),
+//   - a device table of instance descriptors and their tensor maps,
+//   - a work list balanced by cells over one wave of resident CTAs.
+// Kernel boundaries order the steps, so no device-side grid barrier exists.
+#include <algorithm>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <numeric>
+#include <vector>
+
+#include "internal.h"
+#include "step_strip.cuh"
+
+using namespace mrt;
+
+namespace {
+
+constexpr int kCoefSlots = 256;                     // instances across all live batches (per device)
+__constant__ Coef<float> c_batch_coef[kCoefSlots];  // 52 floats each: 53 KB
+
+std::mutex g_slot_mu;
+bool g_slot_used[kCoefSlots] = {};
+
+struct BatchInst {
+    Layout L;
+    int per_x, per_y;
+    float* f[2];
+    unsigned* flag;
+    int cslot;
+    int pad;
+    const CUtensorMap* maps;  // [load0, load1, store0, store1]
+};
+
+struct Item {
+    int inst, x0, y0, nrows;
+};
+
+template <int NS, bool TSTORE, bool YWIN, int MINB>
+__global__ void __launch_bounds__(TMA_W, MINB) batch_step_kernel(const BatchInst* __restrict__ insts,
+                                                                 const Item* __restrict__ items,
+                                                                 const int* __restrict__ item_begin, int parity) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    const int i0 = item_begin[blockIdx.x], i1 = item_begin[blockIdx.x + 1];
+    if (i0 >= i1) return;
+    StripRing<float> R = strip_ring_init<float, NS, TSTORE>(smem_raw);
+    for (int it = i0; it < i1; ++it) {
+        const Item w = items[it];
+        const BatchInst& I = insts[w.inst];
+        const Layout L = I.L;
+        const CUtensorMap* mi = I.maps + parity;
+        const CUtensorMap* mo = I.maps + 2 + (parity ^ 1);
+        bool bad = false;
+        if (!strip_chunk<float, false, NS, TSTORE, YWIN>(R, mi, mo, L, I.per_x, I.per_y, I.f[parity ^ 1],
+                                                         c_batch_coef[I.cslot], w.x0, w.y0, w.nrows, bad,
+                                                         (Acc<float>*)nullptr)) {
+            strip_drain<float, NS>(R, I.flag);
+            return;
+        }
+        if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(I.flag, FLAG_UNSTABLE);
+    }
+}
+
+template <int NS, bool TSTORE, bool YWIN, int MINB>
+struct BatchKernel {
+    static size_t smem() {
+        return NS * tma_slot_bytes<float>() + (TSTORE ? 2 * tma_out_slot_bytes<float>() : 0) + 64;
+    }
+    static cudaError_t setup(int* occ) {
+        cudaError_t e = cudaFuncSetAttribute(batch_step_kernel<NS, TSTORE, YWIN, MINB>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem());
+        if (e != cudaSuccess) return e;
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, batch_step_kernel<NS, TSTORE, YWIN, MINB>, TMA_W,
+                                                             smem());
+    }
+    static cudaError_t launch(int grid, const BatchInst* insts, const Item* items, const int* begin, int parity,
+                              cudaStream_t st) {
+        batch_step_kernel<NS, TSTORE, YWIN, MINB><<<grid, TMA_W, smem(), st>>>(insts, items, begin, parity);
+        return cudaGetLastError();
+    }
+};
+
+template <class Fn>
+cudaError_t with_batch_tile(int tile, Fn&& fn) {
+    switch (tile) {
+        case 2: return fn(BatchKernel<4, true, false, 4>());
+        case 4: return fn(BatchKernel<5, true, false, 3>());
+        case 5: return fn(BatchKernel<4, true, true, 4>());
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace
+
+struct mrt_batch {
+    int n = 0;
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    std::vector<mrt_grid*> grids;
+    std::vector<int> slots;
+    BatchInst* d_insts = nullptr;
+    CUtensorMap* d_maps = nullptr;
+    Item* d_items = nullptr;
+    int* d_begin = nullptr;
+    int tile = 4, rows_per_item = 64, grid = 0, nitems = 0;
+    cudaGraphExec_t exec = nullptr;
+    long steps = 0;
+};
+
+static void batch_release(mrt_batch* b) {
+    if (!b) return;
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    for (mrt_grid* g : b->grids) mrt_destroy(g);
+    cudaFree(b->d_insts);
+    cudaFree(b->d_maps);
+    cudaFree(b->d_items);
+    cudaFree(b->d_begin);
+    {
+        std::lock_guard<std::mutex> lock(g_slot_mu);
+        for (int s : b->slots) g_slot_used[s] = false;
+    }
+    if (b->stream) cudaStreamDestroy(b->stream);
+    delete b;
+}
+
+// Work list: items of up to rows_per_item rows per strip, assigned to `grid`
+// CTAs longest-first to the least-loaded CTA (cost = cells + a per-item
+// start-up term), then laid out CTA by CTA.
+static mrt_status build_work(mrt_batch* b) {
+    struct W { Item it; double cost; };
+    std::vector<W> ws;
+    for (int i = 0; i < b->n; ++i) {
+        const Layout& L = b->grids[i]->L;
+        for (int x0 = 0; x0 < L.nx; x0 += TMA_W)
+            for (int y0 = 0; y0 < L.ny; y0 += b->rows_per_item) {
+                const int nr = std::min(b->rows_per_item, L.ny - y0);
+                const int w = std::min(TMA_W, L.nx - x0);
+                ws.push_back({{i, x0, y0, nr}, (double)TMA_W * (nr + 2) + 0.0 * w});
+            }
+    }
+    std::sort(ws.begin(), ws.end(), [](const W& a, const W& c) { return a.cost > c.cost; });
+    std::vector<std::vector<Item>> per(b->grid);
+    std::vector<double> load(b->grid, 0.0);
+    for (const W& w : ws) {
+        const int c = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+        per[c].push_back(w.it);
+        load[c] += w.cost + 2.0 * TMA_W;  // prologue of an item ~ two extra rows
+    }
+    std::vector<Item> items;
+    std::vector<int> begin(b->grid + 1, 0);
+    for (int c = 0; c < b->grid; ++c) {
+        begin[c] = (int)items.size();
+        items.insert(items.end(), per[c].begin(), per[c].end());
+    }
+    begin[b->grid] = (int)items.size();
+    b->nitems = (int)items.size();
+    cudaFree(b->d_items);
+    cudaFree(b->d_begin);
+    b->d_items = nullptr;
+    b->d_begin = nullptr;
+    cudaError_t e;
+    if ((e = cudaMalloc(&b->d_items, sizeof(Item) * std::max<size_t>(items.size(), 1))) != cudaSuccess ||
+        (e = cudaMalloc(&b->d_begin, sizeof(int) * begin.size())) != cudaSuccess)
+        return mrt_fail(MRT_ENOMEM, "batch work list: %s", cudaGetErrorString(e));
+    if ((e = cudaMemcpy(b->d_items, items.data(), sizeof(Item) * items.size(), cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemcpy(b->d_begin, begin.data(), sizeof(int) * begin.size(), cudaMemcpyHostToDevice)) != cudaSuccess)
+        return mrt_fail(MRT_ECUDA, "batch work list: %s", cudaGetErrorString(e));
+    return MRT_OK;
+}
+
+static mrt_status build_graph(mrt_batch* b) {
+    if (b->exec) {
+        cudaGraphExecDestroy(b->exec);
+        b->exec = nullptr;
+    }
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return mrt_fail(MRT_ECUDA, "capture: %s", cudaGetErrorString(e));
+    for (int parity = 0; parity < 2; ++parity) {
+        e = with_batch_tile(b->tile, [&](auto k) {
+            return k.launch(b->grid, b->d_insts, b->d_items, b->d_begin, parity, b->stream);
+        });
+        if (e != cudaSuccess) break;
+    }
+    cudaError_t e2 = cudaStreamEndCapture(b->stream, &graph);
+    if (e != cudaSuccess || e2 != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        return mrt_fail(MRT_ECUDA, "capture: %s", cudaGetErrorString(e != cudaSuccess ? e : e2));
+    }
+    e = cudaGraphInstantiate(&b->exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return mrt_fail(MRT_ECUDA, "graph instantiate: %s", cudaGetErrorString(e));
+    return MRT_OK;
+}
+
+extern "C" mrt_status mrt_batch_tune(mrt_batch* b, int tile, int rows_per_item) {
+    if (!b) return mrt_fail(MRT_EINVAL, "batch is NULL");
+    if (tile != 2 && tile != 4 && tile != 5) return mrt_fail(MRT_EINVAL, "batch tile must be 2, 4 or 5");
+    if (rows_per_item < 1) return mrt_fail(MRT_EINVAL, "rows_per_item must be >= 1");
+    int occ = 0, sms = 0;
+    cudaError_t e = with_batch_tile(tile, [&](auto k) { return k.setup(&occ); });
+    if (e != cudaSuccess) return mrt_fail(MRT_ECUDA, "batch occupancy: %s", cudaGetErrorString(e));
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device);
+    cudaStreamSynchronize(b->stream);
+    b->tile = tile;
+    b->rows_per_item = rows_per_item;
+    b->grid = std::max(1, sms * std::max(occ, 1));
+    mrt_status st = build_work(b);
+    if (st != MRT_OK) return st;
+    return build_graph(b);
+}
+
+extern "C" mrt_status mrt_batch_create(int n, const mrt_params* params, const double* const* rho,
+                                       const double* const* ux, const double* const* uy, const double* const* T,
+                                       int fields_on_device, mrt_batch** out) {
+    if (!out || !params || !rho || !ux || !uy || !T) return mrt_fail(MRT_EINVAL, "null argument");
+    if (n < 1 || n > kCoefSlots) return mrt_fail(MRT_EINVAL, "batch size must be 1..%d", kCoefSlots);
+    *out = nullptr;
+    for (int i = 0; i < n; ++i)
+        if (params[i].precision != MRT_FP32) return mrt_fail(MRT_EINVAL, "batched instances are FP32 (instance %d)", i);
+    mrt_batch* b = new (std::nothrow) mrt_batch();
+    if (!b) return mrt_fail(MRT_ENOMEM, "host allocation failed");
+    b->n = n;
+    cudaGetDevice(&b->device);
+    cudaError_t e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) { batch_release(b); return mrt_fail(MRT_ECUDA, "stream: %s", cudaGetErrorString(e)); }
+    {
+        std::lock_guard<std::mutex> lock(g_slot_mu);
+        for (int s = 0; s < kCoefSlots && (int)b->slots.size() < n; ++s)
+            if (!g_slot_used[s]) { g_slot_used[s] = true; b->slots.push_back(s); }
+    }
+    if ((int)b->slots.size() < n) {
+        batch_release(b);
+        return mrt_fail(MRT_ENOMEM, "constant table full: %d instances fit across all live batches", kCoefSlots);
+    }
+    b->grids.assign(n, nullptr);
+    std::vector<BatchInst> hi(n);
+    std::vector<CUtensorMap> maps(4 * (size_t)n);
+    for (int i = 0; i < n; ++i) {
+        mrt_params p = params[i];
+        p.kernel = MRT_KERNEL_TMA;
+        p.tile = 4;
+        mrt_status st = mrt_create(&p, rho[i], ux[i], uy[i], T[i], fields_on_device, b->stream, &b->grids[i]);
+        if (st != MRT_OK) { batch_release(b); return st; }
+        mrt_grid* g = b->grids[i];
+        if ((e = cudaMemcpyToSymbolAsync(c_batch_coef, &g->kf, sizeof(Coef<float>), sizeof(Coef<float>) * b->slots[i],
+                                         cudaMemcpyHostToDevice, b->stream)) != cudaSuccess) {
+            batch_release(b);
+            return mrt_fail(MRT_ECUDA, "coefficients: %s", cudaGetErrorString(e));
+        }
+        hi[i].L = g->L;
+        hi[i].per_x = g->p.bc_x == MRT_BC_PERIODIC;
+        hi[i].per_y = g->p.bc_y == MRT_BC_PERIODIC;
+        hi[i].f[0] = static_cast<float*>(g->f[0]);
+        hi[i].f[1] = static_cast<float*>(g->f[1]);
+        hi[i].flag = g->flag;
+        hi[i].cslot = b->slots[i];
+        maps[4 * i + 0] = g->maps[0];
+        maps[4 * i + 1] = g->maps[1];
+        maps[4 * i + 2] = g->maps_out[0];
+        maps[4 * i + 3] = g->maps_out[1];
+    }
+    if ((e = cudaMalloc(&b->d_maps, sizeof(CUtensorMap) * maps.size())) != cudaSuccess ||
+        (e = cudaMalloc(&b->d_insts, sizeof(BatchInst) * n)) != cudaSuccess) {
+        batch_release(b);
+        return mrt_fail(MRT_ENOMEM, "batch tables: %s", cudaGetErrorString(e));
+    }
+    for (int i = 0; i < n; ++i) hi[i].maps = b->d_maps + 4 * i;
+    if ((e = cudaMemcpy(b->d_maps, maps.data(), sizeof(CUtensorMap) * maps.size(), cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemcpy(b->d_insts, hi.data(), sizeof(BatchInst) * n, cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(b->stream)) != cudaSuccess) {
+        batch_release(b);
+        return mrt_fail(MRT_ECUDA, "batch tables: %s", cudaGetErrorString(e));
+    }
+    mrt_status st = mrt_batch_tune(b, 4, 64);
+    if (st != MRT_OK) { batch_release(b); return st; }
+    *out = b;
+    return MRT_OK;
+}
+
+extern "C" mrt_status mrt_batch_step(mrt_batch* b, long nsteps) {
+    if (!b) return mrt_fail(MRT_EINVAL, "batch is NULL");
+    if (nsteps < 0) return mrt_fail(MRT_EINVAL, "nsteps must be >= 0");
+    long done = 0;
+    int cur = b->grids[0]->cur;  // all instances share the buffer parity
+    auto single = [&](int parity) -> mrt_status {
+        cudaError_t e = with_batch_tile(b->tile, [&](auto k) {
+            return k.launch(b->grid, b->d_insts, b->d_items, b->d_begin, parity, b->stream);
+        });
+        if (e != cudaSuccess) return mrt_fail(MRT_ECUDA, "batch step: %s", cudaGetErrorString(e));
+        return MRT_OK;
+    };
+    if (cur == 1 && nsteps > 0) {
+        mrt_status st = single(1);
+        if (st != MRT_OK) return st;
+        cur = 0;
+        done = 1;
+    }
+    for (; done + 2 <= nsteps; done += 2) {
+        cudaError_t e = cudaGraphLaunch(b->exec, b->stream);
+        if (e != cudaSuccess) return mrt_fail(MRT_ECUDA, "graph launch: %s", cudaGetErrorString(e));
+    }
+    if (done < nsteps) {
+        mrt_status st = single(0);
+        if (st != MRT_OK) return st;
+        cur = 1;
+        done += 1;
+    }
+    for (mrt_grid* g : b->grids) {
+        g->cur = cur;
+        g->steps += nsteps;
+        g->totals_fresh = false;
+    }
+    b->steps += nsteps;
+    return MRT_OK;
+}
+
+extern "C" mrt_status mrt_batch_grid(mrt_batch* b, int i, mrt_grid** g) {
+    if (!b || !g) return mrt_fail(MRT_EINVAL, "null argument");
+    if (i < 0 || i >= b->n) return mrt_fail(MRT_EINVAL, "instance %d out of range", i);
+    cudaError_t e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return mrt_fail(MRT_ECUDA, "sync: %s", cudaGetErrorString(e));
+    *g = b->grids[i];
+    return MRT_OK;
+}
+
+extern "C" mrt_status mrt_batch_info(const mrt_batch* b, int* n, int* tile, int* rows_per_item, int* ctas,
+                                     int* items) {
+    if (!b) return mrt_fail(MRT_EINVAL, "batch is NULL");
+    if (n) *n = b->n;
+    if (tile) *tile = b->tile;
+    if (rows_per_item) *rows_per_item = b->rows_per_item;
+    if (ctas) *ctas = b->grid;
+    if (items) *items = b->nitems;
+    return MRT_OK;
+}
+
+extern "C" mrt_status mrt_batch_stream(const mrt_batch* b, void** stream) {
+    if (!b || !stream) return mrt_fail(MRT_EINVAL, "null argument");
+    *stream = (void*)b->stream;
+    return MRT_OK;
+}
+
+extern "C" mrt_status mrt_batch_sync(mrt_batch* b) {
+    if (!b) return mrt_fail(MRT_EINVAL, "batch is NULL");
+    cudaError_t e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return mrt_fail(MRT_ECUDA, "sync: %s", cudaGetErrorString(e));
+    return MRT_OK;
+}
+
+extern "C" void mrt_batch_destroy(mrt_batch* b) { batch_release(b); }

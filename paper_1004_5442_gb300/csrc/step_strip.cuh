@@ -1,0 +1,298 @@
+// step_strip.cuh - the strip machinery shared by the single-grid and the
+// batched step kernels: a ring of TMA-loaded rows in shared memory, the
+// per-row cell update, row stores (TMA for whole strips, per thread for a
+// ragged strip), periodic ghost refresh, and the bounded-wait bookkeeping.
+#pragma once
+#include <cstdint>
+
+#include "internal.h"
+#include "tma.cuh"
+
+namespace mrt {
+
+using namespace tma;
+
+// Error-free accumulation of FP32 values into (hi, lo); FP64 sums plainly.
+template <class T>
+struct Acc {
+    T hi = 0, lo = 0;
+    __device__ __forceinline__ void add(T v) {
+        const T s = hi + v;
+        const T bb = s - hi;
+        lo += (hi - (s - bb)) + (v - bb);
+        hi = s;
+    }
+    __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+};
+template <>
+struct Acc<double> {
+    double hi = 0;
+    __device__ __forceinline__ void add(double v) { hi += v; }
+    __device__ __forceinline__ double value() const { return hi; }
+};
+
+// CTA-wide FP64 sum of 4 values; thread 0 writes them to dst[0..3].
+__device__ __forceinline__ void block_sum4(double v[4], double* dst) {
+    __shared__ double red[32][4];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nwarps = (blockDim.x * blockDim.y + 31) >> 5;
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+        for (int o = 16; o > 0; o >>= 1) v[q] += __shfl_xor_sync(0xffffffffu, v[q], o);
+    if (lane == 0)
+        for (int q = 0; q < 4; ++q) red[warp][q] = v[q];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int q = 0; q < 4; ++q) {
+            double s = 0.0;
+            for (int w = 0; w < nwarps; ++w) s += red[w][q];
+            dst[q] = s;
+        }
+    }
+}
+
+template <class T>
+__device__ __forceinline__ bool healthy(T rho, T P) {
+    // false for NaN, non-positive or infinite values
+    return rho > (T)0 && P > (T)0 && rho < (T)INFINITY && P < (T)INFINITY;
+}
+
+// Store a cell's 16 outputs and, on periodic axes, the ghost copies the next
+// step reads (column G-1 mirrors x = nx-1, column G+nx mirrors x = 0; row 0
+// mirrors y = ny-1, row ny+1 mirrors y = 0).
+template <class T>
+__device__ __forceinline__ void store_cell(T* __restrict__ out, const Layout& L, int per_x,
+                                           int per_y, int x, int y, const T v[NV]) {
+    const long row = (long)(y + 1) * L.pitch;
+    const long col = L.G + x;
+#pragma unroll
+    for (int i = 0; i < NV; ++i) out[i * L.plane + row + col] = v[i];
+    if (per_x) {
+        if (x == 0) {
+#pragma unroll
+            for (int i = 0; i < NV; ++i) out[i * L.plane + row + L.G + L.nx] = v[i];
+        }
+        if (x == L.nx - 1) {
+#pragma unroll
+            for (int i = 0; i < NV; ++i) out[i * L.plane + row + L.G - 1] = v[i];
+        }
+    }
+    if (per_y) {
+        if (y == 0) {
+#pragma unroll
+            for (int i = 0; i < NV; ++i) out[i * L.plane + (long)(L.ny + 1) * L.pitch + col] = v[i];
+        }
+        if (y == L.ny - 1) {
+#pragma unroll
+            for (int i = 0; i < NV; ++i) out[i * L.plane + col] = v[i];
+        }
+    }
+}
+
+// --------------------------------------------------------------------------
+// TMA-staged strip kernel.
+// --------------------------------------------------------------------------
+// YWIN: the 12 planes that move along y keep row r-1 in registers, so only
+// rows r and r+1 must be resident and the ring holds NS-2 rows in flight.
+template <bool YWIN> __device__ __forceinline__ constexpr bool moves_y(int i) {
+    return (i >= 8) || (i & 1);
+}
+
+// Shared-memory ring of a strip kernel and its row bookkeeping.  Row indices
+// are global over all the work items a CTA processes, so each ring slot's
+// mbarrier phases follow one another without re-initialisation.
+template <class T>
+struct StripRing {
+    T* ring;          // NS slots of NV x BOXW
+    T* outbuf;        // 2 output rows of NV x TMA_W
+    uint64_t* full;   // NS mbarriers
+    int base;         // global index of local row 0 of the current item
+    int issued;       // thread 0: global rows issued
+    int waited;       // thread 0: global rows seen complete (contiguous)
+};
+
+// One work item of a strip kernel: columns [x0, x0+TMA_W) and rows
+// [y0, y0+nrows) of the field described by L, read through map_in and
+// written to out (map_out for whole-strip TMA row stores).  Returns false if
+// a bounded wait ran out (the caller drains and flags).
+template <class T, bool TOTALS, int NS, bool TSTORE, bool YWIN, class CoefT>
+__device__ __forceinline__ bool strip_chunk(StripRing<T>& R, const CUtensorMap* map_in, const CUtensorMap* map_out,
+                                            const Layout& L, int per_x, int per_y, T* __restrict__ out,
+                                            const CoefT& k, int x0, int y0, int nrows, bool& bad, Acc<T>* acc) {
+    constexpr int HALO = tma_halo<T>();
+    constexpr int BOXW = tma_boxw<T>();
+    constexpr uint32_t SLOT_BYTES = (uint32_t)tma_slot_bytes<T>();
+    const int tid = threadIdx.x;
+    const int nload = nrows + 2;           // local rows 0..nrows+1 = padded rows y0..y0+nrows+1
+    const int x = x0 + tid;
+    const bool active = x < L.nx;
+    const int tma_x = L.G + x0 - HALO;     // 16-byte aligned start column of the load box
+    // Row stores by TMA only for whole strips: a TMA store that ends inside a
+    // 16-byte chunk can write that whole chunk, which for a ragged last strip
+    // holds the right ghost column.  The ragged strip copies its staged row
+    // out per thread instead.
+    const bool tstore = TSTORE && (x0 + TMA_W <= L.nx);
+    T* ring = R.ring;
+    uint64_t* full = R.full;
+    const int base = R.base;
+    auto slot_of = [&](int l) { return (base + l) % NS; };
+    auto issue = [&](int l) {
+        const int sl = slot_of(l);
+        mbar_arrive_expect_tx(&full[sl], SLOT_BYTES);
+        tma_load_3d(ring + (size_t)sl * NV * BOXW, map_in, &full[sl], tma_x, y0 + l, 0);
+        R.issued = base + l + 1;
+    };
+    auto wait_row = [&](int l) -> bool {
+        const int gl = base + l;
+        const bool ok = mbar_wait_bounded(&full[gl % NS], (uint32_t)((gl / NS) & 1));
+        if (tid == 0 && ok && gl == R.waited) R.waited = gl + 1;
+        return ok;
+    };
+
+    if (tid == 0) {
+        const int first = min(NS, nload);
+        for (int l = 0; l < first; ++l) issue(l);
+    }
+    bool ok = wait_row(0);
+    ok = wait_row(1) && ok;
+    if (!YWIN) ok = wait_row(2) && ok;
+    const int col = tid + HALO;
+    T ym[NV], fc[NV];  // YWIN: rows r-1 (y-moving planes) and r at this column
+    if (YWIN && ok) {
+        const T* s0 = ring + (size_t)slot_of(0) * NV * BOXW;
+        const T* s1 = ring + (size_t)slot_of(1) * NV * BOXW;
+#pragma unroll
+        for (int i = 0; i < NV; ++i) {
+            if (moves_y<YWIN>(i)) ym[i] = s0[i * BOXW + col];
+            fc[i] = s1[i * BOXW + col];
+        }
+    }
+    if (__syncthreads_or(!ok)) return false;
+    if (YWIN && tid == 0 && NS < nload) issue(NS);  // row 0 now lives in registers
+
+#pragma unroll 1
+    for (int r = 1; r <= nrows; ++r) {
+        const int y = y0 + r - 1;
+        T* ob = R.outbuf + (size_t)(r & 1) * NV * TMA_W;
+        if (YWIN) {
+            ok = wait_row(r + 1);  // a failed wait is acted on at the barrier below
+        }
+        if (active && ok) {
+            const T* sm = ring + (size_t)slot_of(r - 1) * NV * BOXW;
+            const T* sc = ring + (size_t)slot_of(r) * NV * BOXW;
+            const T* sp = ring + (size_t)slot_of(r + 1) * NV * BOXW;
+            T yp[NV];
+            if (YWIN) {
+#pragma unroll
+                for (int i = 0; i < NV; ++i) yp[i] = sp[i * BOXW + col];
+            }
+            auto F = [&](int i, int pos) -> T {
+                switch (pos) {
+                    case C: return YWIN ? fc[i] : sc[i * BOXW + col];
+                    case XM: return sc[i * BOXW + col - 1];
+                    case XP: return sc[i * BOXW + col + 1];
+                    case YM: return YWIN ? ym[i] : sm[i * BOXW + col];
+                    default: return YWIN ? yp[i] : sp[i * BOXW + col];
+                }
+            };
+            T o[NV];
+            T rho, P;
+            cell_update<T>(F, k, o, rho, P);
+            if (YWIN) {
+#pragma unroll
+                for (int i = 0; i < NV; ++i) {
+                    if (moves_y<YWIN>(i)) ym[i] = fc[i];
+                    fc[i] = yp[i];
+                }
+            }
+            bad |= !(rho > (T)0) | !(P > (T)0);
+            if (TSTORE) {
+#pragma unroll
+                for (int i = 0; i < NV; ++i) ob[i * TMA_W + tid] = o[i];
+            } else {
+                store_cell<T>(out, L, per_x, per_y, x, y, o);
+            }
+            if (TOTALS) {
+                T q0, q1, q2, q3;
+                conserved_moments<T>(o, q0, q1, q2, q3);
+                acc[0].add(q0); acc[1].add(q1); acc[2].add(q2); acc[3].add(q3);
+            }
+        }
+        if (tstore) {
+            fence_async_shared();                // make this thread's row visible to the TMA engine
+            if (tid == 0) bulk_wait_read_all();  // the store from the other out slot has read it
+        }
+        if (!YWIN) ok = (r + 2 < nload) ? wait_row(r + 2) : true;
+        // every thread is done with the slot released below, and the out row
+        // is complete
+        if (__syncthreads_or(!ok)) return false;
+        if (tid == 0) {
+            if (tstore) {
+                tma_store_3d(map_out, ob, L.G + x0, y + 1, 0);
+                if (per_y && y == 0) tma_store_3d(map_out, ob, L.G + x0, L.ny + 1, 0);
+                if (per_y && y == L.ny - 1) tma_store_3d(map_out, ob, L.G + x0, 0, 0);
+                bulk_commit();
+            }
+            // without YWIN row r-1 is the oldest row still read; with it, row r
+            const int l = YWIN ? r + NS : r - 1 + NS;
+            if (l < nload) issue(l);
+        }
+        // after the elected thread has queued its copies
+        if (TSTORE) {
+            if (!tstore && active) {
+                // ragged strip: this thread's column of the staged row, plus
+                // the periodic ghost rows
+                const long c0 = (long)(y + 1) * L.pitch + L.G + x;
+#pragma unroll 4
+                for (int i = 0; i < NV; ++i) {
+                    const T v = ob[i * TMA_W + tid];
+                    out[i * L.plane + c0] = v;
+                    if (per_y && y == 0) out[i * L.plane + (long)(L.ny + 1) * L.pitch + L.G + x] = v;
+                    if (per_y && y == L.ny - 1) out[i * L.plane + L.G + x] = v;
+                }
+            }
+            if (per_x && (x == 0 || x == L.nx - 1)) {
+                // periodic ghost columns are single values: plain stores
+                const long gc = (long)(y + 1) * L.pitch + (x == 0 ? L.G + L.nx : L.G - 1);
+#pragma unroll 4
+                for (int i = 0; i < NV; ++i) out[i * L.plane + gc] = ob[i * TMA_W + tid];
+            }
+        }
+    }
+    if (tstore && tid == 0) bulk_wait_all();
+    R.base += nload;
+    return true;
+}
+
+// After a failed wait: thread 0 waits (bounded) for its loads still in
+// flight and for its stores, then flags the timeout.
+template <class T, int NS>
+__device__ __forceinline__ void strip_drain(StripRing<T>& R, unsigned* flag) {
+    if (threadIdx.x == 0) {
+        for (int gl = R.waited; gl < R.issued; ++gl) mbar_wait_bounded(&R.full[gl % NS], (uint32_t)((gl / NS) & 1));
+        bulk_wait_all();
+        atomicOr(flag, FLAG_TIMEOUT);
+    }
+}
+
+template <class T, int NS, bool TSTORE>
+__device__ __forceinline__ StripRing<T> strip_ring_init(unsigned char* smem_raw) {
+    constexpr uint32_t SLOT_BYTES = (uint32_t)tma_slot_bytes<T>();
+    constexpr uint32_t OUT_BYTES = TSTORE ? (uint32_t)tma_out_slot_bytes<T>() : 0u;
+    StripRing<T> R;
+    R.ring = reinterpret_cast<T*>(smem_raw);
+    R.outbuf = reinterpret_cast<T*>(smem_raw + NS * SLOT_BYTES);
+    R.full = reinterpret_cast<uint64_t*>(smem_raw + NS * SLOT_BYTES + 2 * OUT_BYTES);
+    R.base = 0;
+    R.issued = 0;
+    R.waited = 0;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < NS; ++s) mbar_init(&R.full[s], 1);
+        fence_barrier_init();
+    }
+    __syncthreads();
+    return R;
+}
+
+
+}  // namespace mrt

@@ -1,0 +1,111 @@
+"""Batched independent grids: each instance of a batch step must equal the
+same instance stepped alone (same kernel arithmetic, so bit for bit), for
+every kernel variant and work-item height; the seeded 256-instance sweep is
+checked the same way on sampled instances, and against the oracle on a few
+small ones."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1004_5442_gb300 import binding as Bd
+from paper_1004_5442_gb300 import workloads as W
+from _parity import assert_parity, run_oracle
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    Bd.load()
+    yield
+
+
+def screened():
+    import json
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "riemann_instances_screened.json")
+    with open(path) as fh:
+        return W.riemann_instances(count=256, accepted=json.load(fh)["accepted"])
+
+
+def _mixed(count=10, seed=21):
+    """Uneven small instances: tubes, ripples, periodic smooth fields."""
+    out = W.riemann_instances(count=count // 2, seed=seed, nx_range=(129, 700), ny_choices=(4, 37), nsteps=0)
+    for k in range(count - count // 2):
+        nx = [130, 257, 300, 384, 95][k % 5]
+        ny = [9, 40, 5, 17, 64][k % 5]
+        out.append(W.random_smooth(nx, ny, seed=seed + k, amp=0.05, bc_x=k % 2, bc_y=(k // 2) % 2))
+    return out
+
+
+def _alone(w, nsteps):
+    with Bd.Grid.from_workload(w, precision=Bd.FP32, kernel=Bd.KERNEL_TMA, tile=4) as g:
+        g.step(nsteps)
+        return g.get_f()
+
+
+@pytest.mark.parametrize("tile,rows", [(4, 64), (2, 16), (5, 256), (4, 7)])
+def test_batch_equals_single_grids(tile, rows):
+    ws = _mixed()
+    with Bd.Batch(ws) as b:
+        b.tune(tile, rows)
+        b.step(7)       # odd: leaves the buffers swapped
+        b.step(4)
+        got = [b.grid(i).get_f() for i in range(len(ws))]
+        info = b.info()
+    assert info["tile"] == tile and info["rows_per_item"] == rows
+    for w, f in zip(ws, got):
+        np.testing.assert_array_equal(f, _alone(w, 11))
+
+
+def test_batch_instances_match_oracle():
+    ws = _mixed(count=6, seed=5)
+    with Bd.Batch(ws) as b:
+        b.step(25)
+        macros = [b.grid(i).macro() for i in range(len(ws))]
+    for w, got in zip(ws, macros):
+        want = oracle.macro(run_oracle(w, 25))
+        assert_parity(got, want, l1=1e-5, linf=1e-4, label=w.name)
+
+
+def test_seeded_sweep_sampled_instances():
+    """The 256-instance sweep (nx 256..4096, ny 4 or 256, gamma 1.1..1.67,
+    Pr 0.5..2, pressure ratio 10..100), 1000 FP32 steps: 12 seeded instances
+    (both heights) equal their single-grid runs bit for bit; every instance's
+    health flag is read."""
+    ws = screened()
+    rng = np.random.default_rng(3)
+    pick = sorted(set(rng.choice(len(ws), 12, replace=False).tolist()))
+    with Bd.Batch(ws) as b:
+        b.step(1000)
+        got = {i: b.grid(i).get_f() for i in pick}
+        health = [b.grid(i).health() for i in range(len(ws))]
+    print("unstable instances after 1000 steps:", [i for i, h in enumerate(health) if h != Bd.MRT_OK])
+    assert set(health) <= {Bd.MRT_OK, Bd.MRT_EUNSTABLE}
+    assert sum(h == Bd.MRT_OK for h in health) >= 0.9 * len(ws)
+    for i in pick:
+        np.testing.assert_array_equal(got[i], _alone(ws[i], 1000), err_msg=f"instance {i}")
+
+
+def test_constant_table_capacity():
+    small = [W.uniform(5, 3) for _ in range(200)]
+    more = [W.uniform(5, 3) for _ in range(100)]
+    with Bd.Batch(small):
+        with pytest.raises(Bd.MrtError) as ei:
+            Bd.Batch(more)
+        assert ei.value.code == Bd.MRT_ENOMEM
+    with Bd.Batch(more):   # the slots are free again
+        pass
+
+
+def test_autotuner_picks_a_valid_variant(tmp_path):
+    from paper_1004_5442_gb300 import autotune
+    ws = _mixed(count=8, seed=9)
+    res = autotune.tune_workloads(ws, steps=3, cache_path=str(tmp_path / "cache.json"))
+    assert (res["tile"], res["rows_per_item"]) in autotune.CANDIDATES
+    assert len(res["timings"]) == len(autotune.CANDIDATES) and not res["cached"]
+    again = autotune.tune_workloads(ws, cache_path=str(tmp_path / "cache.json"))
+    assert again["cached"] and again["tile"] == res["tile"]
