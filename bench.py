@@ -56,6 +56,7 @@ def parse():
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--batch-steps", type=int, default=1000, help="timed steps of the 256-instance sweep")
+    ap.add_argument("--batch-count", type=int, default=256, help="instances of the sweep (first n screened draws)")
     ap.add_argument("--tile", type=int, default=0, help="TMA kernel variant (0 = library default)")
     ap.add_argument("--sweep-tiles", action="store_true", help="time every TMA variant, print one line each")
     return ap.parse_args()
@@ -398,7 +399,7 @@ def batch_sweep(Bd, W, torch, args, peak):
     here = os.path.dirname(os.path.abspath(__file__))
     with open(os.path.join(here, "tests", "golden", "riemann_instances_screened.json")) as fh:
         screened = json.load(fh)
-    ws = W.riemann_instances(count=256, accepted=screened["accepted"])
+    ws = W.riemann_instances(count=args.batch_count, accepted=screened["accepted"])
     cells = sum(w.nx * w.ny for w in ws)
     t0 = time.perf_counter()
     tuned = AT.tune_workloads(ws, use_cache=False)
@@ -420,7 +421,7 @@ def batch_sweep(Bd, W, torch, args, peak):
         healthy = sum(b.grid(i).health() == Bd.MRT_OK for i in range(len(ws)))
     per_s = ms * 1e-3 / k
     gbs = BYTES_PER_CELL_F32 * cells / per_s / 1e9
-    return {"workload": "riemann_ripple_sweep_256_fp32", "instances": len(ws), "cells": cells,
+    return {"workload": f"riemann_ripple_sweep_{len(ws)}_fp32", "instances": len(ws), "cells": cells,
             "value": cells / per_s, "unit": "cell-updates/s", "steps": k, "ms_per_step": ms / k,
             "hbm_achieved_gbs": gbs, "hbm_frac": gbs / peak, "launches_per_step": 1,
             "tile": info["tile"], "rows_per_item": info["rows_per_item"], "ctas": info["ctas"],

@@ -193,7 +193,8 @@ mrt_status mrt_conserved_totals_static(const void *f, int precision, int nx, int
 /* Batched independent grids (many instances of uneven size, gamma, Pr and
  * rates advanced together).  Every time step is one kernel launch covering
  * all instances' work items (instance x 128-column strip x chunk of rows),
- * balanced by cells over one wave of resident CTAs; two consecutive steps
+ * which one wave of resident CTAs takes, longest first, from an atomic
+ * counter; two consecutive steps
  * are captured once in a CUDA graph and replayed.  Each instance is an
  * ordinary FP32 grid with the TMA step kernel; its handle (mrt_batch_grid)
  * serves for readout (mrt_get_macro, mrt_get_f, mrt_conserved_totals,
@@ -209,8 +210,9 @@ mrt_status mrt_conserved_totals_static(const void *f, int precision, int nx, int
  * constant table is full), MRT_ECUDA.
  * mrt_batch_step: advance every instance nsteps >= 0 steps (asynchronous).
  * mrt_batch_tune: choose the kernel variant (tile 2, 4 or 5, as in
- * mrt_params) and the rows per work item (>= 1); rebuilds the work list and
- * the graph.  Results do not depend on the choice.
+ * mrt_params) and the rows per work item (>= 1; 32 with tile 4 at
+ * creation); rebuilds the work list and the graph.  Results do not depend
+ * on the choice.
  * mrt_batch_grid: handle of instance i (synchronises the batch stream).
  * mrt_batch_info: instances, tile, rows per item, CTAs and work items.
  * mrt_batch_sync: wait for the batch's work.

@@ -7,7 +7,8 @@
 //   - a __constant__ table of the instances' step constants (the
 //     relaxation rates, b, and Lax-Wendroff weights differ per instance),
 //   - a device table of instance descriptors and their tensor maps,
-//   - a work list balanced by cells over one wave of resident CTAs.
+//   - a work list (instance x strip x chunk of rows, longest first) that one
+//     wave of resident CTAs takes items from through an atomic counter.
 // Kernel boundaries order the steps, so no device-side grid barrier exists.
 #include <algorithm>
 #include <cstring>
@@ -43,16 +44,28 @@ struct Item {
     int inst, x0, y0, nrows;
 };
 
+// One step of every instance.  Each CTA takes work items in list order
+// from the step's counter (next[parity]); the index of its next item is
+// fetched while the current one is processed, into the other of two shared
+// slots (the barriers of an item separate a slot's read from its next
+// write).  The CTA-level ring of the strip loop carries over from item to
+// item.  The kernel also clears the other parity's counter for the next
+// step, which stream order runs after this one.
 template <int NS, bool TSTORE, bool YWIN, int MINB>
 __global__ void __launch_bounds__(TMA_W, MINB) batch_step_kernel(const BatchInst* __restrict__ insts,
-                                                                 const Item* __restrict__ items,
-                                                                 const int* __restrict__ item_begin, int parity) {
+                                                                 const Item* __restrict__ items, int nitems,
+                                                                 unsigned* __restrict__ next, int parity) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    const int i0 = item_begin[blockIdx.x], i1 = item_begin[blockIdx.x + 1];
-    if (i0 >= i1) return;
+    __shared__ int s_item[2];
+    if (blockIdx.x == 0 && threadIdx.x == 0) next[parity ^ 1] = 0u;
+    if (threadIdx.x == 0) s_item[0] = (int)atomicAdd(&next[parity], 1u);
+    __syncthreads();
+    int cur = s_item[0];
+    if (cur >= nitems) return;
     StripRing<float> R = strip_ring_init<float, NS, TSTORE>(smem_raw);
-    for (int it = i0; it < i1; ++it) {
-        const Item w = items[it];
+    for (int k = 1; cur < nitems; ++k) {
+        if (threadIdx.x == 0) s_item[k & 1] = (int)atomicAdd(&next[parity], 1u);
+        const Item w = items[cur];
         const BatchInst& I = insts[w.inst];
         const Layout L = I.L;
         const CUtensorMap* mi = I.maps + parity;
@@ -65,6 +78,7 @@ __global__ void __launch_bounds__(TMA_W, MINB) batch_step_kernel(const BatchInst
             return;
         }
         if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(I.flag, FLAG_UNSTABLE);
+        cur = s_item[k & 1];
     }
 }
 
@@ -80,9 +94,9 @@ struct BatchKernel {
         return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, batch_step_kernel<NS, TSTORE, YWIN, MINB>, TMA_W,
                                                              smem());
     }
-    static cudaError_t launch(int grid, const BatchInst* insts, const Item* items, const int* begin, int parity,
-                              cudaStream_t st) {
-        batch_step_kernel<NS, TSTORE, YWIN, MINB><<<grid, TMA_W, smem(), st>>>(insts, items, begin, parity);
+    static cudaError_t launch(int grid, const BatchInst* insts, const Item* items, int nitems, unsigned* next,
+                              int parity, cudaStream_t st) {
+        batch_step_kernel<NS, TSTORE, YWIN, MINB><<<grid, TMA_W, smem(), st>>>(insts, items, nitems, next, parity);
         return cudaGetLastError();
     }
 };
@@ -108,8 +122,8 @@ struct mrt_batch {
     BatchInst* d_insts = nullptr;
     CUtensorMap* d_maps = nullptr;
     Item* d_items = nullptr;
-    int* d_begin = nullptr;
-    int tile = 4, rows_per_item = 64, grid = 0, nitems = 0;
+    unsigned* d_next = nullptr;  // per-parity work counters
+    int tile = 4, rows_per_item = 32, grid = 0, nitems = 0;
     cudaGraphExec_t exec = nullptr;
     long steps = 0;
 };
@@ -122,7 +136,7 @@ static void batch_release(mrt_batch* b) {
     cudaFree(b->d_insts);
     cudaFree(b->d_maps);
     cudaFree(b->d_items);
-    cudaFree(b->d_begin);
+    cudaFree(b->d_next);
     {
         std::lock_guard<std::mutex> lock(g_slot_mu);
         for (int s : b->slots) g_slot_used[s] = false;
@@ -131,47 +145,33 @@ static void batch_release(mrt_batch* b) {
     delete b;
 }
 
-// Work list: items of up to rows_per_item rows per strip, assigned to `grid`
-// CTAs longest-first to the least-loaded CTA (cost = cells + a per-item
-// start-up term), then laid out CTA by CTA.
+// Work list: every strip of every instance cut into items of up to
+// rows_per_item rows, longest first (ties in instance and strip order).  The
+// CTAs of a step take items from this list through an atomic counter, so
+// the balance does not rest on a cost model: a row of a narrow ragged strip
+// or of a short instance costs about as much as a full one (each row is a
+// ring step with a CTA barrier) while moving far fewer bytes.
 static mrt_status build_work(mrt_batch* b) {
-    struct W { Item it; double cost; };
-    std::vector<W> ws;
+    std::vector<Item> items;
     for (int i = 0; i < b->n; ++i) {
         const Layout& L = b->grids[i]->L;
         for (int x0 = 0; x0 < L.nx; x0 += TMA_W)
-            for (int y0 = 0; y0 < L.ny; y0 += b->rows_per_item) {
-                const int nr = std::min(b->rows_per_item, L.ny - y0);
-                const int w = std::min(TMA_W, L.nx - x0);
-                ws.push_back({{i, x0, y0, nr}, (double)TMA_W * (nr + 2) + 0.0 * w});
-            }
+            for (int y0 = 0; y0 < L.ny; y0 += b->rows_per_item)
+                items.push_back({i, x0, y0, std::min(b->rows_per_item, L.ny - y0)});
     }
-    std::sort(ws.begin(), ws.end(), [](const W& a, const W& c) { return a.cost > c.cost; });
-    std::vector<std::vector<Item>> per(b->grid);
-    std::vector<double> load(b->grid, 0.0);
-    for (const W& w : ws) {
-        const int c = (int)(std::min_element(load.begin(), load.end()) - load.begin());
-        per[c].push_back(w.it);
-        load[c] += w.cost + 2.0 * TMA_W;  // prologue of an item ~ two extra rows
-    }
-    std::vector<Item> items;
-    std::vector<int> begin(b->grid + 1, 0);
-    for (int c = 0; c < b->grid; ++c) {
-        begin[c] = (int)items.size();
-        items.insert(items.end(), per[c].begin(), per[c].end());
-    }
-    begin[b->grid] = (int)items.size();
+    std::stable_sort(items.begin(), items.end(), [](const Item& a, const Item& c) { return a.nrows > c.nrows; });
     b->nitems = (int)items.size();
     cudaFree(b->d_items);
-    cudaFree(b->d_begin);
     b->d_items = nullptr;
-    b->d_begin = nullptr;
     cudaError_t e;
-    if ((e = cudaMalloc(&b->d_items, sizeof(Item) * std::max<size_t>(items.size(), 1))) != cudaSuccess ||
-        (e = cudaMalloc(&b->d_begin, sizeof(int) * begin.size())) != cudaSuccess)
+    if ((e = cudaMalloc(&b->d_items, sizeof(Item) * items.size())) != cudaSuccess)
         return mrt_fail(MRT_ENOMEM, "batch work list: %s", cudaGetErrorString(e));
-    if ((e = cudaMemcpy(b->d_items, items.data(), sizeof(Item) * items.size(), cudaMemcpyHostToDevice)) != cudaSuccess ||
-        (e = cudaMemcpy(b->d_begin, begin.data(), sizeof(int) * begin.size(), cudaMemcpyHostToDevice)) != cudaSuccess)
+    // on the batch's own (non-blocking) stream, so its kernels are ordered
+    // after the copies
+    if ((e = cudaMemcpyAsync(b->d_items, items.data(), sizeof(Item) * items.size(), cudaMemcpyHostToDevice,
+                             b->stream)) != cudaSuccess ||
+        (e = cudaMemsetAsync(b->d_next, 0, 2 * sizeof(unsigned), b->stream)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(b->stream)) != cudaSuccess)
         return mrt_fail(MRT_ECUDA, "batch work list: %s", cudaGetErrorString(e));
     return MRT_OK;
 }
@@ -186,7 +186,7 @@ static mrt_status build_graph(mrt_batch* b) {
     if (e != cudaSuccess) return mrt_fail(MRT_ECUDA, "capture: %s", cudaGetErrorString(e));
     for (int parity = 0; parity < 2; ++parity) {
         e = with_batch_tile(b->tile, [&](auto k) {
-            return k.launch(b->grid, b->d_insts, b->d_items, b->d_begin, parity, b->stream);
+            return k.launch(b->grid, b->d_insts, b->d_items, b->nitems, b->d_next, parity, b->stream);
         });
         if (e != cudaSuccess) break;
     }
@@ -269,18 +269,21 @@ extern "C" mrt_status mrt_batch_create(int n, const mrt_params* params, const do
         maps[4 * i + 3] = g->maps_out[1];
     }
     if ((e = cudaMalloc(&b->d_maps, sizeof(CUtensorMap) * maps.size())) != cudaSuccess ||
-        (e = cudaMalloc(&b->d_insts, sizeof(BatchInst) * n)) != cudaSuccess) {
+        (e = cudaMalloc(&b->d_insts, sizeof(BatchInst) * n)) != cudaSuccess ||
+        (e = cudaMalloc(&b->d_next, 2 * sizeof(unsigned))) != cudaSuccess) {
         batch_release(b);
         return mrt_fail(MRT_ENOMEM, "batch tables: %s", cudaGetErrorString(e));
     }
     for (int i = 0; i < n; ++i) hi[i].maps = b->d_maps + 4 * i;
-    if ((e = cudaMemcpy(b->d_maps, maps.data(), sizeof(CUtensorMap) * maps.size(), cudaMemcpyHostToDevice)) != cudaSuccess ||
-        (e = cudaMemcpy(b->d_insts, hi.data(), sizeof(BatchInst) * n, cudaMemcpyHostToDevice)) != cudaSuccess ||
+    if ((e = cudaMemcpyAsync(b->d_maps, maps.data(), sizeof(CUtensorMap) * maps.size(), cudaMemcpyHostToDevice,
+                             b->stream)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(b->d_insts, hi.data(), sizeof(BatchInst) * n, cudaMemcpyHostToDevice, b->stream)) !=
+            cudaSuccess ||
         (e = cudaStreamSynchronize(b->stream)) != cudaSuccess) {
         batch_release(b);
         return mrt_fail(MRT_ECUDA, "batch tables: %s", cudaGetErrorString(e));
     }
-    mrt_status st = mrt_batch_tune(b, 4, 64);
+    mrt_status st = mrt_batch_tune(b, 4, 32);
     if (st != MRT_OK) { batch_release(b); return st; }
     *out = b;
     return MRT_OK;
@@ -293,7 +296,7 @@ extern "C" mrt_status mrt_batch_step(mrt_batch* b, long nsteps) {
     int cur = b->grids[0]->cur;  // all instances share the buffer parity
     auto single = [&](int parity) -> mrt_status {
         cudaError_t e = with_batch_tile(b->tile, [&](auto k) {
-            return k.launch(b->grid, b->d_insts, b->d_items, b->d_begin, parity, b->stream);
+            return k.launch(b->grid, b->d_insts, b->d_items, b->nitems, b->d_next, parity, b->stream);
         });
         if (e != cudaSuccess) return mrt_fail(MRT_ECUDA, "batch step: %s", cudaGetErrorString(e));
         return MRT_OK;

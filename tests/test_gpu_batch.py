@@ -47,7 +47,7 @@ def _alone(w, nsteps):
         return g.get_f()
 
 
-@pytest.mark.parametrize("tile,rows", [(4, 64), (2, 16), (5, 256), (4, 7)])
+@pytest.mark.parametrize("tile,rows", [(4, 32), (2, 16), (5, 256), (4, 7), (4, 1)])
 def test_batch_equals_single_grids(tile, rows):
     ws = _mixed()
     with Bd.Batch(ws) as b:
@@ -59,6 +59,14 @@ def test_batch_equals_single_grids(tile, rows):
     assert info["tile"] == tile and info["rows_per_item"] == rows
     for w, f in zip(ws, got):
         np.testing.assert_array_equal(f, _alone(w, 11))
+
+
+def test_default_work_split():
+    ws = _mixed(count=4)
+    with Bd.Batch(ws) as b:
+        info = b.info()
+    items = sum(((w.nx + 127) // 128) * ((w.ny + 31) // 32) for w in ws)
+    assert (info["tile"], info["rows_per_item"], info["items"]) == (4, 32, items)
 
 
 def test_batch_instances_match_oracle():
