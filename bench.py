@@ -63,13 +63,16 @@ def parse():
 
 
 # ---------------------------------------------------------------------------
-def dist_init(n_gpus):
+def dist_init(n_gpus, backend=None):
+    """Rank, world size and local rank from the launcher's environment; one
+    process group (NCCL on GPUs) when the world has more than one rank."""
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if world > 1:
         import torch.distributed as dist
-        dist.init_process_group("nccl")
+        if not dist.is_initialized():
+            dist.init_process_group(backend or "nccl")
     return rank, world, local
 
 
@@ -80,13 +83,27 @@ def barrier(world):
 
 
 def allmax(x, world):
+    """Maximum of x over all ranks (the slowest replica sets the time)."""
     if world <= 1:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def whole_job_rate(units_per_rank, steps, ms_max, world):
+    """Units of all replicas per second over the slowest rank's time."""
+    return world * units_per_rank * steps / (ms_max * 1e-3)
+
+
+def workload_config(w, world):
+    return {"workload": f"kelvin_helmholtz_{w.nx}x{w.ny}_fp32", "nx": w.nx, "ny": w.ny, "gamma": w.gamma,
+            "Pr": w.Pr, "cfl": 0.1, "precision": "fp32",
+            "l2": "state 2 x %.2f GB > 129 MB L2, no flush" % (16 * w.nx * w.ny * 4 / 1e9),
+            "parallelism": f"replicas{world}"}
 
 
 # ---------------------------------------------------------------------------
@@ -201,9 +218,11 @@ def cpu_oracle_rate(w, budget_s=12.0, max_steps=None, rows=512):
 
 # ---------------------------------------------------------------------------
 def run_reference(args):
-    rank, world, local = int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), 0
+    """The oracle timed on the host cores (rank 0 only; other ranks exit
+    without work)."""
+    rank, world = int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1"))
     if rank != 0:
-        return
+        return None
     from paper_1004_5442_gb300 import workloads as W
     w = W.kelvin_helmholtz(n=args.n, nsteps=0)
     import oracle
@@ -222,11 +241,12 @@ def run_reference(args):
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": f"kelvin_helmholtz_{args.n}x{args.n}", "sample_rows": rows},
+            "config": workload_config(w, world),
             "cpu_baseline": {"value": rate, "unit": "cell-updates/s", "cores": oracle.get_threads(),
                              "kind": "oracle", "sample": sample},
             "e2e": {"value": rate, "unit": "cell-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+    return line
 
 
 # ---------------------------------------------------------------------------
@@ -266,7 +286,7 @@ def run_ours(args):
     ms = allmax(ms, world)
     tot = grid.totals()
     assert grid.health() == Bd.MRT_OK and np.all(np.isfinite(tot))
-    value = world * cells * args.steps / (ms * 1e-3)
+    value = whole_job_rate(cells, args.steps, ms, world)
     per_launch_s = ms * 1e-3 / args.steps
     peak, peak_kind = measured_peak_hbm()
     achieved = BYTES_PER_CELL_F32 * cells / per_launch_s / 1e9
@@ -277,11 +297,8 @@ def run_ours(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
-            "config": {"workload": f"kelvin_helmholtz_{w.nx}x{w.ny}_fp32", "nx": w.nx, "ny": w.ny,
-                       "gamma": w.gamma, "Pr": w.Pr, "cfl": 0.1, "precision": "fp32", "kernel": "tma",
-                       "tile": info["tile"],
-                       "l2": "state 2 x %.2f GB > 129 MB L2, no flush" % (16 * cells * 4 / 1e9),
-                       "parallelism": f"replicas{world}"},
+            "config": workload_config(w, world),
+            "kernel": {"name": "step_tma", "tile": info["tile"]},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
                          "peak_source": f"{peak_kind} hbm_gbs",
@@ -337,7 +354,7 @@ def run_ours(args):
         g2.close()
         h2d = 4 * 8 * cells
         d2h = 4 * 8 * cells + 32 * args.steps
-        line["e2e"] = {"value": world * cells * args.steps / el, "unit": "cell-updates/s",
+        line["e2e"] = {"value": whole_job_rate(cells, args.steps, el * 1e3, world), "unit": "cell-updates/s",
                        "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
                        "what": "mrt_create from pinned host rho,u,v,T; per step mrt_step(1) + "
                                "mrt_conserved_totals (D2H); final mrt_get_macro to pinned host"}
