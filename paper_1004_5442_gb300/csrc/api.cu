@@ -292,9 +292,11 @@ __global__ void __launch_bounds__(RED_THREADS) totals_partial_kernel(Layout L, c
         }
 }
 
-// Fixed-order sum of nparts block partials, times dx*dy, into out[4].
+// Fixed-order sum of nparts block partials, times dx*dy, into out[0..3];
+// out[4] takes the flag word, so one copy brings back totals and health.
 __global__ void __launch_bounds__(RED_THREADS) totals_final_kernel(const double* partials, int nparts,
-                                                                   double scale, double* out) {
+                                                                   double scale, const unsigned* flag,
+                                                                   double* out) {
     __shared__ double red[RED_THREADS][4];
     double acc[4] = {0, 0, 0, 0};
     for (int p = threadIdx.x; p < nparts; p += RED_THREADS)
@@ -306,8 +308,10 @@ __global__ void __launch_bounds__(RED_THREADS) totals_final_kernel(const double*
             for (int k = 0; k < 4; ++k) red[threadIdx.x][k] += red[threadIdx.x + s][k];
         __syncthreads();
     }
-    if (threadIdx.x == 0)
+    if (threadIdx.x == 0) {
         for (int k = 0; k < 4; ++k) out[k] = red[0][k] * scale;
+        out[4] = (double)*flag;
+    }
 }
 
 int grid_for(long n, int threads, int cap = 4096) {
@@ -394,6 +398,7 @@ static void release(mrt_grid* g) {
     cudaFree(g->flag);
     cudaFree(g->partials);
     cudaFree(g->totals_dev);
+    cudaFreeHost(g->host_stage);
     cudaFree(g->macro_tmp);
     mrt_tape_free(g->tape);
     if (prev >= 0) cudaSetDevice(prev);
@@ -466,7 +471,8 @@ extern "C" mrt_status mrt_create(const mrt_params* params, const double* rho, co
         return bail(fail(MRT_ECUDA, "memset: %s", cudaGetErrorString(e)));
     if ((e = cudaMalloc(&g->flag, sizeof(unsigned))) != cudaSuccess ||
         (e = cudaMemsetAsync(g->flag, 0, sizeof(unsigned), g->stream)) != cudaSuccess ||
-        (e = cudaMalloc(&g->totals_dev, 4 * sizeof(double))) != cudaSuccess)
+        (e = cudaMalloc(&g->totals_dev, 5 * sizeof(double))) != cudaSuccess ||
+        (e = cudaMallocHost(&g->host_stage, 8 * sizeof(double))) != cudaSuccess)
         return bail(fail(MRT_ENOMEM, "cudaMalloc: %s", cudaGetErrorString(e)));
 
     // kernel choice and launch geometry
@@ -615,7 +621,7 @@ static mrt_status step_impl(mrt_grid* g, long nsteps) {
         if (e != cudaSuccess) return fail(MRT_ECUDA, "step launch: %s", cudaGetErrorString(e));
         if (totals) {
             totals_final_kernel<<<1, RED_THREADS, 0, g->stream>>>(g->partials, parts, g->p.dx * g->p.dx,
-                                                                 g->totals_dev);
+                                                                 g->flag, g->totals_dev);
             CUDA_TRY(cudaGetLastError());
         }
         g->cur ^= 1;
@@ -665,7 +671,8 @@ static mrt_status totals_impl(mrt_grid* g) {
     totals_partial_kernel<T><<<blocks, RED_THREADS, 0, g->stream>>>(g->L, static_cast<const T*>(g->f[g->cur]),
                                                                      g->partials);
     CUDA_TRY(cudaGetLastError());
-    totals_final_kernel<<<1, RED_THREADS, 0, g->stream>>>(g->partials, blocks, g->p.dx * g->p.dx, g->totals_dev);
+    totals_final_kernel<<<1, RED_THREADS, 0, g->stream>>>(g->partials, blocks, g->p.dx * g->p.dx, g->flag,
+                                                          g->totals_dev);
     CUDA_TRY(cudaGetLastError());
     g->totals_fresh = true;
     return MRT_OK;
@@ -677,10 +684,10 @@ extern "C" mrt_status mrt_conserved_totals(mrt_grid* g, double out[4]) {
         mrt_status st = g->fp64 ? totals_impl<double>(g) : totals_impl<float>(g);
         if (st != MRT_OK) return st;
     }
-    unsigned flag = 0;
-    CUDA_TRY(cudaMemcpyAsync(out, g->totals_dev, 4 * sizeof(double), cudaMemcpyDeviceToHost, g->stream));
-    CUDA_TRY(cudaMemcpyAsync(&flag, g->flag, sizeof flag, cudaMemcpyDeviceToHost, g->stream));
+    CUDA_TRY(cudaMemcpyAsync(g->host_stage, g->totals_dev, 5 * sizeof(double), cudaMemcpyDeviceToHost, g->stream));
     CUDA_TRY(cudaStreamSynchronize(g->stream));
+    for (int k = 0; k < 4; ++k) out[k] = g->host_stage[k];
+    const unsigned flag = (unsigned)g->host_stage[4];
     if (flag & FLAG_TIMEOUT) return fail(MRT_ETIMEOUT, "a device-side wait ran out");
     if (flag & FLAG_UNSTABLE) return fail(MRT_EUNSTABLE, "non-positive or non-finite rho or pressure");
     return MRT_OK;
@@ -742,11 +749,11 @@ mrt_status mrt_refresh_periodic_ghosts(mrt_grid* g, void* buf) {
 
 extern "C" mrt_status mrt_health(mrt_grid* g) {
     if (!g) return fail(MRT_EINVAL, "grid is NULL");
-    unsigned flag = 0;
-    CUDA_TRY(cudaMemcpyAsync(&flag, g->flag, sizeof flag, cudaMemcpyDeviceToHost, g->stream));
+    unsigned* flag = reinterpret_cast<unsigned*>(g->host_stage + 6);
+    CUDA_TRY(cudaMemcpyAsync(flag, g->flag, sizeof(unsigned), cudaMemcpyDeviceToHost, g->stream));
     CUDA_TRY(cudaStreamSynchronize(g->stream));
-    if (flag & FLAG_TIMEOUT) return fail(MRT_ETIMEOUT, "a device-side wait ran out");
-    if (flag & FLAG_UNSTABLE) return fail(MRT_EUNSTABLE, "non-positive or non-finite rho or pressure");
+    if (*flag & FLAG_TIMEOUT) return fail(MRT_ETIMEOUT, "a device-side wait ran out");
+    if (*flag & FLAG_UNSTABLE) return fail(MRT_EUNSTABLE, "non-positive or non-finite rho or pressure");
     return MRT_OK;
 }
 

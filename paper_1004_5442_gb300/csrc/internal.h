@@ -170,7 +170,8 @@ struct mrt_grid {
     unsigned* flag = nullptr;        // device flag word
     double* partials = nullptr;      // 4 doubles per CTA
     int max_parts = 0;
-    double* totals_dev = nullptr;    // 4 doubles
+    double* totals_dev = nullptr;    // 4 totals + a copy of the flag word, as doubles
+    double* host_stage = nullptr;    // pinned host copy of totals_dev (one small DMA per read)
     bool totals_fresh = false;
     double* macro_tmp = nullptr;     // 4 fields, for host readout
     long steps = 0;
