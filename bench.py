@@ -41,6 +41,16 @@ KERNEL_SOURCES = ["paper_1004_5442_gb300/csrc/step_kernels.cu", "paper_1004_5442
                   "paper_1004_5442_gb300/csrc/tma.cuh", "paper_1004_5442_gb300/csrc/model.cuh",
                   "paper_1004_5442_gb300/csrc/internal.h"]
 PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "step_tma_f32_kh4096.md")
+# FP64 step, per cell-update (ncu instruction counters of step_tma<double>,
+# profiles/step_tma_f64_kh2048.md): FP64-pipe thread instructions and flops
+# (DADD + DMUL + 2 DFMA).  The FP64 pipe issues 2 thread instructions per
+# clock per SM (152 SMs; 2 x 2 flops x 152 x 2.07 GHz = 1.26 TFLOP/s, the
+# part's FP64 rate).
+FP64_PIPE_INST_PER_CELL = 327.3
+FP64_FLOPS_PER_CELL = 436.3
+FP64_LANES_PER_SM = 2
+N_SMS = 152
+EXACT_PROFILES = os.path.join(ROOT, "tests", "golden", "riemann_exact_profiles.json")
 
 
 def parse():
@@ -55,6 +65,7 @@ def parse():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-problems", action="store_true", help="skip the tube / 2-D Riemann problem runs")
     ap.add_argument("--batch-steps", type=int, default=1000, help="timed steps of the 256-instance sweep")
     ap.add_argument("--batch-count", type=int, default=256, help="instances of the sweep (first n screened draws)")
     ap.add_argument("--tile", type=int, default=0, help="TMA kernel variant (0 = library default)")
@@ -322,14 +333,28 @@ def run_ours(args):
         assert g64.health() == Bd.MRT_OK
         g64.close()
         per64 = ms64 * 1e-3 / k64
-        line["fp64"] = {"value": cells / per64, "unit": "cell-updates/s", "steps": k64,
+        rate64 = cells / per64
+        clk = (line["clocks"].get("sm_max_mhz") or 2070.0) * 1e6
+        pipe_peak = N_SMS * FP64_LANES_PER_SM * clk                    # thread instructions / s
+        line["fp64"] = {"value": rate64, "unit": "cell-updates/s", "steps": k64,
                         "hbm_achieved_gbs": BYTES_PER_CELL_F64 * cells / per64 / 1e9,
-                        "hbm_frac": BYTES_PER_CELL_F64 * cells / per64 / 1e9 / peak, "bound": "alu (FP64)"}
+                        "hbm_frac": BYTES_PER_CELL_F64 * cells / per64 / 1e9 / peak,
+                        "roofline": {"bound": "alu", "achieved": rate64 * FP64_FLOPS_PER_CELL / 1e12,
+                                     "peak": 2 * pipe_peak / 1e12, "unit": "TFLOP/s",
+                                     "frac": rate64 * FP64_FLOPS_PER_CELL / (2 * pipe_peak),
+                                     "pipe_frac": rate64 * FP64_PIPE_INST_PER_CELL / pipe_peak,
+                                     "peak_source": "derived: 152 SMs x 2 FP64 lanes x 2 flops x max SM clock",
+                                     "per_cell": {"fp64_pipe_inst": FP64_PIPE_INST_PER_CELL,
+                                                  "flops": FP64_FLOPS_PER_CELL}}}
 
     # adjoint / forward cost (smooth vortex 512^2, 500 FP32 steps, checkpoints
     # every 50; and the 4096^2 workload for the HBM-bound ratio)
     if not args.no_adjoint:
         line["adjoint"] = adjoint_costs(Bd, W, torch, stream)
+
+    # the paper's tube and 2-D problems: throughput next to error vs exact
+    if not args.no_problems:
+        line["paper_problems"] = paper_problems(Bd, W, torch, stream)
 
     # 256 independent tube/ripple instances of uneven size, one launch per step
     if not args.no_batch:
@@ -405,6 +430,75 @@ def adjoint_costs(Bd, W, torch, stream):
                      "backward_over_forward": bwd / fwd,
                      "note": "device-resident fields and gradients; backward = segment recompute + "
                              "reverse step + ghost/init adjoints + rate sums"}
+    return out
+
+
+def _shock_x(rho, dx, behind, ahead):
+    """Position of a right-moving shock: the last cell centre (from the
+    right) where rho exceeds the mean of the two states, interpolated."""
+    mid = 0.5 * (behind + ahead)
+    i = int(np.nonzero(rho > mid)[0][-1])
+    x = (i + 0.5) * dx
+    if i + 1 < len(rho):
+        x += dx * (rho[i] - mid) / (rho[i] - rho[i + 1])
+    return x
+
+
+def paper_problems(Bd, W, torch, stream):
+    """Sod (400 x 4, FP64), strong shock (2048 x 8, FP32 and FP64), colliding
+    shocks (1300 x 4, gamma 7/5, MRT and SRT rates, FP64, t = 0.13) and the
+    four-quadrant 2-D Riemann problem (500^2): cell-updates/s with the error
+    against the stored exact solutions."""
+    with open(EXACT_PROFILES) as fh:
+        exact = json.load(fh)
+    out = {}
+
+    def timed(w, prec, nsteps):
+        g = Bd.Grid.from_workload(w, precision=prec, stream=stream.cuda_stream)
+        t0 = g.totals()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        g.step(nsteps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        return g, ms, t0
+
+    cases = [("sod_400x4", W.sod_tube(), (Bd.FP64,)), ("strong_shock_2048x8", W.strong_shock(), (Bd.FP32, Bd.FP64)),
+             ("colliding_shocks_gamma1.4", W.colliding_shocks(gamma=1.4), (Bd.FP64,)),
+             ("colliding_shocks_gamma1.4_srt", W.colliding_shocks(gamma=1.4, mrt=False), (Bd.FP64,))]
+    for name, w, precs in cases:
+        ex = exact[name.replace("_srt", "")]
+        rho_ex = np.asarray(ex["rho"])
+        for prec in precs:
+            g, ms, t0 = timed(w, prec, w.nsteps)
+            ok = g.health() == Bd.MRT_OK
+            r = g.macro()[0][0]
+            t1 = g.totals()
+            g.close()
+            d = {"steps": w.nsteps, "ms": ms, "cell_updates_per_s": w.cells * w.nsteps / (ms * 1e-3),
+                 "healthy": ok, "l1_rho_vs_exact": float(np.mean(np.abs(r - rho_ex))),
+                 "tv_excess": float(np.sum(np.abs(np.diff(r))) - np.sum(np.abs(np.diff(rho_ex))))}
+            if not name.startswith("colliding"):
+                # u = 0 at both fixed ends: the total mass is conserved
+                d["mass_drift_rel"] = float(abs(t1[0] - t0[0]) / abs(t0[0]))
+                d["shock_x_error_dx"] = (_shock_x(r, w.dx, ex["star"]["rho_r"], ex["right"][0])
+                                         - ex["shock_x"]["right"]) / w.dx
+            out[f"{name}_{'fp64' if prec == Bd.FP64 else 'fp32'}"] = d
+    w = W.four_quadrant_riemann(n=500, nsteps=1000)
+    g, ms, _ = timed(w, Bd.FP32, 1000)
+    flagged = None
+    for k in range(1000, 12000, 100):
+        if g.health() != Bd.MRT_OK:
+            flagged = k
+            break
+        g.step(100)
+    g.close()
+    out["four_quadrant_500x500_fp32"] = {"steps": 1000, "ms": ms,
+                                         "cell_updates_per_s": w.cells * 1000 / (ms * 1e-3),
+                                         "health_flag_by_step": flagged,
+                                         "note": "positivity of P is lost near step 1400 under forward Euler"}
     return out
 
 

@@ -182,6 +182,59 @@ def vortex_target(w: Workload, seed: int = 5) -> np.ndarray:
     return np.ascontiguousarray(T ** (1.0 / (w.gamma - 1.0)))
 
 
+def four_quadrant_riemann(n: int = 500, nsteps: int = 12000) -> Workload:
+    """Two-dimensional Riemann problem of Sect. (c): four uniform states in
+    the quadrants of the unit square, split at x = y = 1/2 (quadrant 1 upper
+    right, counted counter-clockwise):
+        1: (rho, u, v, T) = (1.5, 0, 0, 1)
+        2: (0.5323, 1.206, 0, 0.3/0.5323)
+        3: (0.138, 1.206, 1.206, 0.029/0.138)
+        4: (0.5323, 0, 1.206, 0.3/0.5323)
+    gamma 1.4; dx = 1/n, dt = 0.005 dx (1e-5 at the paper's n = 500, so
+    t = 0.12 after 12000 steps); s_8 = s_9 = 2e4, every other rate 3e3 at
+    n = 500 (sigma = s dt = 0.2 and 0.03, kept at other n); fixed-equilibrium
+    ghosts on all four sides.  Pr = s_8/s_6 follows from these rates."""
+    dx = 1.0 / n
+    dt = 0.005 * dx
+    c = (np.arange(n) + 0.5) * dx
+    Y, X = np.meshgrid(c, c, indexing="ij")
+    q = np.where(X >= 0.5, np.where(Y >= 0.5, 0, 3), np.where(Y >= 0.5, 1, 2))
+    states = np.array([[1.5, 0.0, 0.0, 1.0],
+                       [0.5323, 1.206, 0.0, 0.3 / 0.5323],
+                       [0.138, 1.206, 1.206, 0.029 / 0.138],
+                       [0.5323, 0.0, 1.206, 0.3 / 0.5323]])
+    f = [np.ascontiguousarray(states[q, k]) for k in range(4)]
+    sigma = np.full(16, 0.03)
+    sigma[7] = sigma[8] = 0.2
+    return Workload("four_quadrant_riemann", n, n, dx, dt, 1.4, 0.2 / 0.03, sigma, BC_FIXED_EQ, BC_FIXED_EQ,
+                    f[0], f[1], f[2], f[3], nsteps, {"t_end": nsteps * dt})
+
+
+def colliding_shocks(gamma: float = 1.4, mrt: bool = True, nx: int = 1300, ny: int = 4, x0: float = 0.4,
+                     nsteps: int = 130000) -> Workload:
+    """One-dimensional Riemann problem of Sect. (b) on the 2-D model:
+    (rho, u, v, T) = (5.99924, 19.5975, 0, 76.8254) left of x0 and
+    (5.99242, -6.19633, 0, 7.69222) right of it; dx = 0.002, dt = 1e-6
+    (t = 0.13 after 130000 steps); x in [0, nx dx] with fixed-equilibrium
+    ends (2.6 units at nx = 1300, so that no wave of either gamma reaches an
+    end by t = 0.13), y periodic.  Rates: MRT s_5 = 5e3, s_6 = 1e4, every
+    other s = 1e5; SRT every s = 1e5 (tau = 1e-5)."""
+    dx, dt = 0.002, 1e-6
+    x = (np.arange(nx) + 0.5) * dx
+    left = np.broadcast_to(x < x0, (ny, nx))
+    rho = np.where(left, 5.99924, 5.99242)
+    ux = np.where(left, 19.5975, -6.19633)
+    T = np.where(left, 76.8254, 7.69222)
+    s = np.full(16, 1e5)
+    if mrt:
+        s[4], s[5] = 5e3, 1e4
+    return Workload("colliding_shocks_" + ("mrt" if mrt else "srt"), nx, ny, dx, dt, gamma, s[7] / s[5],
+                    s * dt, BC_FIXED_EQ, BC_PERIODIC, np.ascontiguousarray(rho), np.ascontiguousarray(ux),
+                    np.zeros((ny, nx)), np.ascontiguousarray(T), nsteps,
+                    {"x0": x0, "left": (5.99924, 19.5975, 5.99924 * 76.8254),
+                     "right": (5.99242, -6.19633, 5.99242 * 7.69222)})
+
+
 def shrink(w: Workload, nsteps: int) -> Workload:
     return replace(w, nsteps=nsteps)
 
