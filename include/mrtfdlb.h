@@ -58,9 +58,12 @@ typedef enum mrt_precision { MRT_FP32 = 0, MRT_FP64 = 1 } mrt_precision;
  * nodes set to f^eq). */
 typedef enum mrt_bc { MRT_BC_PERIODIC = 0, MRT_BC_FIXED_EQ = 1 } mrt_bc;
 
-/* Step kernel selection: MRT_KERNEL_AUTO picks the TMA-staged strip kernel
- * where it applies, MRT_KERNEL_DIRECT the one-thread-per-cell kernel that
- * reads its stencil straight from global memory. */
+/* Step kernel selection: MRT_KERNEL_TMA is the TMA-staged strip kernel,
+ * MRT_KERNEL_DIRECT the one-thread-per-cell kernel that reads its stencil
+ * straight from global memory.  MRT_KERNEL_AUTO picks the TMA kernel, except
+ * for FP64 grids of fewer than 77,824 cells, where the direct kernel (whose
+ * small blocks spread the FP64 arithmetic over more SMs) is faster.  Both
+ * run the same cell arithmetic; results agree to rounding. */
 typedef enum mrt_kernel { MRT_KERNEL_AUTO = 0, MRT_KERNEL_TMA = 1, MRT_KERNEL_DIRECT = 2 } mrt_kernel;
 
 typedef struct mrt_params {

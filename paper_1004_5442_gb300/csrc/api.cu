@@ -476,7 +476,11 @@ extern "C" mrt_status mrt_create(const mrt_params* params, const double* rho, co
         return bail(fail(MRT_ENOMEM, "cudaMalloc: %s", cudaGetErrorString(e)));
 
     // kernel choice and launch geometry
-    int kernel = params->kernel == MRT_KERNEL_AUTO ? MRT_KERNEL_TMA : params->kernel;
+    // AUTO: the TMA strip kernel, except for small FP64 grids, where the
+    // direct kernel's small blocks spread the FP64 arithmetic over more SMs
+    const long cells = (long)params->nx * params->ny;
+    int kernel = params->kernel;
+    if (kernel == MRT_KERNEL_AUTO) kernel = (g->fp64 && cells < kSmallFp64Cells) ? MRT_KERNEL_DIRECT : MRT_KERNEL_TMA;
     int parts = 0;
     if (kernel == MRT_KERNEL_TMA) {
         int occ = 0, sms = 0;

@@ -62,13 +62,17 @@ __global__ void __launch_bounds__(TMA_W, MINB) step_tma(const __grid_constant__ 
 // --------------------------------------------------------------------------
 // One thread per cell, stencil straight from global memory.
 // --------------------------------------------------------------------------
-constexpr int DIR_BX = 32, DIR_BY = 8;
+constexpr int DIR_BX = 32;
+// Block height: the tallest of 8, 4, 2, 1 rows that still gives this many
+// blocks (two per SM), so that small grids spread over the SMs; this matters
+// most in FP64, where one SM retires only two FP64 lanes per clock.
+constexpr long kDirectMinBlocks = 304;
 
-template <class T, bool TOTALS>
-__global__ void __launch_bounds__(DIR_BX* DIR_BY) step_direct(const StepArgs<T> a) {
+template <class T, bool TOTALS, int BY>
+__global__ void __launch_bounds__(DIR_BX* BY) step_direct(const StepArgs<T> a) {
     const Layout& L = a.L;
     const int x = blockIdx.x * DIR_BX + threadIdx.x;
-    const int y = blockIdx.y * DIR_BY + threadIdx.y;
+    const int y = blockIdx.y * BY + threadIdx.y;
     const bool active = x < L.nx && y < L.ny;
     bool bad = false;
     T q[4] = {0, 0, 0, 0};
@@ -153,18 +157,30 @@ cudaError_t tma_occupancy(int tile, int* blocks_per_sm) {
 
 template <class T>
 void direct_grid(const Layout& L, dim3* grid, dim3* block) {
-    *block = dim3(DIR_BX, DIR_BY);
-    *grid = dim3((L.nx + DIR_BX - 1) / DIR_BX, (L.ny + DIR_BY - 1) / DIR_BY);
+    const long bx = (L.nx + DIR_BX - 1) / DIR_BX;
+    int by = 8;
+    while (by > 1 && bx * ((L.ny + by - 1) / by) < kDirectMinBlocks) by /= 2;
+    *block = dim3(DIR_BX, by);
+    *grid = dim3((unsigned)bx, (L.ny + by - 1) / by);
+}
+
+template <class T, int BY>
+static void launch_direct_by(const StepArgs<T>& a, bool totals, dim3 grid, cudaStream_t st) {
+    if (totals)
+        step_direct<T, true, BY><<<grid, dim3(DIR_BX, BY), 0, st>>>(a);
+    else
+        step_direct<T, false, BY><<<grid, dim3(DIR_BX, BY), 0, st>>>(a);
 }
 
 template <class T>
 cudaError_t launch_step_direct(const StepArgs<T>& a, bool totals, cudaStream_t st) {
     dim3 grid, block;
     direct_grid<T>(a.L, &grid, &block);
-    if (totals) {
-        step_direct<T, true><<<grid, block, 0, st>>>(a);
-    } else {
-        step_direct<T, false><<<grid, block, 0, st>>>(a);
+    switch (block.y) {
+        case 8: launch_direct_by<T, 8>(a, totals, grid, st); break;
+        case 4: launch_direct_by<T, 4>(a, totals, grid, st); break;
+        case 2: launch_direct_by<T, 2>(a, totals, grid, st); break;
+        default: launch_direct_by<T, 1>(a, totals, grid, st); break;
     }
     return cudaGetLastError();
 }
