@@ -159,7 +159,16 @@ static mrt_status build_work(mrt_batch* b) {
             for (int y0 = 0; y0 < L.ny; y0 += b->rows_per_item)
                 items.push_back({i, x0, y0, std::min(b->rows_per_item, L.ny - y0)});
     }
-    std::stable_sort(items.begin(), items.end(), [](const Item& a, const Item& c) { return a.nrows > c.nrows; });
+    // longest first; among equal heights instance by instance and, inside an
+    // instance, row band by row band across all its strips, so that the items
+    // in flight at any moment form a compact block of one or a few instances
+    // whose shared boundary rows and halo columns are still in L2
+    std::stable_sort(items.begin(), items.end(), [](const Item& a, const Item& c) {
+        if (a.nrows != c.nrows) return a.nrows > c.nrows;
+        if (a.inst != c.inst) return a.inst < c.inst;
+        if (a.y0 != c.y0) return a.y0 < c.y0;
+        return a.x0 < c.x0;
+    });
     b->nitems = (int)items.size();
     cudaFree(b->d_items);
     b->d_items = nullptr;

@@ -23,10 +23,11 @@ struct Layout {
     long plane;     // elements per plane = pitch * (ny + 2)
 };
 
-// Flag word bits written by the kernels.
 // FP64 grids below this many cells (4 rows of 128 cells per SM) run the
 // direct kernel under MRT_KERNEL_AUTO.
 constexpr long kSmallFp64Cells = 152L * 128 * 4;
+
+// Flag word bits written by the kernels.
 constexpr unsigned FLAG_UNSTABLE = 1u;  // rho or P not positive, or not finite
 constexpr unsigned FLAG_TIMEOUT = 2u;   // a bounded wait ran out
 
