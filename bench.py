@@ -552,7 +552,7 @@ def sweep_tiles(args):
     from paper_1004_5442_gb300 import workloads as W
     w = W.kelvin_helmholtz(n=args.n, nsteps=0)
     for prec in (Bd.FP32, Bd.FP64):
-        for tile in (1, 2, 3, 4, 5):
+        for tile in (1, 2, 3, 4, 5, 6, 7):
             g = Bd.Grid.from_workload(w, precision=prec, kernel=Bd.KERNEL_TMA, tile=tile)
             g.step(max(args.warmup, 3))
             k = args.steps if prec == Bd.FP32 else max(5, args.steps // 10)

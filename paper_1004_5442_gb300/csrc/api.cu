@@ -398,6 +398,7 @@ static void release(mrt_grid* g) {
     cudaFree(g->flag);
     cudaFree(g->partials);
     cudaFree(g->totals_dev);
+    cudaFree(g->qnext);
     cudaFreeHost(g->host_stage);
     cudaFree(g->macro_tmp);
     mrt_tape_free(g->tape);
@@ -484,28 +485,55 @@ extern "C" mrt_status mrt_create(const mrt_params* params, const double* rho, co
     int parts = 0;
     if (kernel == MRT_KERNEL_TMA) {
         int occ = 0, sms = 0;
-        g->tile = params->tile ? params->tile : (g->fp64 ? default_tile<double>() : default_tile<float>());
-        e = g->fp64 ? tma_occupancy<double>(g->tile, &occ) : tma_occupancy<float>(g->tile, &occ);
-        if (e != cudaSuccess) return bail(fail(MRT_ECUDA, "occupancy query: %s", cudaGetErrorString(e)));
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, g->device);
-        if (occ < 1) occ = 1;
         const int strips = (params->nx + TMA_W - 1) / TMA_W;
+        auto occupancy = [&](int tile, int* o) {
+            return g->fp64 ? tma_occupancy<double>(tile, o) : tma_occupancy<float>(tile, o);
+        };
+        g->tile = params->tile;
+        if (g->tile == 0) {
+            // the work-queue tile when the grid gives every resident CTA at
+            // least two items, else one static chunk of rows per CTA
+            const int qt = kQueueTile, qr = tile_cfg(qt).queue_rows;
+            if ((e = occupancy(qt, &occ)) != cudaSuccess)
+                return bail(fail(MRT_ECUDA, "occupancy query: %s", cudaGetErrorString(e)));
+            const long items = (long)strips * ((params->ny + qr - 1) / qr);
+            g->tile = items >= 2L * sms * std::max(occ, 1) ? qt : (g->fp64 ? kStaticTileF64 : kStaticTileF32);
+        }
+        e = occupancy(g->tile, &occ);
+        if (e != cudaSuccess) return bail(fail(MRT_ECUDA, "occupancy query: %s", cudaGetErrorString(e)));
+        if (occ < 1) occ = 1;
         const long resident = (long)sms * occ;
-        // as many row chunks as fit in one wave of resident CTAs
-        long chunks = resident / strips;
-        if (chunks < 1) chunks = 1;
-        int rows = (int)((params->ny + chunks - 1) / chunks);
-        if (rows < 1) rows = 1;
-        g->rows_per_cta = rows;
-        g->tma_grid_x = strips;
-        g->tma_grid_y = (params->ny + rows - 1) / rows;
-        parts = g->tma_grid_x * g->tma_grid_y;
+        const int qrows = tile_cfg(g->tile).queue_rows;
+        g->strips = strips;
+        if (qrows > 0) {
+            // one wave of resident CTAs taking (row band, strip) items
+            g->rows_per_cta = qrows;
+            g->nitems = strips * ((params->ny + qrows - 1) / qrows);
+            g->tma_grid_x = (int)std::min<long>(resident, g->nitems);
+            g->tma_grid_y = 1;
+            parts = g->nitems;
+            if ((e = cudaMalloc(&g->qnext, 2 * sizeof(unsigned))) != cudaSuccess ||
+                (e = cudaMemsetAsync(g->qnext, 0, 2 * sizeof(unsigned), g->stream)) != cudaSuccess)
+                return bail(fail(MRT_ENOMEM, "cudaMalloc: %s", cudaGetErrorString(e)));
+        } else {
+            // as many row chunks as fit in one wave of resident CTAs
+            long chunks = resident / strips;
+            if (chunks < 1) chunks = 1;
+            int rows = (int)((params->ny + chunks - 1) / chunks);
+            if (rows < 1) rows = 1;
+            g->rows_per_cta = rows;
+            g->tma_grid_x = strips;
+            g->tma_grid_y = (params->ny + rows - 1) / rows;
+            parts = g->tma_grid_x * g->tma_grid_y;
+        }
     } else {
         dim3 gr, bl;
         if (g->fp64) direct_grid<double>(g->L, &gr, &bl); else direct_grid<float>(g->L, &gr, &bl);
         parts = (int)(gr.x * gr.y);
     }
     g->kernel = kernel;
+    g->parts = parts;
     const int red_parts = grid_for((long)params->nx * params->ny, RED_THREADS, 1024);
     g->max_parts = parts > red_parts ? parts : red_parts;
     if ((e = cudaMalloc(&g->partials, 4 * sizeof(double) * (size_t)g->max_parts)) != cudaSuccess)
@@ -569,6 +597,16 @@ mrt_status mrt_reinit(mrt_grid* g, const double* rho, const double* ux, const do
     return MRT_OK;
 }
 
+// Work-queue arguments of one launch; consecutive launches on the grid's
+// stream alternate between the two counters.
+static void queue_args(mrt_grid* g, StepArgsBase& a) {
+    a.strips = g->strips;
+    a.nitems = g->nitems;
+    a.next = g->qnext;
+    a.parity = g->qpar;
+    if (g->qnext) g->qpar ^= 1;
+}
+
 // One step from buffer `in` to buffer `out` (padded layout, same grid), with
 // the TMA maps of those buffers when the TMA kernel is in use.
 template <class T>
@@ -584,6 +622,7 @@ mrt_status step_between(mrt_grid* g, const void* in, void* out, const CUtensorMa
     if constexpr (sizeof(T) == 8) a.k = g->kd; else a.k = g->kf;
     a.in = static_cast<const T*>(in);
     a.out = static_cast<T*>(out);
+    queue_args(g, a);
     cudaError_t e = g->kernel == MRT_KERNEL_TMA
         ? launch_step_tma<T>(g->tile, map_in, map_out, a, g->tma_grid_x, g->tma_grid_y, totals, g->stream)
         : launch_step_direct<T>(a, totals, g->stream);
@@ -610,21 +649,17 @@ static mrt_status step_impl(mrt_grid* g, long nsteps) {
         const bool totals = s == nsteps - 1;
         a.in = static_cast<const T*>(g->f[g->cur]);
         a.out = static_cast<T*>(g->f[g->cur ^ 1]);
+        queue_args(g, a);
         cudaError_t e;
-        int parts;
         if (g->kernel == MRT_KERNEL_TMA) {
             e = launch_step_tma<T>(g->tile, &g->maps[g->cur], &g->maps_out[g->cur ^ 1], a, g->tma_grid_x,
                                    g->tma_grid_y, totals, g->stream);
-            parts = g->tma_grid_x * g->tma_grid_y;
         } else {
             e = launch_step_direct<T>(a, totals, g->stream);
-            dim3 gr, bl;
-            direct_grid<T>(g->L, &gr, &bl);
-            parts = (int)(gr.x * gr.y);
         }
         if (e != cudaSuccess) return fail(MRT_ECUDA, "step launch: %s", cudaGetErrorString(e));
         if (totals) {
-            totals_final_kernel<<<1, RED_THREADS, 0, g->stream>>>(g->partials, parts, g->p.dx * g->p.dx,
+            totals_final_kernel<<<1, RED_THREADS, 0, g->stream>>>(g->partials, g->parts, g->p.dx * g->p.dx,
                                                                  g->flag, g->totals_dev);
             CUDA_TRY(cudaGetLastError());
         }

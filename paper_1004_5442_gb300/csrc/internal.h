@@ -34,9 +34,14 @@ constexpr unsigned FLAG_TIMEOUT = 2u;   // a bounded wait ran out
 struct StepArgsBase {
     Layout L;
     int per_x, per_y;        // 1 where the axis is periodic (kernel refreshes ghosts)
-    int rows_per_cta;        // TMA kernel: rows per CTA chunk
-    double* partials;        // 4 doubles per CTA when totals are requested
+    int rows_per_cta;        // TMA kernel: rows per CTA chunk (per work item with a queue)
+    double* partials;        // 4 doubles per CTA (per work item with a queue) when totals are requested
     unsigned* flag;
+    // work-queue tiles: items are (row band, strip) pairs, numbered row band
+    // by row band; next[parity] is this launch's counter, next[parity ^ 1]
+    // the one the kernel clears for the following launch
+    int strips, nitems, parity;
+    unsigned* next;
 };
 
 template <class T>
@@ -62,20 +67,31 @@ struct TileCfg {
     int tstore;
     int minb;
     const char* name;
+    int queue_rows;  // 0: one static chunk of rows per CTA; else rows per work item
 };
-constexpr int NUM_TILES = 6;
-// tile 0 is "automatic"; 1..5 are explicit.  Tile 5 keeps row r-1 of the
-// y-moving planes in registers so more of the ring is in flight.
+constexpr int NUM_TILES = 8;
+// tile 0 is "automatic"; 1..7 are explicit.  Tiles 5 and 6 keep row r-1 of
+// the y-moving planes in registers so more of the ring is in flight.  Tiles
+// 6 and 7 are tiles 5 and 4 with a work queue: one wave of resident CTAs
+// takes (row band, strip) items of queue_rows rows from an atomic counter,
+// row band by row band, so the items in flight form a compact block whose
+// shared boundary rows and halo columns are still in L2.
 inline TileCfg tile_cfg(int tile) {
     switch (tile) {
-        case 1: return {6, 0, 4, "ring6-stg-4cta"};
-        case 2: return {4, 1, 4, "ring4-tma-4cta"};
-        case 3: return {6, 1, 3, "ring6-tma-3cta"};
-        case 4: return {5, 1, 3, "ring5-tma-3cta"};
-        default: return {4, 1, 4, "ring4-tma-4cta-ywin"};
+        case 1: return {6, 0, 4, "ring6-stg-4cta", 0};
+        case 2: return {4, 1, 4, "ring4-tma-4cta", 0};
+        case 3: return {6, 1, 3, "ring6-tma-3cta", 0};
+        case 4: return {5, 1, 3, "ring5-tma-3cta", 0};
+        case 5: return {4, 1, 4, "ring4-tma-4cta-ywin", 0};
+        case 6: return {4, 1, 4, "ring4-tma-4cta-ywin-queue16", 16};
+        default: return {5, 1, 3, "ring5-tma-3cta-queue32", 32};
     }
 }
-template <class T> constexpr int default_tile() { return sizeof(T) == 4 ? 4 : 1; }
+// Tile 0 picks the work-queue tile for grids with at least two items per
+// resident CTA, else the static tile of the precision.
+constexpr int kQueueTile = 6;
+constexpr int kStaticTileF32 = 4;
+constexpr int kStaticTileF64 = 1;
 
 template <class T>
 inline size_t tma_smem_bytes(int tile) {
@@ -184,6 +200,10 @@ struct mrt_grid {
     CUtensorMap maps_out[2];   // stores: x extent ends before the right ghost
     int tile = 0;
     int tma_grid_x = 0, tma_grid_y = 0, rows_per_cta = 0;
+    int strips = 0, nitems = 0;      // work-queue tiles: strips and (row band, strip) items
+    int parts = 0;                   // block partials a totals step writes
+    unsigned* qnext = nullptr;       // work-queue tiles: two launch counters
+    int qpar = 0;                    // which counter the next launch uses
     mrt::Coef<double> kd;
     mrt::Coef<float> kf;
     double b;

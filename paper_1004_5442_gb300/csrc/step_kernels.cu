@@ -34,11 +34,54 @@ namespace {
 
 using namespace tma;
 
-template <class T, bool TOTALS, int NS, bool TSTORE, int MINB, bool YWIN>
+// Work-queue form: each resident CTA takes (row band, strip) items from the
+// launch's counter; the index of its next item is fetched while the current
+// one is processed, into the other of two shared slots (the barriers of an
+// item separate a slot's read from its next write).  Totals are reduced per
+// item, so the fixed-order final sum does not depend on which CTA took which
+// item.
+template <class T, bool TOTALS, int NS, bool TSTORE, bool YWIN>
+__device__ __forceinline__ void step_queue(const CUtensorMap* map_in, const CUtensorMap* map_out,
+                                           const StepArgs<T>& a, unsigned char* smem_raw) {
+    __shared__ int s_item[2];
+    const Layout& L = a.L;
+    if (blockIdx.x == 0 && threadIdx.x == 0) a.next[a.parity ^ 1] = 0u;
+    if (threadIdx.x == 0) s_item[0] = (int)atomicAdd(&a.next[a.parity], 1u);
+    __syncthreads();
+    int cur = s_item[0];
+    if (cur >= a.nitems) return;
+    StripRing<T> R = strip_ring_init<T, NS, TSTORE>(smem_raw);
+    for (int k = 1; cur < a.nitems; ++k) {
+        if (threadIdx.x == 0) s_item[k & 1] = (int)atomicAdd(&a.next[a.parity], 1u);
+        const int band = cur / a.strips;
+        const int x0 = (cur - band * a.strips) * TMA_W;
+        const int y0 = band * a.rows_per_cta;
+        const int nrows = min(a.rows_per_cta, L.ny - y0);
+        bool bad = false;
+        Acc<T> acc[4];
+        if (!strip_chunk<T, TOTALS, NS, TSTORE, YWIN>(R, map_in, map_out, L, a.per_x, a.per_y, a.out, a.k, x0, y0,
+                                                      nrows, bad, acc)) {
+            strip_drain<T, NS>(R, a.flag);
+            return;
+        }
+        if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(a.flag, FLAG_UNSTABLE);
+        if (TOTALS) {
+            double v[4] = {acc[0].value(), acc[1].value(), acc[2].value(), acc[3].value()};
+            block_sum4(v, a.partials + 4 * (size_t)cur);
+        }
+        cur = s_item[k & 1];
+    }
+}
+
+template <class T, bool TOTALS, int NS, bool TSTORE, int MINB, bool YWIN, bool QUEUE>
 __global__ void __launch_bounds__(TMA_W, MINB) step_tma(const __grid_constant__ CUtensorMap map_in,
                                                         const __grid_constant__ CUtensorMap map_out,
                                                         const StepArgs<T> a) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
+    if (QUEUE) {
+        step_queue<T, TOTALS, NS, TSTORE, YWIN>(&map_in, &map_out, a, smem_raw);
+        return;
+    }
     const Layout& L = a.L;
     const int x0 = blockIdx.x * TMA_W;
     const int y0 = blockIdx.y * a.rows_per_cta;
@@ -103,25 +146,26 @@ __global__ void __launch_bounds__(DIR_BX* BY) step_direct(const StepArgs<T> a) {
     }
 }
 
-template <class T, int NS, bool TSTORE, int MINB, bool YWIN = false>
+template <class T, int NS, bool TSTORE, int MINB, bool YWIN = false, bool QUEUE = false>
 struct TmaKernels {
     static cudaError_t launch(const CUtensorMap* mi, const CUtensorMap* mo, const StepArgs<T>& a, dim3 grid,
                               size_t smem, bool totals, cudaStream_t st) {
         if (totals)
-            step_tma<T, true, NS, TSTORE, MINB, YWIN><<<grid, TMA_W, smem, st>>>(*mi, *mo, a);
+            step_tma<T, true, NS, TSTORE, MINB, YWIN, QUEUE><<<grid, TMA_W, smem, st>>>(*mi, *mo, a);
         else
-            step_tma<T, false, NS, TSTORE, MINB, YWIN><<<grid, TMA_W, smem, st>>>(*mi, *mo, a);
+            step_tma<T, false, NS, TSTORE, MINB, YWIN, QUEUE><<<grid, TMA_W, smem, st>>>(*mi, *mo, a);
         return cudaGetLastError();
     }
     static cudaError_t occupancy(size_t smem, int* occ) {
         cudaError_t e;
-        if ((e = cudaFuncSetAttribute(step_tma<T, true, NS, TSTORE, MINB, YWIN>,
+        if ((e = cudaFuncSetAttribute(step_tma<T, true, NS, TSTORE, MINB, YWIN, QUEUE>,
                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
             return e;
-        if ((e = cudaFuncSetAttribute(step_tma<T, false, NS, TSTORE, MINB, YWIN>,
+        if ((e = cudaFuncSetAttribute(step_tma<T, false, NS, TSTORE, MINB, YWIN, QUEUE>,
                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
             return e;
-        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, step_tma<T, false, NS, TSTORE, MINB, YWIN>, TMA_W, smem);
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, step_tma<T, false, NS, TSTORE, MINB, YWIN, QUEUE>,
+                                                             TMA_W, smem);
     }
 };
 
@@ -136,6 +180,8 @@ cudaError_t with_tile(int tile, Fn&& fn) {
         case 3: return fn(TmaKernels<T, ring_depth<T, 6>(), true, (sizeof(T) == 8 ? 2 : 3)>());
         case 4: return fn(TmaKernels<T, ring_depth<T, 5>(), true, (sizeof(T) == 8 ? 2 : 3)>());
         case 5: return fn(TmaKernels<T, ring_depth<T, 4>(), true, (sizeof(T) == 8 ? 2 : 4), true>());
+        case 6: return fn(TmaKernels<T, ring_depth<T, 4>(), true, (sizeof(T) == 8 ? 2 : 4), true, true>());
+        case 7: return fn(TmaKernels<T, ring_depth<T, 5>(), true, (sizeof(T) == 8 ? 2 : 3), false, true>());
         default: return cudaErrorInvalidValue;
     }
 }

@@ -22,7 +22,7 @@ pytestmark = pytest.mark.gpu
 
 KERNELS = [Bd.KERNEL_TMA, Bd.KERNEL_DIRECT]
 # (kernel, tile): every compiled TMA variant and the direct kernel
-VARIANTS = [(Bd.KERNEL_TMA, t) for t in (1, 2, 3, 4, 5)] + [(Bd.KERNEL_DIRECT, 0)]
+VARIANTS = [(Bd.KERNEL_TMA, t) for t in (1, 2, 3, 4, 5, 6, 7)] + [(Bd.KERNEL_DIRECT, 0)]
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -255,7 +255,7 @@ def test_full_size_kh_sampled_windows():
     corners = [(0, 0), (w.ny - n, w.nx - n), (0, w.nx - n), (w.ny - n, 0), (2000, 128 * 16 - 24)]
     wins = corners + [(int(rng.integers(0, w.ny - n)), int(rng.integers(0, w.nx - n))) for _ in range(7)]
     with Bd.Grid.from_workload(w, precision=Bd.FP32, kernel=Bd.KERNEL_TMA) as grid:
-        assert grid.info()["kernel"] == Bd.KERNEL_TMA and grid.info()["tile"] == 4
+        assert grid.info()["kernel"] == Bd.KERNEL_TMA and grid.info()["tile"] == 6
         grid.step(3)
         f3 = grid.get_f()
         grid.step(1)
