@@ -294,16 +294,26 @@ __global__ void __launch_bounds__(RED_THREADS) totals_partial_kernel(Layout L, c
 
 // Fixed-order sum of nparts block partials, times dx*dy, into out[0..3];
 // out[4] takes the flag word, so one copy brings back totals and health.
-__global__ void __launch_bounds__(RED_THREADS) totals_final_kernel(const double* partials, int nparts,
-                                                                   double scale, const unsigned* flag,
-                                                                   double* out) {
-    __shared__ double red[RED_THREADS][4];
+// Each of the FINAL_THREADS threads sums partials t, t + FINAL_THREADS, ...
+// in that order (loads unrolled so several are in flight), then a fixed tree.
+constexpr int FINAL_THREADS = 1024;
+__global__ void __launch_bounds__(FINAL_THREADS) totals_final_kernel(const double* partials, int nparts,
+                                                                     double scale, const unsigned* flag,
+                                                                     double* out) {
+    __shared__ double red[FINAL_THREADS][4];
     double acc[4] = {0, 0, 0, 0};
-    for (int p = threadIdx.x; p < nparts; p += RED_THREADS)
-        for (int k = 0; k < 4; ++k) acc[k] += partials[4 * p + k];
+    const double2* P = reinterpret_cast<const double2*>(partials);
+#pragma unroll 8
+    for (int p = threadIdx.x; p < nparts; p += FINAL_THREADS) {
+        const double2 a = P[2 * p], b = P[2 * p + 1];
+        acc[0] += a.x;
+        acc[1] += a.y;
+        acc[2] += b.x;
+        acc[3] += b.y;
+    }
     for (int k = 0; k < 4; ++k) red[threadIdx.x][k] = acc[k];
     __syncthreads();
-    for (int s = RED_THREADS / 2; s > 0; s >>= 1) {
+    for (int s = FINAL_THREADS / 2; s > 0; s >>= 1) {
         if (threadIdx.x < s)
             for (int k = 0; k < 4; ++k) red[threadIdx.x][k] += red[threadIdx.x + s][k];
         __syncthreads();
@@ -659,7 +669,7 @@ static mrt_status step_impl(mrt_grid* g, long nsteps) {
         }
         if (e != cudaSuccess) return fail(MRT_ECUDA, "step launch: %s", cudaGetErrorString(e));
         if (totals) {
-            totals_final_kernel<<<1, RED_THREADS, 0, g->stream>>>(g->partials, g->parts, g->p.dx * g->p.dx,
+            totals_final_kernel<<<1, FINAL_THREADS, 0, g->stream>>>(g->partials, g->parts, g->p.dx * g->p.dx,
                                                                  g->flag, g->totals_dev);
             CUDA_TRY(cudaGetLastError());
         }
@@ -710,7 +720,7 @@ static mrt_status totals_impl(mrt_grid* g) {
     totals_partial_kernel<T><<<blocks, RED_THREADS, 0, g->stream>>>(g->L, static_cast<const T*>(g->f[g->cur]),
                                                                      g->partials);
     CUDA_TRY(cudaGetLastError());
-    totals_final_kernel<<<1, RED_THREADS, 0, g->stream>>>(g->partials, blocks, g->p.dx * g->p.dx, g->flag,
+    totals_final_kernel<<<1, FINAL_THREADS, 0, g->stream>>>(g->partials, blocks, g->p.dx * g->p.dx, g->flag,
                                                           g->totals_dev);
     CUDA_TRY(cudaGetLastError());
     g->totals_fresh = true;
