@@ -79,11 +79,11 @@ typedef struct mrt_params {
     int precision;      /* mrt_precision of the stored f and of the arithmetic */
     int kernel;         /* mrt_kernel */
     int tile;           /* TMA kernel variant: 0 = tile 6 when the grid gives
-                           every resident CTA at least two 16-row items, else
+                           every resident CTA at least two 8-row items, else
                            tile 4 (FP32) or 1 (FP64);
                            1..5 = ring depth / store path / CTAs-per-SM choices
                            with one static chunk of rows per CTA; 6, 7 = the
-                           variants of 5 and 4 whose CTAs take 16- or 32-row
+                           variants of 5 and 4 whose CTAs take 8- or 32-row
                            work items from an atomic counter; other values
                            give MRT_EINVAL.  Results do not depend on it. */
 } mrt_params;

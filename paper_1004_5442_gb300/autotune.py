@@ -15,7 +15,7 @@ from . import binding as Bd
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 DEFAULT_CACHE = os.path.join(HERE, "_build", "autotune_cache.json")
-CANDIDATES = [(t, r) for t in (2, 4, 5) for r in (16, 32, 64, 128)]
+CANDIDATES = [(t, r) for t in (2, 4, 5) for r in (8, 16, 32, 64)]
 
 
 def signature(workloads) -> str:

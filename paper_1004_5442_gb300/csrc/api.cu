@@ -294,23 +294,15 @@ __global__ void __launch_bounds__(RED_THREADS) totals_partial_kernel(Layout L, c
 
 // Fixed-order sum of nparts block partials, times dx*dy, into out[0..3];
 // out[4] takes the flag word, so one copy brings back totals and health.
-// Each of the FINAL_THREADS threads sums partials t, t + FINAL_THREADS, ...
-// in that order (loads unrolled so several are in flight), then a fixed tree.
-constexpr int FINAL_THREADS = 1024;
-__global__ void __launch_bounds__(FINAL_THREADS) totals_final_kernel(const double* partials, int nparts,
-                                                                     double scale, const unsigned* flag,
-                                                                     double* out) {
-    __shared__ double red[FINAL_THREADS][4];
-    double acc[4] = {0, 0, 0, 0};
-    const double2* P = reinterpret_cast<const double2*>(partials);
-#pragma unroll 8
-    for (int p = threadIdx.x; p < nparts; p += FINAL_THREADS) {
-        const double2 a = P[2 * p], b = P[2 * p + 1];
-        acc[0] += a.x;
-        acc[1] += a.y;
-        acc[2] += b.x;
-        acc[3] += b.y;
-    }
+// Two passes spread the FP64 additions over many SMs (one SM of this part
+// retires only two FP64 lanes per clock): block b of the first pass sums
+// partials [b*chunk, (b+1)*chunk) - thread t those at t, t+256, ... - and a
+// fixed tree; the second pass sums the block results the same way.
+constexpr int FINAL_THREADS = 256;
+constexpr int FINAL_PER_BLOCK = 4 * FINAL_THREADS;  // partials per first-pass block
+constexpr int FINAL_MAX_BLOCKS = 1024;
+
+__device__ __forceinline__ void tree_sum4(double acc[4], double (*red)[4], double* dst, double scale) {
     for (int k = 0; k < 4; ++k) red[threadIdx.x][k] = acc[k];
     __syncthreads();
     for (int s = FINAL_THREADS / 2; s > 0; s >>= 1) {
@@ -318,10 +310,51 @@ __global__ void __launch_bounds__(FINAL_THREADS) totals_final_kernel(const doubl
             for (int k = 0; k < 4; ++k) red[threadIdx.x][k] += red[threadIdx.x + s][k];
         __syncthreads();
     }
-    if (threadIdx.x == 0) {
-        for (int k = 0; k < 4; ++k) out[k] = red[0][k] * scale;
-        out[4] = (double)*flag;
+    if (threadIdx.x == 0)
+        for (int k = 0; k < 4; ++k) dst[k] = red[0][k] * scale;
+}
+
+__global__ void __launch_bounds__(FINAL_THREADS) totals_pass_kernel(const double* partials, int nparts, int chunk,
+                                                                    double* block_sums) {
+    __shared__ double red[FINAL_THREADS][4];
+    double acc[4] = {0, 0, 0, 0};
+    const int p0 = blockIdx.x * chunk, p1 = min(nparts, p0 + chunk);
+    const double2* P = reinterpret_cast<const double2*>(partials);
+#pragma unroll 4
+    for (int p = p0 + threadIdx.x; p < p1; p += FINAL_THREADS) {
+        const double2 a = P[2 * p], b = P[2 * p + 1];
+        acc[0] += a.x;
+        acc[1] += a.y;
+        acc[2] += b.x;
+        acc[3] += b.y;
     }
+    tree_sum4(acc, red, block_sums + 4 * blockIdx.x, 1.0);
+}
+
+__global__ void __launch_bounds__(FINAL_THREADS) totals_final_kernel(const double* block_sums, int nblocks,
+                                                                     double scale, const unsigned* flag,
+                                                                     double* out) {
+    __shared__ double red[FINAL_THREADS][4];
+    double acc[4] = {0, 0, 0, 0};
+    for (int p = threadIdx.x; p < nblocks; p += FINAL_THREADS)
+        for (int k = 0; k < 4; ++k) acc[k] += block_sums[4 * p + k];
+    tree_sum4(acc, red, out, scale);
+    if (threadIdx.x == 0) out[4] = (double)*flag;
+}
+
+// Both passes on the grid's stream; result in g->totals_dev.
+static cudaError_t reduce_totals(mrt_grid* g, int nparts) {
+    int chunk = FINAL_PER_BLOCK;
+    int blocks = (nparts + chunk - 1) / chunk;
+    if (blocks > FINAL_MAX_BLOCKS) {
+        blocks = FINAL_MAX_BLOCKS;
+        chunk = (nparts + blocks - 1) / blocks;
+    }
+    if (blocks < 1) blocks = 1;
+    totals_pass_kernel<<<blocks, FINAL_THREADS, 0, g->stream>>>(g->partials, nparts, chunk, g->block_sums);
+    totals_final_kernel<<<1, FINAL_THREADS, 0, g->stream>>>(g->block_sums, blocks, g->p.dx * g->p.dx, g->flag,
+                                                            g->totals_dev);
+    return cudaGetLastError();
 }
 
 int grid_for(long n, int threads, int cap = 4096) {
@@ -408,6 +441,7 @@ static void release(mrt_grid* g) {
     cudaFree(g->flag);
     cudaFree(g->partials);
     cudaFree(g->totals_dev);
+    cudaFree(g->block_sums);
     cudaFree(g->qnext);
     cudaFreeHost(g->host_stage);
     cudaFree(g->macro_tmp);
@@ -483,6 +517,7 @@ extern "C" mrt_status mrt_create(const mrt_params* params, const double* rho, co
     if ((e = cudaMalloc(&g->flag, sizeof(unsigned))) != cudaSuccess ||
         (e = cudaMemsetAsync(g->flag, 0, sizeof(unsigned), g->stream)) != cudaSuccess ||
         (e = cudaMalloc(&g->totals_dev, 5 * sizeof(double))) != cudaSuccess ||
+        (e = cudaMalloc(&g->block_sums, 4 * sizeof(double) * FINAL_MAX_BLOCKS)) != cudaSuccess ||
         (e = cudaMallocHost(&g->host_stage, 8 * sizeof(double))) != cudaSuccess)
         return bail(fail(MRT_ENOMEM, "cudaMalloc: %s", cudaGetErrorString(e)));
 
@@ -522,7 +557,7 @@ extern "C" mrt_status mrt_create(const mrt_params* params, const double* rho, co
             g->nitems = strips * ((params->ny + qrows - 1) / qrows);
             g->tma_grid_x = (int)std::min<long>(resident, g->nitems);
             g->tma_grid_y = 1;
-            parts = g->nitems;
+            parts = g->nitems * (TMA_W / 32);  // one totals partial per warp of each item
             if ((e = cudaMalloc(&g->qnext, 2 * sizeof(unsigned))) != cudaSuccess ||
                 (e = cudaMemsetAsync(g->qnext, 0, 2 * sizeof(unsigned), g->stream)) != cudaSuccess)
                 return bail(fail(MRT_ENOMEM, "cudaMalloc: %s", cudaGetErrorString(e)));
@@ -668,11 +703,7 @@ static mrt_status step_impl(mrt_grid* g, long nsteps) {
             e = launch_step_direct<T>(a, totals, g->stream);
         }
         if (e != cudaSuccess) return fail(MRT_ECUDA, "step launch: %s", cudaGetErrorString(e));
-        if (totals) {
-            totals_final_kernel<<<1, FINAL_THREADS, 0, g->stream>>>(g->partials, g->parts, g->p.dx * g->p.dx,
-                                                                 g->flag, g->totals_dev);
-            CUDA_TRY(cudaGetLastError());
-        }
+        if (totals) CUDA_TRY(reduce_totals(g, g->parts));
         g->cur ^= 1;
         g->steps++;
     }
@@ -720,9 +751,7 @@ static mrt_status totals_impl(mrt_grid* g) {
     totals_partial_kernel<T><<<blocks, RED_THREADS, 0, g->stream>>>(g->L, static_cast<const T*>(g->f[g->cur]),
                                                                      g->partials);
     CUDA_TRY(cudaGetLastError());
-    totals_final_kernel<<<1, FINAL_THREADS, 0, g->stream>>>(g->partials, blocks, g->p.dx * g->p.dx, g->flag,
-                                                          g->totals_dev);
-    CUDA_TRY(cudaGetLastError());
+    CUDA_TRY(reduce_totals(g, blocks));
     g->totals_fresh = true;
     return MRT_OK;
 }

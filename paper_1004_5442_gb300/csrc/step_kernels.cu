@@ -38,8 +38,8 @@ using namespace tma;
 // launch's counter; the index of its next item is fetched while the current
 // one is processed, into the other of two shared slots (the barriers of an
 // item separate a slot's read from its next write).  Totals are reduced per
-// item, so the fixed-order final sum does not depend on which CTA took which
-// item.
+// warp and item (one partial per warp of each item, without a CTA barrier),
+// so the fixed-order final sum does not depend on which CTA took which item.
 template <class T, bool TOTALS, int NS, bool TSTORE, bool YWIN>
 __device__ __forceinline__ void step_queue(const CUtensorMap* map_in, const CUtensorMap* map_out,
                                            const StepArgs<T>& a, unsigned char* smem_raw) {
@@ -65,10 +65,7 @@ __device__ __forceinline__ void step_queue(const CUtensorMap* map_in, const CUte
             return;
         }
         if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(a.flag, FLAG_UNSTABLE);
-        if (TOTALS) {
-            double v[4] = {acc[0].value(), acc[1].value(), acc[2].value(), acc[3].value()};
-            block_sum4(v, a.partials + 4 * (size_t)cur);
-        }
+        if (TOTALS) warp_sum4(acc, a.partials + 4 * ((size_t)cur * (TMA_W / 32) + (threadIdx.x >> 5)));
         cur = s_item[k & 1];
     }
 }

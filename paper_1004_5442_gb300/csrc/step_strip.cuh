@@ -51,6 +51,37 @@ __device__ __forceinline__ void block_sum4(double v[4], double* dst) {
     }
 }
 
+// Warp-wide sum of the 4 running totals (fixed butterfly order, no CTA
+// barrier); lane 0 writes them to dst[0..3] as doubles.  FP32 accumulators
+// are combined as (hi, lo) pairs with error-free FP32 additions (Knuth's
+// TwoSum), which keeps their double-float accuracy without FP64
+// arithmetic: one SM of this part retires only two FP64 lanes per clock.
+__device__ __forceinline__ void warp_sum4(Acc<float> acc[4], double* dst) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        float hi = acc[q].hi, lo = acc[q].lo;
+        for (int o = 16; o > 0; o >>= 1) {
+            const float h2 = __shfl_xor_sync(0xffffffffu, hi, o);
+            const float l2 = __shfl_xor_sync(0xffffffffu, lo, o);
+            const float s = hi + h2;
+            const float bb = s - hi;
+            const float e = (hi - (s - bb)) + (h2 - bb);
+            lo = lo + l2 + e;
+            hi = s + lo;            // renormalise (fast two-sum, |s| >= |lo|)
+            lo = lo - (hi - s);
+        }
+        if ((threadIdx.x & 31) == 0) dst[q] = (double)hi + (double)lo;
+    }
+}
+__device__ __forceinline__ void warp_sum4(Acc<double> acc[4], double* dst) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        double v = acc[q].value();
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if ((threadIdx.x & 31) == 0) dst[q] = v;
+    }
+}
+
 template <class T>
 __device__ __forceinline__ bool healthy(T rho, T P) {
     // false for NaN, non-positive or infinite values
