@@ -163,7 +163,8 @@ mrt_status mrt_info(const mrt_grid *g, long *steps, long *pitch, long *plane_str
  * adding dL/ds_k of this step to g_s (fixed-ghost adjoints are not
  * returned).  Allocates its own temporaries; synchronises.
  * Errors: MRT_EINVAL (null pointers, bad counts, backward before record),
- * MRT_ENOMEM, MRT_ECUDA. */
+ * MRT_ENOMEM, MRT_ECUDA, MRT_ETIMEOUT (backward: a bounded device-side wait
+ * of the reverse step ran out). */
 mrt_status mrt_adjoint_record(mrt_grid *g, const double *rho0, const double *ux0, const double *uy0,
                               const double *T0, int on_device, long nsteps, int ckpt_every);
 mrt_status mrt_adjoint_backward(mrt_grid *g, const double *dL_drhoN, int on_device, double *g_rho0,

@@ -156,6 +156,7 @@ static mrt_status backward_impl(mrt_grid* g, const double* drho, double* outs[4]
     a.gyb = t->gyb;
     a.gpart = t->gpart;
     if constexpr (sizeof(T) == 8) a.k = g->kd; else a.k = g->kf;
+    a.flag = g->flag;
     int cur = 0;
     for (int c = t->nck - 1; c >= 0; --c) {
         const long s0 = (long)c * t->K;
@@ -192,8 +193,11 @@ static mrt_status backward_impl(mrt_grid* g, const double* drho, double* outs[4]
             A_TRY(cudaMemcpyAsync(outs[q], gout + q * n, sizeof(double) * n,
                                   on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, g->stream));
     double hs[12];
+    unsigned flag = 0;
     A_TRY(cudaMemcpyAsync(hs, sums, sizeof hs, cudaMemcpyDeviceToHost, g->stream));
+    A_TRY(cudaMemcpyAsync(&flag, g->flag, sizeof flag, cudaMemcpyDeviceToHost, g->stream));
     A_TRY(cudaStreamSynchronize(g->stream));
+    if (flag & FLAG_TIMEOUT) return mrt_fail(MRT_ETIMEOUT, "a device-side wait ran out");
     if (g_s) {
         for (int k = 0; k < 4; ++k) g_s[k] = 0.0;  // conserved moments: no dependence
         for (int k = 0; k < 12; ++k) g_s[4 + k] = hs[k] * g->p.dt;  // sigma_k = s_k dt
@@ -263,6 +267,7 @@ static mrt_status adjoint_step_impl(mrt_grid* g, const void* f, const void* lam_
     a.gyb = gyb;
     a.gpart = gpart;
     if constexpr (sizeof(T) == 8) a.k = g->kd; else a.k = g->kf;
+    a.flag = g->flag;
     if ((e = launch_adjoint_step<T>(a, g->stream)) == cudaSuccess) e = launch_sum_partials(gpart, nparts, sums, g->stream);
     for (int i = 0; i < 16 && e == cudaSuccess; ++i) {
         const size_t off = ((size_t)i * g->L.plane + g->L.pitch + g->L.G) * g->elem;

@@ -177,6 +177,7 @@ __global__ void __launch_bounds__(TMA_W) adjoint_tma_kernel(const __grid_constan
     };
     auto drain = [&]() {
         if (tid == 0) {
+            atomicOr(a.flag, FLAG_TIMEOUT);
             for (int l = waitedL; l < issuedL; ++l) mbar_wait_bounded(&fullL[l % ADJ_NSL], (uint32_t)((l / ADJ_NSL) & 1));
             for (int j = waitedF; j < issuedF; ++j) mbar_wait_bounded(&fullF[j % ADJ_NSF], (uint32_t)((j / ADJ_NSF) & 1));
             bulk_wait_all();
@@ -185,7 +186,7 @@ __global__ void __launch_bounds__(TMA_W) adjoint_tma_kernel(const __grid_constan
     bool ok = wait_l(0);
     ok = wait_l(1) && ok;
     ok = wait_l(2) && ok;
-    if (__syncthreads_or(!ok)) { drain(); return; }
+    if (__syncthreads_or(!ok)) { drain(); return; }  // drain() raises FLAG_TIMEOUT
 
     T gs[12];
 #pragma unroll

@@ -127,8 +127,9 @@ struct AdjArgs {
     T* lam_out;            // dL/df^n
     double* gxb;           // fixed x-ghost adjoints [16][2][ny] (unused if periodic)
     double* gyb;           // fixed y-ghost adjoints [16][2][nx]
-    double* gpart;         // per-block rate partials [nblocks][12], accumulated
+    double* gpart;         // rate partials [slots][12], accumulated (TMA kernel: one slot per item)
     Coef<T> k;
+    unsigned* flag;        // FLAG_TIMEOUT when a bounded wait ran out (TMA kernel)
 };
 
 template <class T>

@@ -204,7 +204,11 @@ __device__ __forceinline__ bool strip_chunk(StripRing<T>& R, const CUtensorMap* 
 #pragma unroll 1
     for (int r = 1; r <= nrows; ++r) {
         const int y = y0 + r - 1;
-        T* ob = R.outbuf + (size_t)(r & 1) * NV * TMA_W;
+        // Out slots alternate on the global row count (base + r), not on r:
+        // across an item boundary the first row then uses the slot whose
+        // last store the previous row already waited for (bulk_wait_read
+        // below), whatever the previous item's height.
+        T* ob = R.outbuf + (size_t)((base + r) & 1) * NV * TMA_W;
         if (YWIN) {
             ok = wait_row(r + 1);  // a failed wait is acted on at the barrier below
         }
