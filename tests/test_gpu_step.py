@@ -267,3 +267,21 @@ def test_full_size_kh_sampled_windows():
         scale = np.max(np.abs(want))
         assert np.max(np.abs(got - want)) <= 2e-6 * scale, (y0, x0)
     assert np.all(np.isfinite(tot)) and abs(tot[0] - 1.0) < 1e-6
+
+
+def test_automatic_kernel_and_tile_choice():
+    """Tile 0 / MRT_KERNEL_AUTO: the work-queue tile 6 on grids with at least
+    two 8-row items per resident CTA, the static tile 4 (FP32) or 1 (FP64)
+    on smaller ones, and the direct kernel on small FP64 grids."""
+    cases = [(W.kelvin_helmholtz(n=2048, nsteps=0), Bd.FP32, (Bd.KERNEL_TMA, 6)),
+             (W.kelvin_helmholtz(n=2048, nsteps=0), Bd.FP64, (Bd.KERNEL_TMA, 6)),
+             (W.kelvin_helmholtz(n=512, nsteps=0), Bd.FP32, (Bd.KERNEL_TMA, 4)),
+             (W.kelvin_helmholtz(n=512, nsteps=0), Bd.FP64, (Bd.KERNEL_TMA, 1)),
+             (W.sod_tube(), Bd.FP64, (Bd.KERNEL_DIRECT, None)),
+             (W.strong_shock(), Bd.FP32, (Bd.KERNEL_TMA, 4))]
+    for w, prec, (kernel, tile) in cases:
+        with Bd.Grid.from_workload(w, precision=prec) as g:
+            info = g.info()
+        assert info["kernel"] == kernel, (w.name, prec, info)
+        if tile is not None:
+            assert info["tile"] == tile, (w.name, prec, info)
