@@ -31,7 +31,14 @@
  *   - eta enters M only as eta_i^2 = 25/4 for i = 1..4, 0 otherwise;
  *   - a fixed-equilibrium boundary is one ghost cell beyond the domain that
  *     holds, for ever, the initial f (= f^eq of the initial state) of the
- *     adjacent domain cell.
+ *     adjacent domain cell;
+ *   - a reflecting boundary (Sect. (d): the velocity component normal to the
+ *     wall is the reverse of the one at the mirror-image interior point) is
+ *     one ghost cell beyond the domain holding, at every step, the adjacent
+ *     domain cell's f with each velocity mirrored across the wall: f_i of
+ *     the ghost = f_j of the cell, v_j the mirror image of v_i.  Axis kind
+ *     ORC_BC_REFLECT_FIXED puts such a wall at the low end and a
+ *     fixed-equilibrium inflow at the high end.
  *
  * Storage: f[i][y][x], i = 0..15 (paper's i = 1..16), x fastest, no padding.
  */
@@ -44,14 +51,14 @@
 
 #define NV 16
 
-enum { ORC_BC_PERIODIC = 0, ORC_BC_FIXED_EQ = 1 };
+enum { ORC_BC_PERIODIC = 0, ORC_BC_FIXED_EQ = 1, ORC_BC_REFLECT_FIXED = 2 };
 
 typedef struct {
     int nx, ny;
     double dx, dt;     /* dy == dx */
     double b;          /* total number of degrees of freedom; gamma = (b+2)/b */
     double s[NV];      /* relaxation rates s_1..s_16 in 1/time */
-    int bc_x, bc_y;    /* ORC_BC_PERIODIC or ORC_BC_FIXED_EQ */
+    int bc_x, bc_y;    /* ORC_BC_PERIODIC, ORC_BC_FIXED_EQ or ORC_BC_REFLECT_FIXED */
 } orc_cfg;
 
 /* ------------------------------------------------------------------------ */
@@ -254,6 +261,17 @@ void orc_ghosts_from_initial(int nx, int ny, const double *f0, double *gx, doubl
 /* One time step.                                                           */
 /* ------------------------------------------------------------------------ */
 
+/* Index j of the velocity whose v_j is the mirror image of v_i across a
+ * wall normal to x (axis 0) or to y (axis 1), found in the velocity table. */
+static int mirror_index(int i, int axis)
+{
+    const double tx = axis == 0 ? -g_vx[i] : g_vx[i];
+    const double ty = axis == 1 ? -g_vy[i] : g_vy[i];
+    for (int j = 0; j < NV; ++j)
+        if (fabs(g_vx[j] - tx) < 1e-12 && fabs(g_vy[j] - ty) < 1e-12 && g_eta2[j] == g_eta2[i]) return j;
+    return -1;
+}
+
 /* f_i at (x, y) where x may be -1..nx and y may be -1..ny (one at a time). */
 static double fat(const orc_cfg *c, const double *f, const double *gx,
                   const double *gy, int i, int x, int y)
@@ -263,6 +281,8 @@ static double fat(const orc_cfg *c, const double *f, const double *gx,
     if (x < 0 || x >= nx) {
         if (c->bc_x == ORC_BC_PERIODIC) {
             x = (x + nx) % nx;
+        } else if (c->bc_x == ORC_BC_REFLECT_FIXED && x < 0) {
+            return f[(size_t)mirror_index(i, 0) * n + (size_t)y * nx + 0];
         } else {
             const int side = (x < 0) ? 0 : 1;
             return gx[((size_t)i * 2 + side) * ny + y];
@@ -271,6 +291,8 @@ static double fat(const orc_cfg *c, const double *f, const double *gx,
     if (y < 0 || y >= ny) {
         if (c->bc_y == ORC_BC_PERIODIC) {
             y = (y + ny) % ny;
+        } else if (c->bc_y == ORC_BC_REFLECT_FIXED && y < 0) {
+            return f[(size_t)mirror_index(i, 1) * n + 0 * (size_t)nx + x];
         } else {
             const int side = (y < 0) ? 0 : 1;
             return gy[((size_t)i * 2 + side) * nx + x];
