@@ -55,8 +55,13 @@ typedef enum mrt_precision { MRT_FP32 = 0, MRT_FP64 = 1 } mrt_precision;
 /* Boundary treatment of one axis.  MRT_BC_FIXED_EQ: one ghost cell beyond
  * each end holds, for the whole run, the initial f of the adjacent domain
  * cell, i.e. f^eq = M^-1 fhat^eq of its initial state (Sect. (b): boundary
- * nodes set to f^eq). */
-typedef enum mrt_bc { MRT_BC_PERIODIC = 0, MRT_BC_FIXED_EQ = 1 } mrt_bc;
+ * nodes set to f^eq).  MRT_BC_REFLECT_FIXED: a reflecting wall at the low
+ * end (Sect. (d): the normal velocity is the reverse of the one at the
+ * mirror-image interior point) - its ghost holds, at every step, the
+ * adjacent cell's f with each velocity mirrored across the wall - and a
+ * fixed-equilibrium inflow at the high end.  Batches and the reverse mode
+ * accept periodic and fixed-equilibrium axes only. */
+typedef enum mrt_bc { MRT_BC_PERIODIC = 0, MRT_BC_FIXED_EQ = 1, MRT_BC_REFLECT_FIXED = 2 } mrt_bc;
 
 /* Step kernel selection: MRT_KERNEL_TMA is the TMA-staged strip kernel,
  * MRT_KERNEL_DIRECT the one-thread-per-cell kernel that reads its stencil

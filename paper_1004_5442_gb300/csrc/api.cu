@@ -206,27 +206,39 @@ __global__ void init_kernel(Layout L, InitCoef ic, const double* __restrict__ rh
     }
 }
 
-// Ghost columns, then ghost rows, of every plane: periodic axes copy the
-// opposite edge, fixed-equilibrium axes copy the adjacent edge.
+// Ghost columns, then ghost rows, of every plane.  Per side: GH_KEEP leaves
+// the ghost alone, GH_COPY copies the adjacent domain cell (a fixed
+// equilibrium at creation), GH_WRAP copies the opposite edge (periodic),
+// GH_MIRROR copies the adjacent cell with its velocities mirrored across the
+// wall (reflecting).
+enum { GH_KEEP = 0, GH_COPY = 1, GH_WRAP = 2, GH_MIRROR = 3 };
+
 template <class T>
-__global__ void ghost_cols_kernel(Layout L, int per_x, T* f) {
+__global__ void ghost_cols_kernel(Layout L, int lo, int hi, T* f) {
     const long n = 16L * L.ny;
     for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < n; t += (long)gridDim.x * blockDim.x) {
         const int i = (int)(t / L.ny), y = (int)(t % L.ny);
-        T* row = f + i * L.plane + (long)(y + 1) * L.pitch;
-        row[L.G - 1] = per_x ? row[L.G + L.nx - 1] : row[L.G];
-        row[L.G + L.nx] = per_x ? row[L.G] : row[L.G + L.nx - 1];
+        const long r = (long)(y + 1) * L.pitch;
+        T* row = f + i * L.plane + r;
+        if (lo == GH_COPY) row[L.G - 1] = row[L.G];
+        if (lo == GH_WRAP) row[L.G - 1] = row[L.G + L.nx - 1];
+        if (lo == GH_MIRROR) row[L.G - 1] = f[mirror_plane(i, 0) * L.plane + r + L.G];
+        if (hi == GH_COPY) row[L.G + L.nx] = row[L.G + L.nx - 1];
+        if (hi == GH_WRAP) row[L.G + L.nx] = row[L.G];
     }
 }
 
 template <class T>
-__global__ void ghost_rows_kernel(Layout L, int per_y, T* f) {
+__global__ void ghost_rows_kernel(Layout L, int lo, int hi, T* f) {
     const long n = 16L * L.nx;
     for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < n; t += (long)gridDim.x * blockDim.x) {
         const int i = (int)(t / L.nx), x = (int)(t % L.nx);
         T* p = f + i * L.plane + L.G + x;
-        p[0] = per_y ? p[(long)L.ny * L.pitch] : p[L.pitch];
-        p[(long)(L.ny + 1) * L.pitch] = per_y ? p[L.pitch] : p[(long)L.ny * L.pitch];
+        if (lo == GH_COPY) p[0] = p[L.pitch];
+        if (lo == GH_WRAP) p[0] = p[(long)L.ny * L.pitch];
+        if (lo == GH_MIRROR) p[0] = f[mirror_plane(i, 1) * L.plane + L.pitch + L.G + x];
+        if (hi == GH_COPY) p[(long)(L.ny + 1) * L.pitch] = p[(long)L.ny * L.pitch];
+        if (hi == GH_WRAP) p[(long)(L.ny + 1) * L.pitch] = p[L.pitch];
     }
 }
 
@@ -422,8 +434,8 @@ static mrt_status validate(const mrt_params* p) {
         if (!(p->s[k] >= 0) || !std::isfinite(p->s[k]))
             return fail(MRT_EINVAL, "rate s_%d must be finite and >= 0", k + 1);
     if (!std::isfinite(p->Pr)) return fail(MRT_EINVAL, "Pr must be finite");
-    if (p->bc_x != MRT_BC_PERIODIC && p->bc_x != MRT_BC_FIXED_EQ) return fail(MRT_EINVAL, "bad bc_x");
-    if (p->bc_y != MRT_BC_PERIODIC && p->bc_y != MRT_BC_FIXED_EQ) return fail(MRT_EINVAL, "bad bc_y");
+    if (p->bc_x < MRT_BC_PERIODIC || p->bc_x > MRT_BC_REFLECT_FIXED) return fail(MRT_EINVAL, "bad bc_x");
+    if (p->bc_y < MRT_BC_PERIODIC || p->bc_y > MRT_BC_REFLECT_FIXED) return fail(MRT_EINVAL, "bad bc_y");
     if (p->precision != MRT_FP32 && p->precision != MRT_FP64) return fail(MRT_EINVAL, "bad precision");
     if (p->kernel < MRT_KERNEL_AUTO || p->kernel > MRT_KERNEL_DIRECT) return fail(MRT_EINVAL, "bad kernel");
     if (p->tile < 0 || p->tile >= NUM_TILES) return fail(MRT_EINVAL, "bad tile %d", p->tile);
@@ -450,11 +462,33 @@ static void release(mrt_grid* g) {
     delete g;
 }
 
+// Ghost modes of an axis at creation (every ghost set) and on a refresh
+// after the state was replaced (fixed-equilibrium ghosts keep their values).
+static void ghost_modes(int bc, bool creation, int* lo, int* hi) {
+    if (bc == MRT_BC_PERIODIC) {
+        *lo = *hi = GH_WRAP;
+    } else if (bc == MRT_BC_REFLECT_FIXED) {
+        *lo = GH_MIRROR;
+        *hi = creation ? GH_COPY : GH_KEEP;
+    } else {
+        *lo = *hi = creation ? GH_COPY : GH_KEEP;
+    }
+}
+
+template <class T>
+static void launch_ghost_kernels(mrt_grid* g, T* f, bool creation) {
+    int xl, xh, yl, yh;
+    ghost_modes(g->p.bc_x, creation, &xl, &xh);
+    ghost_modes(g->p.bc_y, creation, &yl, &yh);
+    if (xl != GH_KEEP || xh != GH_KEEP)
+        ghost_cols_kernel<T><<<grid_for(16L * g->L.ny, 256), 256, 0, g->stream>>>(g->L, xl, xh, f);
+    if (yl != GH_KEEP || yh != GH_KEEP)
+        ghost_rows_kernel<T><<<grid_for(16L * g->L.nx, 256), 256, 0, g->stream>>>(g->L, yl, yh, f);
+}
+
 template <class T>
 static void launch_ghosts(mrt_grid* g, int buf) {
-    T* f = static_cast<T*>(g->f[buf]);
-    ghost_cols_kernel<T><<<grid_for(16L * g->L.ny, 256), 256, 0, g->stream>>>(g->L, g->p.bc_x == MRT_BC_PERIODIC, f);
-    ghost_rows_kernel<T><<<grid_for(16L * g->L.nx, 256), 256, 0, g->stream>>>(g->L, g->p.bc_y == MRT_BC_PERIODIC, f);
+    launch_ghost_kernels<T>(g, static_cast<T*>(g->f[buf]), true);
 }
 
 template <class T>
@@ -494,6 +528,8 @@ extern "C" mrt_status mrt_create(const mrt_params* params, const double* rho, co
     g->L.nx = params->nx;
     g->L.ny = params->ny;
     g->L.G = G;
+    g->L.refl_x = params->bc_x == MRT_BC_REFLECT_FIXED;
+    g->L.refl_y = params->bc_y == MRT_BC_REFLECT_FIXED;
     // room for the right ghost column, and for a whole TMA box even when the
     // grid is narrower than one strip
     const long need = std::max<long>(G + params->nx + 1, G + TMA_W + 16 / (long)g->elem);
@@ -809,18 +845,13 @@ extern "C" mrt_status mrt_set_f(mrt_grid* g, const void* f, int on_device) {
     return MRT_OK;
 }
 
-// Periodic ghost columns / rows of a padded buffer from its own data.
+// Periodic and reflecting-wall ghosts of a padded buffer from its own data
+// (fixed-equilibrium ghosts keep their values).
 mrt_status mrt_refresh_periodic_ghosts(mrt_grid* g, void* buf) {
-    const int per_x = g->p.bc_x == MRT_BC_PERIODIC, per_y = g->p.bc_y == MRT_BC_PERIODIC;
-    if (g->fp64) {
-        double* fd = static_cast<double*>(buf);
-        if (per_x) ghost_cols_kernel<double><<<grid_for(16L * g->L.ny, 256), 256, 0, g->stream>>>(g->L, 1, fd);
-        if (per_y) ghost_rows_kernel<double><<<grid_for(16L * g->L.nx, 256), 256, 0, g->stream>>>(g->L, 1, fd);
-    } else {
-        float* ff = static_cast<float*>(buf);
-        if (per_x) ghost_cols_kernel<float><<<grid_for(16L * g->L.ny, 256), 256, 0, g->stream>>>(g->L, 1, ff);
-        if (per_y) ghost_rows_kernel<float><<<grid_for(16L * g->L.nx, 256), 256, 0, g->stream>>>(g->L, 1, ff);
-    }
+    if (g->fp64)
+        launch_ghost_kernels<double>(g, static_cast<double*>(buf), false);
+    else
+        launch_ghost_kernels<float>(g, static_cast<float*>(buf), false);
     CUDA_TRY(cudaGetLastError());
     return MRT_OK;
 }

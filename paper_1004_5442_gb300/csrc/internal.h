@@ -21,6 +21,7 @@ struct Layout {
     int G;          // elements before column 0
     long pitch;     // elements per row
     long plane;     // elements per plane = pitch * (ny + 2)
+    int refl_x, refl_y;  // 1: reflecting wall at the low end of the axis (ghost refreshed every step)
 };
 
 // FP64 grids below this many cells (4 rows of 128 cells per SM) run the

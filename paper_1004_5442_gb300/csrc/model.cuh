@@ -36,6 +36,15 @@ __host__ __device__ constexpr double kU(int g) {
 __host__ __device__ constexpr double kV(int g) { return g == 0 ? 1.0 : g == 1 ? 36.0 : g == 2 ? 4.0 : 9.0; }
 __host__ __device__ constexpr double kW(int g) { return g == 0 ? 7.25 : g == 1 ? 36.0 : g == 2 ? 4.0 : 9.0; }
 
+// Plane of the velocity mirrored across a wall normal to x (axis 0) or to y
+// (axis 1).  Inside a group of four the order is (1,0),(0,1),(-1,0),(0,-1)
+// for the axis groups and (1,1),(-1,1),(-1,-1),(1,-1) for the diagonal ones.
+__host__ __device__ constexpr int mirror_plane(int i, int axis) {
+    const int g = i >> 2, k = i & 3;
+    if (g < 2) return 4 * g + (axis == 0 ? (k == 0 ? 2 : k == 2 ? 0 : k) : (k == 1 ? 3 : k == 3 ? 1 : k));
+    return 4 * g + (axis == 0 ? (k ^ 1) : (3 - k));
+}
+
 // Everything a step kernel needs besides the state.
 template <class T>
 struct Coef {

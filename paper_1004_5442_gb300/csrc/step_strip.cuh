@@ -88,9 +88,10 @@ __device__ __forceinline__ bool healthy(T rho, T P) {
     return rho > (T)0 && P > (T)0 && rho < (T)INFINITY && P < (T)INFINITY;
 }
 
-// Store a cell's 16 outputs and, on periodic axes, the ghost copies the next
-// step reads (column G-1 mirrors x = nx-1, column G+nx mirrors x = 0; row 0
-// mirrors y = ny-1, row ny+1 mirrors y = 0).
+// Store a cell's 16 outputs and the ghost copies the next step reads: on
+// periodic axes column G-1 repeats x = nx-1, column G+nx x = 0, row 0
+// y = ny-1, row ny+1 y = 0; behind a reflecting wall (low end) column G-1
+// holds x = 0 and row 0 holds y = 0 with each velocity mirrored.
 template <class T>
 __device__ __forceinline__ void store_cell(T* __restrict__ out, const Layout& L, int per_x,
                                            int per_y, int x, int y, const T v[NV]) {
@@ -117,6 +118,14 @@ __device__ __forceinline__ void store_cell(T* __restrict__ out, const Layout& L,
 #pragma unroll
             for (int i = 0; i < NV; ++i) out[i * L.plane + col] = v[i];
         }
+    }
+    if (L.refl_x && x == 0) {
+#pragma unroll
+        for (int i = 0; i < NV; ++i) out[i * L.plane + row + L.G - 1] = v[mirror_plane(i, 0)];
+    }
+    if (L.refl_y && y == 0) {
+#pragma unroll
+        for (int i = 0; i < NV; ++i) out[i * L.plane + col] = v[mirror_plane(i, 1)];
     }
 }
 
@@ -291,6 +300,17 @@ __device__ __forceinline__ bool strip_chunk(StripRing<T>& R, const CUtensorMap* 
                 const long gc = (long)(y + 1) * L.pitch + (x == 0 ? L.G + L.nx : L.G - 1);
 #pragma unroll 4
                 for (int i = 0; i < NV; ++i) out[i * L.plane + gc] = ob[i * TMA_W + tid];
+            }
+            if (L.refl_x && x == 0) {
+                // reflecting wall: the mirrored cell behind it
+                const long gc = (long)(y + 1) * L.pitch + L.G - 1;
+#pragma unroll 4
+                for (int i = 0; i < NV; ++i) out[i * L.plane + gc] = ob[mirror_plane(i, 0) * TMA_W + tid];
+            }
+            if (L.refl_y && y == 0 && active) {
+                // reflecting wall: ghost row 0 is row 0 with mirrored planes
+#pragma unroll 4
+                for (int i = 0; i < NV; ++i) out[i * L.plane + L.G + x] = ob[mirror_plane(i, 1) * TMA_W + tid];
             }
         }
     }

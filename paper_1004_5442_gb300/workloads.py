@@ -29,6 +29,7 @@ import numpy as np
 
 BC_PERIODIC = 0
 BC_FIXED_EQ = 1
+BC_REFLECT_FIXED = 2   # reflecting wall at the low end, fixed inflow at the high end
 V_MAX = 6.0
 
 
@@ -233,6 +234,32 @@ def colliding_shocks(gamma: float = 1.4, mrt: bool = True, nx: int = 1300, ny: i
                     np.zeros((ny, nx)), np.ascontiguousarray(T), nsteps,
                     {"x0": x0, "left": (5.99924, 19.5975, 5.99924 * 76.8254),
                      "right": (5.99242, -6.19633, 5.99242 * 7.69222)})
+
+
+def richtmyer_meshkov(nx: int = 360, ny: int = 100, nsteps: int = 10400, x_shock: float = 0.25) -> Workload:
+    """Richtmyer-Meshkov configuration of Sect. (d): a 0.36 x 0.1 box on
+    360 x 100 cells (dx = 0.001), light gas (rho, u, v, p) = (0.1358, 0, 0, 1)
+    left of the interface x = 0.24 + 0.005 sin(pi/2 + 40 pi y), heavy gas
+    (1, 0, 0, 1) between it and the Mach 2.5 shock at x_shock, post-shock
+    state (3.33333, -2.07063, 0, 7.125) right of the shock; reflecting wall
+    on the left, fixed inflow of the post-shock state on the right, periodic
+    in y; gamma 1.4, dt = 1e-5 (t = 0.104 after 10400 steps), s_5 = 2e3 and
+    every other rate 1e5 (sigma = 0.02 and 1)."""
+    dx = 0.36 / nx
+    x = (np.arange(nx) + 0.5) * dx
+    y = (np.arange(ny) + 0.5) * dx
+    Y, X = np.meshgrid(y, x, indexing="ij")
+    iface = 0.24 + 0.005 * np.sin(np.pi / 2 + 40 * np.pi * Y)
+    light = X < iface
+    post = X >= x_shock
+    rho = np.where(light, 0.1358, np.where(post, 3.33333, 1.0))
+    ux = np.where(post, -2.07063, 0.0)
+    p = np.where(post, 7.125, 1.0)
+    sigma = np.full(16, 1.0)
+    sigma[4] = 0.02
+    return Workload("richtmyer_meshkov", nx, ny, dx, 1e-5, 1.4, 1.0, sigma, BC_REFLECT_FIXED, BC_PERIODIC,
+                    np.ascontiguousarray(rho), np.ascontiguousarray(ux), np.zeros((ny, nx)),
+                    np.ascontiguousarray(p / rho), nsteps, {"x_shock": x_shock, "t_end": nsteps * 1e-5})
 
 
 def shrink(w: Workload, nsteps: int) -> Workload:

@@ -1,6 +1,7 @@
-"""The paper's second and third test problems on the same kernels: the
-two-dimensional four-quadrant Riemann problem (Sect. (c)) and the colliding
-strong shocks solved with MRT and with SRT rates (Sect. (b)).
+"""The paper's test problems on the same kernels: the two-dimensional
+four-quadrant Riemann problem (Sect. (c)), the colliding strong shocks
+solved with MRT and with SRT rates (Sect. (b)) and the Richtmyer-Meshkov
+configuration with its reflecting wall and inflow (Sect. (d)).
 
 Under the forward-Euler reading of the time scheme, the four-quadrant
 problem with the printed rates loses positivity of the pressure after about
@@ -146,3 +147,38 @@ def test_colliding_shocks_mrt_oscillates_less_than_srt():
     print("MRT (L1, TV excess)", res[True], "SRT", res[False])
     assert res[True][0] < 0.6 * res[False][0]
     assert res[True][1] < 0.5 * res[False][1]
+
+
+def test_richtmyer_meshkov_parity_and_symmetry():
+    """360 x 100, reflecting wall left, post-shock inflow right, periodic in
+    y: 2000 steps (t = 0.02, the paper's second snapshot) against the oracle
+    (FP64 to 1e-10, FP32 L1 1e-4); the perturbation cos(40 pi y) makes the
+    problem symmetric about y = 0.05, which both runs keep."""
+    w = W.richtmyer_meshkov(nsteps=2000)
+    want = oracle.macro(run_oracle(w))
+    assert np.max(np.abs(want[0] - want[0][::-1])) <= 1e-12 * np.max(want[0])
+    with run_gpu(w, Bd.FP64) as g:
+        got = g.macro()
+    assert_parity(got, want, linf=1e-10, label="fp64")
+    with run_gpu(w, Bd.FP32) as g:
+        got32 = g.macro()
+    assert_parity(got32, want, l1=1e-4, label="fp32")
+    # mirrored rows run the same arithmetic in another summation order:
+    # FP64 keeps the symmetry to round-off, FP32 to its shock tolerances
+    assert np.max(np.abs(got[0] - got[0][::-1])) <= 1e-12 * np.max(got[0])
+    r = got32[0]
+    assert np.mean(np.abs(r - r[::-1])) <= 1e-5 * np.mean(r)
+    assert np.max(np.abs(r - r[::-1])) <= 1e-4 * np.max(r)
+
+
+def test_richtmyer_meshkov_full_run():
+    """The whole run to t = 0.104 (10400 steps, the last snapshot) stays
+    admissible in both precisions; the transmitted shock has reached and
+    left the wall (the density at the wall rises above the light gas's)."""
+    w = W.richtmyer_meshkov()
+    for prec in (Bd.FP32, Bd.FP64):
+        with run_gpu(w, prec) as g:
+            assert g.health() == Bd.MRT_OK
+            r = g.macro()[0]
+        assert np.all(np.isfinite(r)) and r.min() > 0
+        assert r[:, 0].mean() > 0.1358 * 1.5

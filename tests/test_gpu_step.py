@@ -285,3 +285,38 @@ def test_automatic_kernel_and_tile_choice():
         assert info["kernel"] == kernel, (w.name, prec, info)
         if tile is not None:
             assert info["tile"] == tile, (w.name, prec, info)
+
+
+@pytest.mark.parametrize("bcy", [Bd.BC_PERIODIC, Bd.BC_FIXED_EQ, Bd.BC_REFLECT_FIXED])
+def test_reflecting_wall_parity(bcy):
+    """Reflecting wall at the low x end (fixed inflow at the high end), and
+    on y as well in the last case: every kernel variant against the oracle,
+    300 x 37 (three strips, a ragged tail), 15 steps."""
+    w = W.random_smooth(300, 37, seed=23, amp=0.1, bc_x=Bd.BC_REFLECT_FIXED, bc_y=bcy, nsteps=15)
+    want = oracle.macro(run_oracle(w))
+    for kernel, tile in VARIANTS:
+        with run_gpu(w, Bd.FP64, kernel, tile=tile) as grid:
+            assert_parity(grid.macro(), want, linf=1e-12, label=f"fp64 k{kernel} t{tile}")
+        with run_gpu(w, Bd.FP32, kernel, tile=tile) as grid:
+            assert_parity(grid.macro(), want, linf=1e-5, label=f"fp32 k{kernel} t{tile}")
+
+
+def test_reflecting_wall_resume_and_rejections():
+    """mrt_set_f refreshes the wall's ghost from the new state (resume is bit
+    identical); batches and the reverse mode reject the wall."""
+    w = W.random_smooth(140, 21, seed=4, amp=0.1, bc_x=Bd.BC_REFLECT_FIXED, bc_y=Bd.BC_REFLECT_FIXED, nsteps=0)
+    with Bd.Grid.from_workload(w, precision=Bd.FP32) as a:
+        a.step(5)
+        ck = a.get_f()
+        a.step(6)
+        want = a.get_f()
+        a.set_f(np.zeros_like(ck) + 1.0)      # disturb the ghosts' sources
+        a.set_f(ck)
+        a.step(6)
+        np.testing.assert_array_equal(a.get_f(), want)
+        with pytest.raises(Bd.MrtError) as ei:
+            a.adjoint_record(w.rho, w.ux, w.uy, w.T, 3, 1)
+        assert ei.value.code == Bd.MRT_EINVAL
+    with pytest.raises(Bd.MrtError) as ei:
+        Bd.Batch([w])
+    assert ei.value.code == Bd.MRT_EINVAL
