@@ -446,9 +446,10 @@ def _shock_x(rho, dx, behind, ahead):
 
 def paper_problems(Bd, W, torch, stream):
     """Sod (400 x 4, FP64), strong shock (2048 x 8, FP32 and FP64), colliding
-    shocks (1300 x 4, gamma 7/5, MRT and SRT rates, FP64, t = 0.13) and the
+    shocks (1300 x 4, gamma 7/5, MRT and SRT rates, FP64, t = 0.13), the
+    Richtmyer-Meshkov run (360 x 100, reflecting wall, t = 0.104) and the
     four-quadrant 2-D Riemann problem (500^2): cell-updates/s with the error
-    against the stored exact solutions."""
+    against the stored exact solutions where one exists."""
     with open(EXACT_PROFILES) as fh:
         exact = json.load(fh)
     out = {}
@@ -495,6 +496,16 @@ def paper_problems(Bd, W, torch, stream):
             break
         g.step(100)
     g.close()
+    w = W.richtmyer_meshkov()
+    for prec in (Bd.FP32, Bd.FP64):
+        g, ms_rm, _ = timed(w, prec, w.nsteps)
+        ok = g.health() == Bd.MRT_OK
+        r = g.macro()[0]
+        g.close()
+        out[f"richtmyer_meshkov_360x100_{'fp64' if prec == Bd.FP64 else 'fp32'}"] = {
+            "steps": w.nsteps, "ms": ms_rm, "cell_updates_per_s": w.cells * w.nsteps / (ms_rm * 1e-3),
+            "healthy": ok, "y_symmetry_max_rel": float(np.max(np.abs(r - r[::-1])) / np.max(r)),
+            "rho_range": [float(r.min()), float(r.max())]}
     out["four_quadrant_500x500_fp32"] = {"steps": 1000, "ms": ms,
                                          "cell_updates_per_s": w.cells * 1000 / (ms * 1e-3),
                                          "health_flag_by_step": flagged,
