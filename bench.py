@@ -551,7 +551,8 @@ def batch_sweep(Bd, W, torch, args, peak):
             "autotune": [(d["tile"], d["rows_per_item"], round(d["ms_per_step"], 4)) for d in tuned["timings"]],
             "healthy_after": {"steps": k + 3, "instances_ok": healthy},
             "screening": {"acceptance_rate": screened["acceptance_rate"],
-                          "rule": "FP64 oracle 1-D pre-run, 1000 steps, rho and T finite and positive"}}
+                          "rule": "FP64 oracle on the full instance: rho and T finite and positive after each of "
+                                  "1000 steps"}}
 
 
 def sweep_tiles(args):

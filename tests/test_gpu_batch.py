@@ -91,9 +91,11 @@ def test_seeded_sweep_sampled_instances():
         b.step(1000)
         got = {i: b.grid(i).get_f() for i in pick}
         health = [b.grid(i).health() for i in range(len(ws))]
+    # the screening kept draws whose FP64 states stay admissible for all
+    # 1000 steps; the FP32 batch flags the states it reads (0..999)
     print("unstable instances after 1000 steps:", [i for i, h in enumerate(health) if h != Bd.MRT_OK])
     assert set(health) <= {Bd.MRT_OK, Bd.MRT_EUNSTABLE}
-    assert sum(h == Bd.MRT_OK for h in health) >= 0.9 * len(ws)
+    assert sum(h == Bd.MRT_OK for h in health) >= len(ws) - 2
     for i in pick:
         np.testing.assert_array_equal(got[i], _alone(ws[i], 1000), err_msg=f"instance {i}")
 
