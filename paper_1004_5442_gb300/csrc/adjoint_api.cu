@@ -187,7 +187,9 @@ static mrt_status backward_impl(mrt_grid* g, const double* drho, double* outs[4]
                                   g->stream));
     InitCoef ic;
     if (mrt_init_coef_build(g->b, &ic) != 0) return mrt_fail(MRT_ECUDA, "model blocks singular");
-    A_TRY(launch_init_adjoint<T>(g->L, ic, g->kd, static_cast<const T*>(t->lam[cur]), f0, f0 + n, f0 + 2 * n,
+    Coef<T> kc;
+    if constexpr (sizeof(T) == 8) kc = g->kd; else kc = g->kf;
+    A_TRY(launch_init_adjoint<T>(g->L, ic, kc, static_cast<const T*>(t->lam[cur]), f0, f0 + n, f0 + 2 * n,
                                  f0 + 3 * n, gout, gout + n, gout + 2 * n, gout + 3 * n, g->stream));
     A_TRY(launch_sum_partials(t->gpart, t->nparts, sums, g->stream));
     for (int q = 0; q < 4; ++q)

@@ -312,54 +312,56 @@ __global__ void ghost_adjoint_kernel(Layout L, int fix_x, int fix_y, const doubl
 }
 
 // dL/d(rho, ux, uy, T) from lam0 = dL/df^0, f^0 = Minv fhat^eq(m), m =
-// (rho, rho ux, rho uy, b rho T + rho (ux^2 + uy^2)).  FP64 throughout.
+// (rho, rho ux, rho uy, b rho T + rho (ux^2 + uy^2)).  Arithmetic in the
+// grid's precision (lam0 is held in it; an FP64 sweep over a large FP32 grid
+// would be bound by the FP64 pipe), results stored as doubles.
 template <class T>
-__global__ void init_adjoint_kernel(Layout L, InitCoef ic, Coef<double> kd, const T* __restrict__ lam,
+__global__ void init_adjoint_kernel(Layout L, InitCoef ic, Coef<T> kc, const T* __restrict__ lam,
                                     const double* __restrict__ rho, const double* __restrict__ ux,
                                     const double* __restrict__ uy, const double* __restrict__ Tf,
                                     double* g_rho, double* g_ux, double* g_uy, double* g_T) {
     const long n = (long)L.nx * L.ny;
     for (long c = blockIdx.x * (long)blockDim.x + threadIdx.x; c < n; c += (long)gridDim.x * blockDim.x) {
         const int x = (int)(c % L.nx), y = (int)(c / L.nx);
-        double l[NV];
-        for (int i = 0; i < NV; ++i) l[i] = (double)lam[i * L.plane + (long)(y + 1) * L.pitch + L.G + x];
+        T l[NV];
+        for (int i = 0; i < NV; ++i) l[i] = lam[i * L.plane + (long)(y + 1) * L.pitch + L.G + x];
         // Minv = (inverse butterfly) o (block inverse); transpose = scaled
         // butterfly, then the transposed block inverses
-        double bS[4], bX[4], bY[4], bQ[4];
+        T bS[4], bX[4], bY[4], bQ[4];
         for (int g = 0; g < 4; ++g) {
-            const double* v = l + 4 * g;
-            const double s02 = v[0] + v[2], s13 = v[1] + v[3], d02 = v[0] - v[2], d13 = v[1] - v[3];
-            bS[g] = 0.25 * (s02 + s13);
-            bQ[g] = 0.25 * (s02 - s13);
-            if (g < 2) { bX[g] = 0.5 * d02; bY[g] = 0.5 * d13; }
-            else { bX[g] = 0.25 * (d02 - d13); bY[g] = 0.25 * (d02 + d13); }
+            const T* v = l + 4 * g;
+            const T s02 = v[0] + v[2], s13 = v[1] + v[3], d02 = v[0] - v[2], d13 = v[1] - v[3];
+            bS[g] = (T)0.25 * (s02 + s13);
+            bQ[g] = (T)0.25 * (s02 - s13);
+            if (g < 2) { bX[g] = (T)0.5 * d02; bY[g] = (T)0.5 * d13; }
+            else { bX[g] = (T)0.25 * (d02 - d13); bY[g] = (T)0.25 * (d02 + d13); }
         }
-        double muA[4], muX[4], muY[4];
+        T muA[4], muX[4], muY[4];
         for (int kk = 0; kk < 4; ++kk) {
             muA[kk] = muX[kk] = muY[kk] = 0;
             for (int g = 0; g < 4; ++g) {
-                muA[kk] += ic.Ainv[g][kk] * bS[g];
-                muX[kk] += ic.Binv[g][kk] * bX[g];
-                muY[kk] += ic.Binv[g][kk] * bY[g];
+                muA[kk] += (T)ic.Ainv[g][kk] * bS[g];
+                muX[kk] += (T)ic.Binv[g][kk] * bX[g];
+                muY[kk] += (T)ic.Binv[g][kk] * bY[g];
             }
         }
         muY[3] = -muY[3];  // the m13 row of the y block is negated
-        const double mu6 = ic.C1inv[0][0] * bQ[0] + ic.C1inv[1][0] * bQ[1];
-        const double mu16 = ic.C1inv[0][1] * bQ[0] + ic.C1inv[1][1] * bQ[1];
-        const double mu7 = ic.C2inv[0][0] * bQ[2] + ic.C2inv[1][0] * bQ[3];
-        const double mu15 = ic.C2inv[0][1] * bQ[2] + ic.C2inv[1][1] * bQ[3];
+        const T mu6 = (T)ic.C1inv[0][0] * bQ[0] + (T)ic.C1inv[1][0] * bQ[1];
+        const T mu16 = (T)ic.C1inv[0][1] * bQ[0] + (T)ic.C1inv[1][1] * bQ[1];
+        const T mu7 = (T)ic.C2inv[0][0] * bQ[2] + (T)ic.C2inv[1][0] * bQ[3];
+        const T mu15 = (T)ic.C2inv[0][1] * bQ[2] + (T)ic.C2inv[1][1] * bQ[3];
         // (m1, m4, m5, m14) = muA, (m2, m8, m10, m12) = muX, (m3, m9, m11, m13) = muY
-        const double nu[12] = {muA[2], mu6, mu7, muX[1], muY[1], muX[2], muY[2], muX[3], muY[3], muA[3], mu15, mu16};
-        const double r = rho[c], u = ux[c], v = uy[c], t = Tf[c];
-        const double b = ic.b;
-        const double jx = r * u, jy = r * v, e = b * r * t + r * (u * u + v * v);
-        double a_r, a_jx, a_jy, a_e;
-        adj_equilibrium<double>(r, jx, jy, e, kd, nu, a_r, a_jx, a_jy, a_e);
-        const double mb1 = muA[0] + a_r, mb2 = muX[0] + a_jx, mb3 = muY[0] + a_jy, mb4 = muA[1] + a_e;
-        g_rho[c] = mb1 + mb2 * u + mb3 * v + mb4 * (b * t + u * u + v * v);
-        g_ux[c] = mb2 * r + mb4 * 2.0 * r * u;
-        g_uy[c] = mb3 * r + mb4 * 2.0 * r * v;
-        g_T[c] = mb4 * b * r;
+        const T nu[12] = {muA[2], mu6, mu7, muX[1], muY[1], muX[2], muY[2], muX[3], muY[3], muA[3], mu15, mu16};
+        const T r = (T)rho[c], u = (T)ux[c], v = (T)uy[c], t = (T)Tf[c];
+        const T b = (T)ic.b;
+        const T jx = r * u, jy = r * v, e = b * r * t + r * (u * u + v * v);
+        T a_r, a_jx, a_jy, a_e;
+        adj_equilibrium<T>(r, jx, jy, e, kc, nu, a_r, a_jx, a_jy, a_e);
+        const T mb1 = muA[0] + a_r, mb2 = muX[0] + a_jx, mb3 = muY[0] + a_jy, mb4 = muA[1] + a_e;
+        g_rho[c] = (double)(mb1 + mb2 * u + mb3 * v + mb4 * (b * t + u * u + v * v));
+        g_ux[c] = (double)(mb2 * r + (T)2 * mb4 * r * u);
+        g_uy[c] = (double)(mb3 * r + (T)2 * mb4 * r * v);
+        g_T[c] = (double)(mb4 * b * r);
     }
 }
 
@@ -425,10 +427,10 @@ cudaError_t launch_ghost_adjoint(const Layout& L, int fix_x, int fix_y, const do
 }
 
 template <class T>
-cudaError_t launch_init_adjoint(const Layout& L, const InitCoef& ic, const Coef<double>& kd, const T* lam,
+cudaError_t launch_init_adjoint(const Layout& L, const InitCoef& ic, const Coef<T>& kc, const T* lam,
                                 const double* rho, const double* ux, const double* uy, const double* Tf,
                                 double* g_rho, double* g_ux, double* g_uy, double* g_T, cudaStream_t st) {
-    init_adjoint_kernel<T><<<blocks_for((long)L.nx * L.ny, 256), 256, 0, st>>>(L, ic, kd, lam, rho, ux, uy, Tf,
+    init_adjoint_kernel<T><<<blocks_for((long)L.nx * L.ny, 256), 256, 0, st>>>(L, ic, kc, lam, rho, ux, uy, Tf,
                                                                               g_rho, g_ux, g_uy, g_T);
     return cudaGetLastError();
 }
@@ -463,7 +465,7 @@ cudaError_t launch_sum_partials(const double* gpart, int nparts, double* out, cu
     template cudaError_t launch_lam_from_drho<T>(const Layout&, const double*, T*, cudaStream_t);               \
     template cudaError_t launch_ghost_adjoint<T>(const Layout&, int, int, const double*, const double*, T*,     \
                                                  cudaStream_t);                                                 \
-    template cudaError_t launch_init_adjoint<T>(const Layout&, const InitCoef&, const Coef<double>&, const T*,  \
+    template cudaError_t launch_init_adjoint<T>(const Layout&, const InitCoef&, const Coef<T>&, const T*,       \
                                                 const double*, const double*, const double*, const double*,     \
                                                 double*, double*, double*, double*, cudaStream_t);
 INST(float)

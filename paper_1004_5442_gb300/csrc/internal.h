@@ -143,7 +143,7 @@ template <class T>
 cudaError_t launch_ghost_adjoint(const Layout& L, int fix_x, int fix_y, const double* gxb, const double* gyb,
                                  T* lam, cudaStream_t st);
 template <class T>
-cudaError_t launch_init_adjoint(const Layout& L, const InitCoef& ic, const Coef<double>& kd, const T* lam,
+cudaError_t launch_init_adjoint(const Layout& L, const InitCoef& ic, const Coef<T>& kc, const T* lam,
                                 const double* rho, const double* ux, const double* uy, const double* Tf,
                                 double* g_rho, double* g_ux, double* g_uy, double* g_T, cudaStream_t st);
 cudaError_t launch_sum_partials(const double* gpart, int nparts, double* out, cudaStream_t st);
