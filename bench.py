@@ -354,7 +354,7 @@ def run_ours(args):
 
     # the paper's tube and 2-D problems: throughput next to error vs exact
     if not args.no_problems:
-        line["paper_problems"] = paper_problems(Bd, W, torch, stream)
+        line["paper_problems"] = paper_problems(Bd, W, torch, stream, peak)
 
     # 256 independent tube/ripple instances of uneven size, one launch per step
     if not args.no_batch:
@@ -386,8 +386,12 @@ def run_ours(args):
 
     if rank == 0 and world == 1 and not args.no_cpu:
         rate, cores, sample = cpu_oracle_rate(w)
+        import oracle
+        oracle.set_threads(1)
+        rate1, _, sample1 = cpu_oracle_rate(w, budget_s=4.0, rows=64)
+        oracle.set_threads(cores)
         line["cpu_baseline"] = {"value": rate, "unit": "cell-updates/s", "cores": cores, "kind": "oracle",
-                                "sample": sample}
+                                "sample": sample, "one_core": {"value": rate1, "sample": sample1}}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -444,7 +448,7 @@ def _shock_x(rho, dx, behind, ahead):
     return x
 
 
-def paper_problems(Bd, W, torch, stream):
+def paper_problems(Bd, W, torch, stream, peak):
     """Sod (400 x 4, FP64), strong shock (2048 x 8, FP32 and FP64), colliding
     shocks (1300 x 4, gamma 7/5, MRT and SRT rates, FP64, t = 0.13), the
     Richtmyer-Meshkov run (360 x 100, reflecting wall, t = 0.104) and the
@@ -469,6 +473,11 @@ def paper_problems(Bd, W, torch, stream):
     cases = [("sod_400x4", W.sod_tube(), (Bd.FP64,)), ("strong_shock_2048x8", W.strong_shock(), (Bd.FP32, Bd.FP64)),
              ("colliding_shocks_gamma1.4", W.colliding_shocks(gamma=1.4), (Bd.FP64,)),
              ("colliding_shocks_gamma1.4_srt", W.colliding_shocks(gamma=1.4, mrt=False), (Bd.FP64,))]
+    def hbm(prec, rate):
+        # algorithmic bytes (16 reads + 16 writes per cell-update) per second
+        # over the measured copy peak
+        return (BYTES_PER_CELL_F64 if prec == Bd.FP64 else BYTES_PER_CELL_F32) * rate / 1e9 / peak
+
     for name, w, precs in cases:
         ex = exact[name.replace("_srt", "")]
         rho_ex = np.asarray(ex["rho"])
@@ -478,7 +487,8 @@ def paper_problems(Bd, W, torch, stream):
             r = g.macro()[0][0]
             t1 = g.totals()
             g.close()
-            d = {"steps": w.nsteps, "ms": ms, "cell_updates_per_s": w.cells * w.nsteps / (ms * 1e-3),
+            rate = w.cells * w.nsteps / (ms * 1e-3)
+            d = {"steps": w.nsteps, "ms": ms, "cell_updates_per_s": rate, "hbm_frac": hbm(prec, rate),
                  "healthy": ok, "l1_rho_vs_exact": float(np.mean(np.abs(r - rho_ex))),
                  "tv_excess": float(np.sum(np.abs(np.diff(r))) - np.sum(np.abs(np.diff(rho_ex))))}
             if not name.startswith("colliding"):
@@ -496,18 +506,20 @@ def paper_problems(Bd, W, torch, stream):
             break
         g.step(100)
     g.close()
-    w = W.richtmyer_meshkov()
+    wr = W.richtmyer_meshkov()
     for prec in (Bd.FP32, Bd.FP64):
-        g, ms_rm, _ = timed(w, prec, w.nsteps)
+        g, ms_rm, _ = timed(wr, prec, wr.nsteps)
         ok = g.health() == Bd.MRT_OK
         r = g.macro()[0]
         g.close()
+        rate = wr.cells * wr.nsteps / (ms_rm * 1e-3)
         out[f"richtmyer_meshkov_360x100_{'fp64' if prec == Bd.FP64 else 'fp32'}"] = {
-            "steps": w.nsteps, "ms": ms_rm, "cell_updates_per_s": w.cells * w.nsteps / (ms_rm * 1e-3),
+            "steps": wr.nsteps, "ms": ms_rm, "cell_updates_per_s": rate, "hbm_frac": hbm(prec, rate),
             "healthy": ok, "y_symmetry_max_rel": float(np.max(np.abs(r - r[::-1])) / np.max(r)),
             "rho_range": [float(r.min()), float(r.max())]}
     out["four_quadrant_500x500_fp32"] = {"steps": 1000, "ms": ms,
                                          "cell_updates_per_s": w.cells * 1000 / (ms * 1e-3),
+                                         "hbm_frac": hbm(Bd.FP32, w.cells * 1000 / (ms * 1e-3)),
                                          "health_flag_by_step": flagged,
                                          "note": "positivity of P is lost near step 1400 under forward Euler"}
     return out
