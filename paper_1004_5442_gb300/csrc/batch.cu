@@ -7,14 +7,14 @@
 //   - a __constant__ table of the instances' step constants (the
 //     relaxation rates, b, and Lax-Wendroff weights differ per instance),
 //   - a device table of instance descriptors and their tensor maps,
-//   - a work list (instance x strip x chunk of rows, longest first) that one
-//     wave of resident CTAs takes items from through an atomic counter.
+//   - a work list (instance x strip x chunk of rows; longest first, then
+//     instance by instance and row band by row band) that one wave of
+//     resident CTAs takes items from through an atomic counter.
 // Kernel boundaries order the steps, so no device-side grid barrier exists.
 #include <algorithm>
 #include <cstring>
 #include <mutex>
 #include <new>
-#include <numeric>
 #include <vector>
 
 #include "internal.h"
