@@ -320,3 +320,30 @@ def test_reflecting_wall_resume_and_rejections():
     with pytest.raises(Bd.MrtError) as ei:
         Bd.Batch([w])
     assert ei.value.code == Bd.MRT_EINVAL
+
+
+def test_grids_on_concurrent_streams():
+    """Two grids stepped with interleaved launches on their own streams
+    (each with its own work-queue counters) give the same states, bit for
+    bit, as each stepped alone."""
+    import torch
+    wa = W.kelvin_helmholtz(n=2048, nsteps=0, seed=1)
+    wb = W.random_smooth(700, 300, seed=2, amp=0.1)
+    alone = []
+    for w, prec in ((wa, Bd.FP32), (wb, Bd.FP64)):
+        with Bd.Grid.from_workload(w, precision=prec) as g:
+            g.step(9)
+            alone.append(g.get_f())
+    sa, sb = torch.cuda.Stream(), torch.cuda.Stream()
+    ga = Bd.Grid.from_workload(wa, precision=Bd.FP32, stream=sa.cuda_stream)
+    gb = Bd.Grid.from_workload(wb, precision=Bd.FP64, stream=sb.cuda_stream)
+    try:
+        assert ga.info()["tile"] == 6
+        for _ in range(3):
+            ga.step(3)
+            gb.step(3)
+        np.testing.assert_array_equal(ga.get_f(), alone[0])
+        np.testing.assert_array_equal(gb.get_f(), alone[1])
+    finally:
+        ga.close()
+        gb.close()
