@@ -37,7 +37,8 @@ def _mixed(count=10, seed=21):
     for k in range(count - count // 2):
         nx = [130, 257, 300, 384, 95][k % 5]
         ny = [9, 40, 5, 17, 64][k % 5]
-        out.append(W.random_smooth(nx, ny, seed=seed + k, amp=0.05, bc_x=k % 2, bc_y=(k // 2) % 2))
+        bc = [(0, 0), (1, 0), (0, 1), (2, 0), (1, 2)][k % 5]   # 2: reflecting wall + inflow
+        out.append(W.random_smooth(nx, ny, seed=seed + k, amp=0.05, bc_x=bc[0], bc_y=bc[1]))
     return out
 
 

@@ -303,7 +303,7 @@ def test_reflecting_wall_parity(bcy):
 
 def test_reflecting_wall_resume_and_rejections():
     """mrt_set_f refreshes the wall's ghost from the new state (resume is bit
-    identical); batches and the reverse mode reject the wall."""
+    identical); the reverse mode rejects the wall."""
     w = W.random_smooth(140, 21, seed=4, amp=0.1, bc_x=Bd.BC_REFLECT_FIXED, bc_y=Bd.BC_REFLECT_FIXED, nsteps=0)
     with Bd.Grid.from_workload(w, precision=Bd.FP32) as a:
         a.step(5)
@@ -317,9 +317,6 @@ def test_reflecting_wall_resume_and_rejections():
         with pytest.raises(Bd.MrtError) as ei:
             a.adjoint_record(w.rho, w.ux, w.uy, w.T, 3, 1)
         assert ei.value.code == Bd.MRT_EINVAL
-    with pytest.raises(Bd.MrtError) as ei:
-        Bd.Batch([w])
-    assert ei.value.code == Bd.MRT_EINVAL
 
 
 def test_grids_on_concurrent_streams():
