@@ -221,8 +221,6 @@ def feq_moments_via_cplx(rho, jx, jy, e, b) -> np.ndarray:
 def step_adjoint(g: Grid, f: np.ndarray, lam_next: np.ndarray, gxb: np.ndarray, gyb: np.ndarray,
                  gs: np.ndarray) -> np.ndarray:
     """dL/df^n from f^n and dL/df^{n+1}; accumulates ghost and rate adjoints."""
-    if BC_REFLECT_FIXED in (g.bc_x, g.bc_y):
-        raise ValueError("the reverse mode covers periodic and fixed-equilibrium boundaries only")
     f = np.ascontiguousarray(f, dtype=np.float64)
     lam_next = np.ascontiguousarray(lam_next, dtype=np.float64)
     out = np.zeros_like(f)

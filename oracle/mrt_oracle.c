@@ -492,8 +492,9 @@ void orc_feq_moments_via_cplx(double rho, double jx, double jy, double e, double
     for (int k = 0; k < NV; ++k) out[k] = creal(o[k]);
 }
 
-/* Add w * lam at (x, y) of plane i to the adjoint of the cell read there:
- * a domain cell, a wrapped cell on a periodic axis, or a fixed ghost whose
+/* Add w * lam at (x, y) of plane i to the adjoint of the cell read there
+ * (the transpose of fat): a domain cell, a wrapped cell on a periodic axis,
+ * the mirrored domain cell behind a reflecting wall, or a fixed ghost whose
  * adjoint is accumulated in gxb / gyb (same layout as gx / gy). */
 static void scatter(const orc_cfg *c, double *lam, double *gxb, double *gyb, int i, int x, int y,
                     double v)
@@ -503,6 +504,9 @@ static void scatter(const orc_cfg *c, double *lam, double *gxb, double *gyb, int
     if (x < 0 || x >= nx) {
         if (c->bc_x == ORC_BC_PERIODIC) {
             x = (x + nx) % nx;
+        } else if (c->bc_x == ORC_BC_REFLECT_FIXED && x < 0) {
+            lam[(size_t)mirror_index(i, 0) * n + (size_t)y * nx + 0] += v;
+            return;
         } else {
             const int side = (x < 0) ? 0 : 1;
             gxb[((size_t)i * 2 + side) * ny + y] += v;
@@ -512,6 +516,9 @@ static void scatter(const orc_cfg *c, double *lam, double *gxb, double *gyb, int
     if (y < 0 || y >= ny) {
         if (c->bc_y == ORC_BC_PERIODIC) {
             y = (y + ny) % ny;
+        } else if (c->bc_y == ORC_BC_REFLECT_FIXED && y < 0) {
+            lam[(size_t)mirror_index(i, 1) * n + 0 * (size_t)nx + x] += v;
+            return;
         } else {
             const int side = (y < 0) ? 0 : 1;
             gyb[((size_t)i * 2 + side) * nx + x] += v;
@@ -629,12 +636,14 @@ void orc_ghosts_adjoint(int nx, int ny, int bc_x, int bc_y, const double *gxb, c
 {
     const size_t n = (size_t)nx * (size_t)ny;
     for (int i = 0; i < NV; ++i) {
-        if (bc_x == ORC_BC_FIXED_EQ)
+        /* fixed ghosts hold the initial f of the adjacent cell (behind a
+         * reflecting wall nothing is accumulated: gxb / gyb stay 0 there) */
+        if (bc_x == ORC_BC_FIXED_EQ || bc_x == ORC_BC_REFLECT_FIXED)
             for (int y = 0; y < ny; ++y) {
                 lam0[(size_t)i * n + (size_t)y * nx + 0] += gxb[((size_t)i * 2 + 0) * ny + y];
                 lam0[(size_t)i * n + (size_t)y * nx + (nx - 1)] += gxb[((size_t)i * 2 + 1) * ny + y];
             }
-        if (bc_y == ORC_BC_FIXED_EQ)
+        if (bc_y == ORC_BC_FIXED_EQ || bc_y == ORC_BC_REFLECT_FIXED)
             for (int x = 0; x < nx; ++x) {
                 lam0[(size_t)i * n + 0 * (size_t)nx + x] += gyb[((size_t)i * 2 + 0) * nx + x];
                 lam0[(size_t)i * n + (size_t)(ny - 1) * nx + x] += gyb[((size_t)i * 2 + 1) * nx + x];

@@ -32,7 +32,7 @@ def test_feq_jacobian_complex_step(orc):
     np.testing.assert_array_equal(J[:4], np.eye(4))
 
 
-@pytest.mark.parametrize("bcx,bcy", [(0, 0), (1, 0), (1, 1)])
+@pytest.mark.parametrize("bcx,bcy", [(0, 0), (1, 0), (1, 1), (2, 0), (2, 2), (1, 2)])
 def test_step_transpose_dot_product(orc, bcx, bcy):
     w = W.random_smooth(9, 7, seed=2, amp=0.1, bc_x=bcx, bc_y=bcy)
     g = orc.create(w.nx, w.ny, w.dx, w.dt, w.b, w.s, w.rho, w.ux, w.uy, w.T, w.bc_x, w.bc_y)
@@ -47,8 +47,11 @@ def test_step_transpose_dot_product(orc, bcx, bcy):
     lhs = np.sum(lam * tangent)
     rhs = np.sum(adj * d)
     assert abs(lhs - rhs) <= 1e-8 * np.sum(np.abs(lam * tangent))
-    # ghost adjoint against a perturbation of the ghost values
-    if bcx == 1:
+    # ghost adjoint against a perturbation of the ghost values (the
+    # reflecting wall's ghost is not a free value: its adjoint goes to the
+    # mirrored cell, covered by the dot product above; the inflow end of a
+    # walled axis is a fixed ghost like the others)
+    if bcx in (1, 2):
         dg = rng.standard_normal(g.gx.shape)
         gp, gm = g.gx + h * dg, g.gx - h * dg
         g.gx = gp
@@ -57,6 +60,8 @@ def test_step_transpose_dot_product(orc, bcx, bcy):
         fm = orc.step(g, f)
         t = np.sum(lam * (fp - fm) / (2 * h))
         assert abs(t - np.sum(gxb * dg)) <= 1e-8 * max(abs(t), 1e-300) + 1e-12
+        if bcx == 2:
+            assert np.all(gxb[:, 0, :] == 0.0)
 
 
 def _loss(target, dx):
@@ -66,14 +71,19 @@ def _loss(target, dx):
     return lg
 
 
-@pytest.mark.parametrize("case", ["vortex", "tube"])
+@pytest.mark.parametrize("case", ["vortex", "tube", "wall"])
 def test_adjoint_matches_finite_differences(orc, case):
     if case == "vortex":
         w = W.smooth_vortex(n=20, nsteps=24, r0=0.15)
         target = W.vortex_target(w)
-    else:
+    elif case == "tube":
         w = W.sod_tube(nx=40, ny=3, nsteps=30)
         target = w.rho * 0.97 + 0.01
+    else:
+        # reflecting wall on the left, inflow on the right, wall in y too
+        w = W.random_smooth(20, 9, seed=31, amp=0.1, bc_x=orc.BC_REFLECT_FIXED, bc_y=orc.BC_REFLECT_FIXED,
+                            nsteps=24)
+        target = w.rho * 0.98 + 0.02
     lg = _loss(target, w.dx)
     args = (w.nx, w.ny, w.dx, w.dt, w.b)
     L, gr, gu, gv, gT, gs = orc.adjoint_run(*args, w.s, w.rho, w.ux, w.uy, w.T, w.nsteps, lg,

@@ -56,10 +56,3 @@ def test_wall_is_impermeable(orc):
     m0 = orc.totals(g)[0]
     orc.run(g, 5)      # disturbances have not reached the high end yet
     assert abs(orc.totals(g)[0] - m0) <= 1e-13 * m0
-
-
-def test_reverse_mode_rejects_wall(orc):
-    w = W.random_smooth(16, 5, seed=1, amp=0.05, nsteps=0)
-    g = orc.create(16, 5, w.dx, w.dt, w.b, w.s, w.rho, w.ux, w.uy, w.T, orc.BC_REFLECT_FIXED, orc.BC_PERIODIC)
-    with pytest.raises(ValueError):
-        orc.step_adjoint(g, g.f, g.f, np.zeros_like(g.gx), np.zeros_like(g.gy), np.zeros(16))
