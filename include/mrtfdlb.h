@@ -59,8 +59,7 @@ typedef enum mrt_precision { MRT_FP32 = 0, MRT_FP64 = 1 } mrt_precision;
  * end (Sect. (d): the normal velocity is the reverse of the one at the
  * mirror-image interior point) - its ghost holds, at every step, the
  * adjacent cell's f with each velocity mirrored across the wall - and a
- * fixed-equilibrium inflow at the high end.  The reverse mode accepts
- * periodic and fixed-equilibrium axes only. */
+ * fixed-equilibrium inflow at the high end. */
 typedef enum mrt_bc { MRT_BC_PERIODIC = 0, MRT_BC_FIXED_EQ = 1, MRT_BC_REFLECT_FIXED = 2 } mrt_bc;
 
 /* Step kernel selection: MRT_KERNEL_TMA is the TMA-staged strip kernel,

@@ -32,6 +32,13 @@ __device__ __forceinline__ void store_plain(T* __restrict__ out, const Layout& L
             for (int i = 0; i < NV; ++i) out[i * L.plane + (long)(L.ny + 1) * L.pitch + col] = v[i];
         if (per_y && y == L.ny - 1)
             for (int i = 0; i < NV; ++i) out[i * L.plane + col] = v[i];
+        // behind a reflecting wall: the mirrored cell (the adjoint of reading
+        // a mirrored ghost is a mirrored ghost of the adjoint, because the
+        // +x weight of a velocity is the -x weight of its mirror image)
+        if (L.refl_x && x == 0)
+            for (int i = 0; i < NV; ++i) out[i * L.plane + row + L.G - 1] = v[mirror_plane(i, 0)];
+        if (L.refl_y && y == 0)
+            for (int i = 0; i < NV; ++i) out[i * L.plane + col] = v[mirror_plane(i, 1)];
     }
 }
 
@@ -64,14 +71,14 @@ __global__ void __launch_bounds__(ABX* ABY) adjoint_step_kernel(AdjArgs<T> a) {
         store_plain<T, true>(a.lam_out, L, a.per_x, a.per_y, x, y, out);
         // a fixed ghost beyond an edge cell received the forward weight of
         // that neighbour position; accumulate its adjoint (one writer each)
-        if (!a.per_x && (x == 0 || x == L.nx - 1)) {
+        if (!a.per_x && ((x == 0 && !L.refl_x) || x == L.nx - 1)) {
             const int side = x == 0 ? 0 : 1;
             for (int i = 0; i < NV; ++i) {
                 const T wgt = lw_weight<T>(a.k, i, side == 0 ? XM : XP);
                 a.gxb[((long)i * 2 + side) * L.ny + y] += (double)(wgt * LF(i, C));
             }
         }
-        if (!a.per_y && (y == 0 || y == L.ny - 1)) {
+        if (!a.per_y && ((y == 0 && !L.refl_y) || y == L.ny - 1)) {
             const int side = y == 0 ? 0 : 1;
             for (int i = 0; i < NV; ++i) {
                 const T wgt = lw_weight<T>(a.k, i, side == 0 ? YM : YP);
@@ -218,12 +225,12 @@ __global__ void __launch_bounds__(TMA_W) adjoint_tma_kernel(const __grid_constan
             cell_adjoint<T>(LF, f, a.k, out, gs);
 #pragma unroll
             for (int i = 0; i < NV; ++i) ob[i * TMA_W + tid] = out[i];
-            if (!a.per_x && (x == 0 || x == L.nx - 1)) {
+            if (!a.per_x && ((x == 0 && !L.refl_x) || x == L.nx - 1)) {
                 const int side = x == 0 ? 0 : 1;
                 for (int i = 0; i < NV; ++i)
                     a.gxb[((long)i * 2 + side) * L.ny + y] += (double)(lw_weight<T>(a.k, i, side == 0 ? XM : XP) * LF(i, C));
             }
-            if (!a.per_y && (y == 0 || y == L.ny - 1)) {
+            if (!a.per_y && ((y == 0 && !L.refl_y) || y == L.ny - 1)) {
                 const int side = y == 0 ? 0 : 1;
                 for (int i = 0; i < NV; ++i)
                     a.gyb[((long)i * 2 + side) * L.nx + x] += (double)(lw_weight<T>(a.k, i, side == 0 ? YM : YP) * LF(i, C));
@@ -259,6 +266,16 @@ __global__ void __launch_bounds__(TMA_W) adjoint_tma_kernel(const __grid_constan
             const long gc = (long)(y + 1) * L.pitch + (x == 0 ? L.G + L.nx : L.G - 1);
 #pragma unroll 4
             for (int i = 0; i < NV; ++i) a.lam_out[i * L.plane + gc] = ob[i * TMA_W + tid];
+        }
+        if (L.refl_x && x == 0) {
+            // reflecting wall: the mirrored cell behind it (see store_plain)
+            const long gc = (long)(y + 1) * L.pitch + L.G - 1;
+#pragma unroll 4
+            for (int i = 0; i < NV; ++i) a.lam_out[i * L.plane + gc] = ob[mirror_plane(i, 0) * TMA_W + tid];
+        }
+        if (L.refl_y && y == 0 && active) {
+#pragma unroll 4
+            for (int i = 0; i < NV; ++i) a.lam_out[i * L.plane + L.G + x] = ob[mirror_plane(i, 1) * TMA_W + tid];
         }
     }
     if (tid == 0) bulk_wait_all();

@@ -29,7 +29,7 @@ def _rel(a, b):
 
 
 @pytest.mark.parametrize("prec,tol", [(Bd.FP64, 1e-12), (Bd.FP32, 2e-5)])
-@pytest.mark.parametrize("bcx,bcy", [(0, 0), (1, 0), (1, 1)])
+@pytest.mark.parametrize("bcx,bcy", [(0, 0), (1, 0), (1, 1), (2, 0), (2, 2)])
 def test_adjoint_step_matches_oracle(prec, tol, bcx, bcy):
     w = W.random_smooth(140, 21, seed=8, amp=0.1, bc_x=bcx, bc_y=bcy)
     g = oracle.create(w.nx, w.ny, w.dx, w.dt, w.b, w.s, w.rho, w.ux, w.uy, w.T, w.bc_x, w.bc_y)
@@ -65,14 +65,19 @@ def _gpu_grads(w, prec, nsteps, ckpt, lg, kernel=Bd.KERNEL_AUTO, dL=None):
     return L, out
 
 
-@pytest.mark.parametrize("case", ["vortex", "tube"])
+@pytest.mark.parametrize("case", ["vortex", "tube", "wall"])
 def test_adjoint_run_matches_oracle(case):
     if case == "vortex":
         w = W.smooth_vortex(n=40, nsteps=30, r0=0.15)
         target = W.vortex_target(w)
-    else:
+    elif case == "tube":
         w = W.sod_tube(nx=150, ny=5, nsteps=30)
         target = w.rho * 0.97 + 0.01
+    else:
+        # reflecting walls at the low ends of both axes, inflow at the high ends
+        w = W.random_smooth(150, 37, seed=31, amp=0.1, bc_x=Bd.BC_REFLECT_FIXED, bc_y=Bd.BC_REFLECT_FIXED,
+                            nsteps=30)
+        target = w.rho * 0.98 + 0.02
     lg = _loss(target, w.dx)
     ref = oracle.adjoint_run(w.nx, w.ny, w.dx, w.dt, w.b, w.s, w.rho, w.ux, w.uy, w.T, w.nsteps, lg,
                              w.bc_x, w.bc_y, ckpt=7)
