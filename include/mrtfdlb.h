@@ -244,6 +244,20 @@ mrt_status mrt_batch_sync(mrt_batch *b);
 mrt_status mrt_batch_stream(const mrt_batch *b, void **stream);
 void mrt_batch_destroy(mrt_batch *b);
 
+/* Diagnostics of the library itself (no counterpart in the paper).
+ *
+ * mrt_debug_padding: *nonzero = the number of nonzero words in the columns
+ * of the grid's two padded buffers that no kernel may write (left of the
+ * left ghost column, right of the right one; zero from creation on): a guard
+ * band that counts out-of-bounds writes.  Synchronises the grid's stream.
+ * mrt_debug_wait_timeout: launches one thread that waits, with the bounded
+ * wait of the TMA kernels, on a barrier nothing completes; after the wait's
+ * 2 s limit the grid's timeout flag is set, so the next mrt_health returns
+ * MRT_ETIMEOUT (the grid stays flagged).  Asynchronous on the grid's stream.
+ * Errors: MRT_EINVAL (null pointers), MRT_ENOMEM, MRT_ECUDA. */
+mrt_status mrt_debug_padding(mrt_grid *g, long *nonzero);
+mrt_status mrt_debug_wait_timeout(mrt_grid *g);
+
 /* Release every device resource of the grid (synchronises its stream). */
 void mrt_destroy(mrt_grid *g);
 

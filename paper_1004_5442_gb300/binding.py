@@ -27,7 +27,7 @@ EXPORTED = ["mrt_create", "mrt_step", "mrt_get_macro", "mrt_conserved_totals", "
             "mrt_last_error", "mrt_conserved_totals_static", "mrt_adjoint_record",
             "mrt_adjoint_backward", "mrt_adjoint_step", "mrt_batch_create", "mrt_batch_step",
             "mrt_batch_tune", "mrt_batch_grid", "mrt_batch_info", "mrt_batch_sync", "mrt_batch_stream",
-            "mrt_batch_destroy"]
+            "mrt_batch_destroy", "mrt_debug_padding", "mrt_debug_wait_timeout"]
 
 
 class MrtError(RuntimeError):
@@ -87,13 +87,15 @@ def load(path: str = LIB_PATH):
     L.mrt_batch_info.argtypes = [vp, ipp, ipp, ipp, ipp, ipp]
     L.mrt_batch_sync.argtypes = [vp]
     L.mrt_batch_stream.argtypes = [vp, ctypes.POINTER(vp)]
+    L.mrt_debug_padding.argtypes = [vp, ctypes.POINTER(ctypes.c_long)]
+    L.mrt_debug_wait_timeout.argtypes = [vp]
     L.mrt_batch_destroy.argtypes = [vp]
     L.mrt_batch_destroy.restype = None
     for name in ("mrt_create", "mrt_step", "mrt_get_macro", "mrt_conserved_totals", "mrt_get_f",
                  "mrt_set_f", "mrt_health", "mrt_info", "mrt_conserved_totals_static",
                  "mrt_adjoint_record", "mrt_adjoint_backward", "mrt_adjoint_step", "mrt_batch_create",
                  "mrt_batch_step", "mrt_batch_tune", "mrt_batch_grid", "mrt_batch_info", "mrt_batch_sync",
-                 "mrt_batch_stream"):
+                 "mrt_batch_stream", "mrt_debug_padding", "mrt_debug_wait_timeout"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -248,6 +250,16 @@ class Grid:
 
     def health(self) -> int:
         return int(load().mrt_health(self._h))
+
+    def debug_padding(self) -> int:
+        """Nonzero words in the never-written padding columns (0 = no stray writes)."""
+        n = ctypes.c_long()
+        check(load().mrt_debug_padding(self._h, ctypes.byref(n)))
+        return n.value
+
+    def debug_wait_timeout(self) -> None:
+        """Let a bounded device wait run out; mrt_health then reports MRT_ETIMEOUT."""
+        check(load().mrt_debug_wait_timeout(self._h))
 
     def info(self) -> dict:
         steps, pitch, plane = ctypes.c_long(), ctypes.c_long(), ctypes.c_long()

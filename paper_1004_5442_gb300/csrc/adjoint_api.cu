@@ -45,6 +45,7 @@ static char* buf_at(void* base, size_t bytes, long i) { return static_cast<char*
 
 extern "C" mrt_status mrt_adjoint_record(mrt_grid* g, const double* rho0, const double* ux0, const double* uy0,
                                          const double* T0, int on_device, long nsteps, int ckpt_every) {
+    NvtxRange range("mrt_adjoint_record");
     if (!g) return mrt_fail(MRT_EINVAL, "grid is NULL");
     if (nsteps < 1) return mrt_fail(MRT_EINVAL, "nsteps must be >= 1");
     if (ckpt_every < 1) return mrt_fail(MRT_EINVAL, "ckpt_every must be >= 1");
@@ -209,6 +210,7 @@ static mrt_status backward_impl(mrt_grid* g, const double* drho, double* outs[4]
 
 extern "C" mrt_status mrt_adjoint_backward(mrt_grid* g, const double* dL_drhoN, int on_device, double* g_rho0,
                                            double* g_ux0, double* g_uy0, double* g_T0, double g_s[16]) {
+    NvtxRange range("mrt_adjoint_backward");
     if (!g) return mrt_fail(MRT_EINVAL, "grid is NULL");
     if (!g->tape) return mrt_fail(MRT_EINVAL, "no recorded run: call mrt_adjoint_record first");
     if (!dL_drhoN) return mrt_fail(MRT_EINVAL, "dL_drhoN is NULL");

@@ -510,6 +510,7 @@ static mrt_status do_init(mrt_grid* g, const double* rho, const double* ux, cons
 extern "C" mrt_status mrt_create(const mrt_params* params, const double* rho, const double* ux,
                                  const double* uy, const double* T, int fields_on_device,
                                  void* stream, mrt_grid** out) {
+    NvtxRange range("mrt_create");
     mrt_status st = validate(params);
     if (st != MRT_OK) return st;
     if (!out || !rho || !ux || !uy || !T) return fail(MRT_EINVAL, "null pointer argument");
@@ -748,6 +749,7 @@ static mrt_status step_impl(mrt_grid* g, long nsteps) {
 }
 
 extern "C" mrt_status mrt_step(mrt_grid* g, long nsteps) {
+    NvtxRange range("mrt_step");
     if (!g) return fail(MRT_EINVAL, "grid is NULL");
     if (nsteps < 0) return fail(MRT_EINVAL, "nsteps must be >= 0");
     if (nsteps == 0) return MRT_OK;

@@ -299,6 +299,7 @@ extern "C" mrt_status mrt_batch_create(int n, const mrt_params* params, const do
 }
 
 extern "C" mrt_status mrt_batch_step(mrt_batch* b, long nsteps) {
+    NvtxRange range("mrt_batch_step");
     if (!b) return mrt_fail(MRT_EINVAL, "batch is NULL");
     if (nsteps < 0) return mrt_fail(MRT_EINVAL, "nsteps must be >= 0");
     long done = 0;

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include "../../include/mrtfdlb.h"
+#include <nvtx3/nvToolsExt.h>
 #include "model.cuh"
 
 namespace mrt {
@@ -22,6 +23,13 @@ struct Layout {
     long pitch;     // elements per row
     long plane;     // elements per plane = pitch * (ny + 2)
     int refl_x, refl_y;  // 1: reflecting wall at the low end of the axis (ghost refreshed every step)
+};
+
+// NVTX range over a host call (profilers show where the library's work
+// starts and ends; costs nothing without one attached).
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
 };
 
 // FP64 grids below this many cells (4 rows of 128 cells per SM) run the
