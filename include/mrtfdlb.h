@@ -180,9 +180,10 @@ mrt_status mrt_adjoint_step(mrt_grid *g, const void *f, const void *lam_next, vo
  * the caller on the device, computed without any allocation by the library.
  * The paper has no counterpart: this entry point exists for callers that
  * cannot allocate device memory at the moment they need the totals, such as
- * code running while a stream is captured into a CUDA graph, code inside a
- * framework that owns the device-memory budget through its own pool, or
- * monitoring loops that must never touch the allocator.
+ * code inside a framework that owns the device-memory budget through its own
+ * pool (an allocation behind its back can fail or break its accounting), or
+ * monitoring loops that must not stall on the allocator (cudaMalloc and
+ * cudaFree can synchronise the device).
  *   f       device pointer, dense [16][ny][nx] (the layout of mrt_get_f, not
  *           the grid's padded layout), float for MRT_FP32, double for
  *           MRT_FP64; read only.

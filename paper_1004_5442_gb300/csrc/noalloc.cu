@@ -3,10 +3,11 @@
 //
 // mrt_conserved_totals() keeps its block partials in memory that mrt_create()
 // allocated.  Some callers cannot allocate device memory when they need the
-// totals: code that runs while a stream is being captured into a CUDA graph,
-// code inside a framework whose memory is owned by its own pool or budget,
-// and monitoring loops that must not touch the allocator.  For them this
-// entry point keeps its scratch in a fixed array in the library's own device
+// totals: a host framework that owns the whole device-memory budget through
+// its own pool (a cudaMalloc behind its back can fail or break its
+// accounting), and monitoring loops that must not stall on the allocator
+// (cudaMalloc and cudaFree can synchronise the device).  For them this entry
+// point keeps its scratch in a fixed array in the library's own device
 // memory instead.
 //
 // The scratch array is a file-scope __device__ variable: every GPU that

@@ -1,8 +1,9 @@
 """mrt_conserved_totals_static: conserved totals of a caller-held device
 state with the scratch in a fixed array of the library instead of memory
 the library allocates.  It serves callers that cannot allocate device memory
-when they need the totals (during stream capture, under a framework that owns
-the memory budget, in allocation-free monitoring loops).  Its result is
+when they need the totals: a framework that owns the device-memory budget
+through its own pool, or a monitoring loop that must not stall on the
+allocator (cudaMalloc and cudaFree can synchronise the device).  Its result is
 checked against the grid entry point mrt_conserved_totals on the same state,
 on two calls in a row, with the tolerances of the other totals tests.
 
