@@ -26,6 +26,14 @@ _LIB = os.path.join(_BUILD, "liboracle.so")
 BC_PERIODIC = 0
 BC_FIXED_EQ = 1
 BC_REFLECT_FIXED = 2   # reflecting wall at the low end, fixed-equilibrium inflow at the high end
+# space discretisation: the paper's Lax-Wendroff operator axis by axis (ADV_LW),
+# the unsplit 2-D Lax-Wendroff operator with the mixed term (ADV_LW2D), or a
+# flux-limited variant (first-order upwind flux plus the Lax-Wendroff
+# correction scaled by a limiter; outside the paper)
+ADV_LW = 0
+ADV_LW2D = 1
+ADV_MINMOD = 2
+ADV_VANLEER = 3
 NV = 16
 
 
@@ -51,7 +59,7 @@ class _Cfg(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int),
                 ("dx", ctypes.c_double), ("dt", ctypes.c_double),
                 ("b", ctypes.c_double), ("s", ctypes.c_double * NV),
-                ("bc_x", ctypes.c_int), ("bc_y", ctypes.c_int)]
+                ("bc_x", ctypes.c_int), ("bc_y", ctypes.c_int), ("advection", ctypes.c_int)]
 
 
 _lib = None
@@ -77,7 +85,7 @@ def lib():
         L.orc_totals.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, dp, dp]
         L.orc_feq_jacobian.argtypes = [ctypes.c_double] * 5 + [dp]
         L.orc_feq_moments_via_cplx.argtypes = [ctypes.c_double] * 5 + [dp]
-        L.orc_step_adjoint.argtypes = [ctypes.POINTER(_Cfg), dp, dp, dp, dp, dp, dp]
+        L.orc_step_adjoint.argtypes = [ctypes.POINTER(_Cfg), dp, dp, dp, dp, dp, dp, dp, dp]
         L.orc_init_adjoint.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double] + [dp] * 9
         L.orc_ghosts_adjoint.argtypes = [ctypes.c_int] * 4 + [dp, dp, dp]
         L.orc_set_threads.argtypes = [ctypes.c_int]
@@ -144,6 +152,7 @@ class Grid:
     s: np.ndarray
     bc_x: int = BC_PERIODIC
     bc_y: int = BC_PERIODIC
+    advection: int = ADV_LW
     f: np.ndarray = field(default=None, repr=False)
     gx: np.ndarray = field(default=None, repr=False)
     gy: np.ndarray = field(default=None, repr=False)
@@ -154,13 +163,15 @@ class Grid:
         for k in range(NV):
             c.s[k] = float(self.s[k])
         c.bc_x, c.bc_y = int(self.bc_x), int(self.bc_y)
+        c.advection = int(self.advection)
         return c
 
 
-def create(nx, ny, dx, dt, b, s, rho, ux, uy, T, bc_x=BC_PERIODIC, bc_y=BC_PERIODIC) -> Grid:
+def create(nx, ny, dx, dt, b, s, rho, ux, uy, T, bc_x=BC_PERIODIC, bc_y=BC_PERIODIC,
+           advection=ADV_LW) -> Grid:
     """Initial state f = M^-1 fhat^eq(rho, u, T) and its fixed ghosts."""
     g = Grid(nx, ny, float(dx), float(dt), float(b), np.asarray(s, dtype=np.float64),
-             bc_x, bc_y)
+             bc_x, bc_y, int(advection))
     arr = [np.ascontiguousarray(np.broadcast_to(np.asarray(a, dtype=np.float64), (ny, nx)))
            for a in (rho, ux, uy, T)]
     g.f = np.zeros((NV, ny, nx))
@@ -225,12 +236,13 @@ def step_adjoint(g: Grid, f: np.ndarray, lam_next: np.ndarray, gxb: np.ndarray, 
     lam_next = np.ascontiguousarray(lam_next, dtype=np.float64)
     out = np.zeros_like(f)
     c = g.cfg()
-    lib().orc_step_adjoint(ctypes.byref(c), _p(f), _p(lam_next), _p(out), _p(gxb), _p(gyb), _p(gs))
+    lib().orc_step_adjoint(ctypes.byref(c), _p(f), _p(g.gx), _p(g.gy), _p(lam_next), _p(out), _p(gxb),
+                           _p(gyb), _p(gs))
     return out
 
 
 def adjoint_run(nx, ny, dx, dt, b, s, rho, ux, uy, T, nsteps, loss_grad, bc_x=BC_PERIODIC,
-                bc_y=BC_PERIODIC, ckpt=None):
+                bc_y=BC_PERIODIC, ckpt=None, advection=ADV_LW):
     """Gradient of a loss L(rho_N) with respect to the initial fields and the
     16 rates, by reverse mode through nsteps oracle steps.
 
@@ -239,7 +251,7 @@ def adjoint_run(nx, ny, dx, dt, b, s, rho, ux, uy, T, nsteps, loss_grad, bc_x=BC
     (L, g_rho, g_ux, g_uy, g_T, g_s)."""
     arr = [np.ascontiguousarray(np.broadcast_to(np.asarray(a, dtype=np.float64), (ny, nx)))
            for a in (rho, ux, uy, T)]
-    g = create(nx, ny, dx, dt, b, s, *arr, bc_x=bc_x, bc_y=bc_y)
+    g = create(nx, ny, dx, dt, b, s, *arr, bc_x=bc_x, bc_y=bc_y, advection=advection)
     K = nsteps if not ckpt else int(ckpt)
     saved = {}
     f = g.f.copy()
@@ -268,8 +280,8 @@ def adjoint_run(nx, ny, dx, dt, b, s, rho, ux, uy, T, nsteps, loss_grad, bc_x=BC
 
 
 def forward_loss(nx, ny, dx, dt, b, s, rho, ux, uy, T, nsteps, loss_grad, bc_x=BC_PERIODIC,
-                 bc_y=BC_PERIODIC) -> float:
+                 bc_y=BC_PERIODIC, advection=ADV_LW) -> float:
     """L(rho_N) of a forward oracle run (for finite differences)."""
-    g = create(nx, ny, dx, dt, b, s, rho, ux, uy, T, bc_x=bc_x, bc_y=bc_y)
+    g = create(nx, ny, dx, dt, b, s, rho, ux, uy, T, bc_x=bc_x, bc_y=bc_y, advection=advection)
     run(g, nsteps)
     return loss_grad(macro(g)[0])[0]

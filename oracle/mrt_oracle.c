@@ -59,7 +59,24 @@ typedef struct {
     double b;          /* total number of degrees of freedom; gamma = (b+2)/b */
     double s[NV];      /* relaxation rates s_1..s_16 in 1/time */
     int bc_x, bc_y;    /* ORC_BC_PERIODIC, ORC_BC_FIXED_EQ or ORC_BC_REFLECT_FIXED */
+    int advection;     /* ORC_ADV_* below */
 } orc_cfg;
+
+/* Space discretisation of v_ia d_a f_i.
+ *   ORC_ADV_LW      the paper's Lax-Wendroff operator, axis by axis (the
+ *                   reading taken for the method);
+ *   ORC_ADV_LW2D    the unsplit two-dimensional Lax-Wendroff operator: the
+ *                   same plus the mixed term c_x c_y d_xy f of the
+ *                   second-order Taylor expansion in time, on the four
+ *                   diagonal neighbours (the other reading of the paper's
+ *                   "Lax-Wendroff");
+ *   ORC_ADV_MINMOD,
+ *   ORC_ADV_VANLEER flux-limited variants outside the paper (it names flux
+ *                   limiters only as earlier work on stabilising LB
+ *                   schemes): per velocity and axis the Lax-Wendroff flux is
+ *                   the first-order upwind flux plus a correction scaled by
+ *                   a limiter phi (Sweby's form); phi = 1 gives ORC_ADV_LW. */
+enum { ORC_ADV_LW = 0, ORC_ADV_LW2D = 1, ORC_ADV_MINMOD = 2, ORC_ADV_VANLEER = 3 };
 
 /* ------------------------------------------------------------------------ */
 /* Model: velocity set, eta_i, M and its inverse.                            */
@@ -272,37 +289,147 @@ static int mirror_index(int i, int axis)
     return -1;
 }
 
-/* f_i at (x, y) where x may be -1..nx and y may be -1..ny (one at a time). */
+/* f_i at (x, y) for x in -2..nx+1 and y in -2..ny+1, either axis or both
+ * outside the domain.  Each axis is mapped in turn, x first:
+ *   periodic            the wrapped index;
+ *   reflecting wall     (low end) the mirrored velocity at the mirror-image
+ *                       cell: -1 <-> 0, -2 <-> 1;
+ *   fixed equilibrium   the ghost, whose every layer holds the initial f of
+ *                       the adjacent domain cell (a corner beyond two fixed
+ *                       ends: the initial f of the corner cell).
+ * A fixed ghost is looked up at the other axis's mapped index. */
 static double fat(const orc_cfg *c, const double *f, const double *gx,
                   const double *gy, int i, int x, int y)
 {
     const int nx = c->nx, ny = c->ny;
     const size_t n = (size_t)nx * (size_t)ny;
+    int side_x = -1, side_y = -1;      /* fixed ghost on that side, or -1 */
     if (x < 0 || x >= nx) {
         if (c->bc_x == ORC_BC_PERIODIC) {
-            x = (x + nx) % nx;
+            x = ((x % nx) + nx) % nx;
         } else if (c->bc_x == ORC_BC_REFLECT_FIXED && x < 0) {
-            return f[(size_t)mirror_index(i, 0) * n + (size_t)y * nx + 0];
+            i = mirror_index(i, 0);
+            x = -x - 1;
         } else {
-            const int side = (x < 0) ? 0 : 1;
-            return gx[((size_t)i * 2 + side) * ny + y];
+            side_x = (x < 0) ? 0 : 1;
+            x = (x < 0) ? 0 : nx - 1;
         }
     }
     if (y < 0 || y >= ny) {
         if (c->bc_y == ORC_BC_PERIODIC) {
-            y = (y + ny) % ny;
+            y = ((y % ny) + ny) % ny;
         } else if (c->bc_y == ORC_BC_REFLECT_FIXED && y < 0) {
-            return f[(size_t)mirror_index(i, 1) * n + 0 * (size_t)nx + x];
+            i = mirror_index(i, 1);
+            y = -y - 1;
         } else {
-            const int side = (y < 0) ? 0 : 1;
-            return gy[((size_t)i * 2 + side) * nx + x];
+            side_y = (y < 0) ? 0 : 1;
+            y = (y < 0) ? 0 : ny - 1;
         }
     }
+    if (side_x >= 0) return gx[((size_t)i * 2 + side_x) * ny + y];
+    if (side_y >= 0) return gy[((size_t)i * 2 + side_y) * nx + x];
     return f[(size_t)i * n + (size_t)y * nx + x];
 }
 
+/* Limiter phi(theta) of the flux-limited variants, theta = ratio of the
+ * upwind-side difference to the local difference at a face:
+ *   minmod:   phi = max(0, min(1, theta))
+ *   van Leer: phi = (theta + |theta|) / (1 + |theta|)   (-> 2 as theta -> inf)
+ * Any other value of lim is phi = 1 (the Lax-Wendroff flux). */
+static double limiter_phi(int lim, double theta)
+{
+    if (lim == ORC_ADV_MINMOD) return fmax(0.0, fmin(1.0, theta));
+    if (lim == ORC_ADV_VANLEER) {
+        if (!(theta > 0.0)) return 0.0;
+        if (isinf(theta)) return 2.0;
+        return (theta + fabs(theta)) / (1.0 + fabs(theta));
+    }
+    return 1.0;
+}
+
+/* d phi / d theta, with the one-sided value that the forward branch takes
+ * at the kinks (a subgradient): minmod 1 on 0 < theta < 1 and 0 elsewhere
+ * (theta = 0 and theta = 1 take 0); van Leer 2/(1+theta)^2 for theta > 0
+ * and 0 for theta <= 0. */
+static double limiter_dphi(int lim, double theta)
+{
+    if (lim == ORC_ADV_MINMOD) return (theta > 0.0 && theta < 1.0) ? 1.0 : 0.0;
+    if (lim == ORC_ADV_VANLEER) {
+        if (!(theta > 0.0) || isinf(theta)) return 0.0;
+        return 2.0 / ((1.0 + theta) * (1.0 + theta));
+    }
+    return 0.0;
+}
+
+/* Flux of one velocity through the face between cells j and j+1 along one
+ * axis, in units of f per step, c = v dt/dx (|c| <= 1):
+ *   F = c f_upwind + (|c| (1 - |c|) / 2) phi(theta) (f_{j+1} - f_j),
+ *   f_upwind = f_j, theta = (f_j - f_{j-1}) / (f_{j+1} - f_j)        (c >= 0)
+ *   f_upwind = f_{j+1}, theta = (f_{j+2} - f_{j+1}) / (f_{j+1} - f_j) (c < 0)
+ * and the correction is 0 where f_{j+1} = f_j.  With phi = 1 the
+ * difference of two such fluxes is the Lax-Wendroff operator
+ * -(c/2)(f_+ - f_-) + (c^2/2)(f_+ - 2 f + f_-).
+ * d[0..3] receives dF/d(f_{j-1}, f_j, f_{j+1}, f_{j+2}) (subgradient at
+ * the limiter's kinks, see limiter_dphi). */
+static double face_flux(int lim, double c, double fjm1, double fj, double fj1, double fj2, double d[4])
+{
+    const double ac = fabs(c);
+    const double K = 0.5 * ac * (1.0 - ac);
+    const double dloc = fj1 - fj;
+    const double dup = (c >= 0.0) ? fj - fjm1 : fj2 - fj1;
+    double F = (c >= 0.0) ? c * fj : c * fj1;
+    double dcorr_dup = 0.0, dcorr_dloc = 0.0;
+    if (dloc != 0.0) {
+        const double th = dup / dloc;
+        const double ph = limiter_phi(lim, th), dph = limiter_dphi(lim, th);
+        F += K * ph * dloc;
+        dcorr_dup = dph;
+        dcorr_dloc = ph - th * dph;
+    }
+    d[0] = d[1] = d[2] = d[3] = 0.0;
+    if (c >= 0.0) {
+        d[1] += c;
+        d[1] += K * dcorr_dup;   d[0] -= K * dcorr_dup;
+    } else {
+        d[2] += c;
+        d[3] += K * dcorr_dup;   d[2] -= K * dcorr_dup;
+    }
+    d[2] += K * dcorr_dloc;  d[1] -= K * dcorr_dloc;
+    return F;
+}
+
+/* Advection increment of velocity i at (x, y) in a flux-limited variant:
+ * minus the flux difference across the cell along x and along y.  If dA is
+ * not NULL it receives dAdv/df_i at (x+m, y), m = -2..2 (dA[0..4]), and at
+ * (x, y+m) (dA[5..9]). */
+static double adv_limited(const orc_cfg *c, const double *f, const double *gx, const double *gy,
+                          int i, int x, int y, double dA[10])
+{
+    const double lam = c->dt / c->dx;
+    const double cv[2] = {g_vx[i] * lam, g_vy[i] * lam};
+    double adv = 0.0;
+    if (dA) for (int m = 0; m < 10; ++m) dA[m] = 0.0;
+    for (int ax = 0; ax < 2; ++ax) {
+        double v[5];                       /* f at offsets -2..2 along the axis */
+        for (int m = -2; m <= 2; ++m)
+            v[m + 2] = ax == 0 ? fat(c, f, gx, gy, i, x + m, y) : fat(c, f, gx, gy, i, x, y + m);
+        double dp[4], dm[4];
+        const double Fp = face_flux(c->advection, cv[ax], v[1], v[2], v[3], v[4], dp);  /* face +1/2 */
+        const double Fm = face_flux(c->advection, cv[ax], v[0], v[1], v[2], v[3], dm);  /* face -1/2 */
+        adv += -(Fp - Fm);
+        if (dA)
+            for (int q = 0; q < 4; ++q) {
+                dA[5 * ax + q + 1] -= dp[q];
+                dA[5 * ax + q] += dm[q];
+            }
+    }
+    return adv;
+}
+
 /* f^{n+1} from f^n.  For every cell and every velocity i (Eq. 3 with
- * forward Euler in time and Lax-Wendroff in space):
+ * forward Euler in time and Lax-Wendroff in space; ORC_ADV_LW2D adds the
+ * mixed term (c_x c_y / 4)(f_{++} - f_{+-} - f_{-+} + f_{--}), the flux-limited
+ * variants take Adv_i = adv_limited instead):
  *   fhat = M f                          (moments, Appendix rows)
  *   fhat^eq from rho, jx, jy, e          (Appendix equilibria)
  *   Omega_i = -sum_k Minv_ik s_k (fhat_k - fhat^eq_k)
@@ -337,6 +464,11 @@ void orc_step(const orc_cfg *c, const double *f, const double *gx, const double 
             }
             for (int i = 0; i < NV; ++i) {
                 const double f0 = fl[i];
+                if (c->advection == ORC_ADV_MINMOD || c->advection == ORC_ADV_VANLEER) {
+                    const double adv = adv_limited(c, f, gx, gy, i, x, y, NULL);
+                    fnew[(size_t)i * n + (size_t)y * nx + x] = f0 + adv + c->dt * om[i];
+                    continue;
+                }
                 const double cx = g_vx[i] * lam, cy = g_vy[i] * lam;
                 const double fxp = fat(c, f, gx, gy, i, x + 1, y);
                 const double fxm = fat(c, f, gx, gy, i, x - 1, y);
@@ -344,7 +476,11 @@ void orc_step(const orc_cfg *c, const double *f, const double *gx, const double 
                 const double fym = fat(c, f, gx, gy, i, x, y - 1);
                 const double adv_x = -0.5 * cx * (fxp - fxm) + 0.5 * cx * cx * (fxp - 2.0 * f0 + fxm);
                 const double adv_y = -0.5 * cy * (fyp - fym) + 0.5 * cy * cy * (fyp - 2.0 * f0 + fym);
-                fnew[(size_t)i * n + (size_t)y * nx + x] = f0 + adv_x + adv_y + c->dt * om[i];
+                double adv_xy = 0.0;
+                if (c->advection == ORC_ADV_LW2D && cx != 0.0 && cy != 0.0)
+                    adv_xy = 0.25 * cx * cy * (fat(c, f, gx, gy, i, x + 1, y + 1) - fat(c, f, gx, gy, i, x + 1, y - 1)
+                                               - fat(c, f, gx, gy, i, x - 1, y + 1) + fat(c, f, gx, gy, i, x - 1, y - 1));
+                fnew[(size_t)i * n + (size_t)y * nx + x] = f0 + adv_x + adv_y + adv_xy + c->dt * om[i];
             }
         }
     }
@@ -492,39 +628,40 @@ void orc_feq_moments_via_cplx(double rho, double jx, double jy, double e, double
     for (int k = 0; k < NV; ++k) out[k] = creal(o[k]);
 }
 
-/* Add w * lam at (x, y) of plane i to the adjoint of the cell read there
- * (the transpose of fat): a domain cell, a wrapped cell on a periodic axis,
- * the mirrored domain cell behind a reflecting wall, or a fixed ghost whose
- * adjoint is accumulated in gxb / gyb (same layout as gx / gy). */
+/* Add v at (x, y) of plane i to the adjoint of the value read there: the
+ * transpose of fat, with the same mapping of each axis (a domain cell, a
+ * wrapped cell, the mirrored cell behind a reflecting wall, or a fixed
+ * ghost whose adjoint is accumulated in gxb / gyb, same layout as gx / gy). */
 static void scatter(const orc_cfg *c, double *lam, double *gxb, double *gyb, int i, int x, int y,
                     double v)
 {
     const int nx = c->nx, ny = c->ny;
     const size_t n = (size_t)nx * (size_t)ny;
+    int side_x = -1, side_y = -1;
     if (x < 0 || x >= nx) {
         if (c->bc_x == ORC_BC_PERIODIC) {
-            x = (x + nx) % nx;
+            x = ((x % nx) + nx) % nx;
         } else if (c->bc_x == ORC_BC_REFLECT_FIXED && x < 0) {
-            lam[(size_t)mirror_index(i, 0) * n + (size_t)y * nx + 0] += v;
-            return;
+            i = mirror_index(i, 0);
+            x = -x - 1;
         } else {
-            const int side = (x < 0) ? 0 : 1;
-            gxb[((size_t)i * 2 + side) * ny + y] += v;
-            return;
+            side_x = (x < 0) ? 0 : 1;
+            x = (x < 0) ? 0 : nx - 1;
         }
     }
     if (y < 0 || y >= ny) {
         if (c->bc_y == ORC_BC_PERIODIC) {
-            y = (y + ny) % ny;
+            y = ((y % ny) + ny) % ny;
         } else if (c->bc_y == ORC_BC_REFLECT_FIXED && y < 0) {
-            lam[(size_t)mirror_index(i, 1) * n + 0 * (size_t)nx + x] += v;
-            return;
+            i = mirror_index(i, 1);
+            y = -y - 1;
         } else {
-            const int side = (y < 0) ? 0 : 1;
-            gyb[((size_t)i * 2 + side) * nx + x] += v;
-            return;
+            side_y = (y < 0) ? 0 : 1;
+            y = (y < 0) ? 0 : ny - 1;
         }
     }
+    if (side_x >= 0) { gxb[((size_t)i * 2 + side_x) * ny + y] += v; return; }
+    if (side_y >= 0) { gyb[((size_t)i * 2 + side_y) * nx + x] += v; return; }
     lam[(size_t)i * n + (size_t)y * nx + x] += v;
 }
 
@@ -537,9 +674,14 @@ static void scatter(const orc_cfg *c, double *lam, double *gxb, double *gyb, int
  *   d(dt Omega)/df = -dt Minv S (I - JE) M,  JE = d fhat^eq / d fhat
  *                                               (non-zero in columns 1..4),
  *   d f^{n+1}_i/d s_k = -dt Minv_ik (fhat_k - fhat^eq_k).
+ * With ORC_ADV_LW2D the mixed term is scattered to the four diagonal
+ * neighbours.  In a flux-limited variant the advection part is transposed from the
+ * derivatives of adv_limited, which reads the forward ghosts gx_fwd / gy_fwd
+ * (the limiter's branch depends on them); at a kink the branch the forward
+ * step takes supplies the derivative (a subgradient).
  * Serial (the scatter form writes to neighbours). */
-void orc_step_adjoint(const orc_cfg *c, const double *f, const double *lam_next, double *lam,
-                      double *gxb, double *gyb, double gs[NV])
+void orc_step_adjoint(const orc_cfg *c, const double *f, const double *gx_fwd, const double *gy_fwd,
+                      const double *lam_next, double *lam, double *gxb, double *gyb, double gs[NV])
 {
     ensure_model();
     const int nx = c->nx, ny = c->ny;
@@ -555,6 +697,18 @@ void orc_step_adjoint(const orc_cfg *c, const double *f, const double *lam_next,
             }
             /* advection and identity: scatter to the cells the output read */
             for (int i = 0; i < NV; ++i) {
+                if (c->advection == ORC_ADV_MINMOD || c->advection == ORC_ADV_VANLEER) {
+                    /* flux-limited variant: the local derivatives of Adv_i
+                     * (subgradients at the limiter's kinks) */
+                    double dA[10];
+                    adv_limited(c, f, gx_fwd, gy_fwd, i, x, y, dA);
+                    scatter(c, lam, gxb, gyb, i, x, y, ln[i]);
+                    for (int m = -2; m <= 2; ++m) {
+                        scatter(c, lam, gxb, gyb, i, x + m, y, dA[m + 2] * ln[i]);
+                        scatter(c, lam, gxb, gyb, i, x, y + m, dA[5 + m + 2] * ln[i]);
+                    }
+                    continue;
+                }
                 const double cx = g_vx[i] * lam_r, cy = g_vy[i] * lam_r;
                 /* f_new = f0 + ax_m f(x-1) + ax_p f(x+1) + (-cx^2) f0 + (same in y) */
                 const double am_x = 0.5 * cx + 0.5 * cx * cx, ap_x = -0.5 * cx + 0.5 * cx * cx;
@@ -565,6 +719,13 @@ void orc_step_adjoint(const orc_cfg *c, const double *f, const double *lam_next,
                 scatter(c, lam, gxb, gyb, i, x + 1, y, ap_x * ln[i]);
                 scatter(c, lam, gxb, gyb, i, x, y - 1, am_y * ln[i]);
                 scatter(c, lam, gxb, gyb, i, x, y + 1, ap_y * ln[i]);
+                if (c->advection == ORC_ADV_LW2D && cx != 0.0 && cy != 0.0) {
+                    const double wxy = 0.25 * cx * cy * ln[i];
+                    scatter(c, lam, gxb, gyb, i, x + 1, y + 1, wxy);
+                    scatter(c, lam, gxb, gyb, i, x + 1, y - 1, -wxy);
+                    scatter(c, lam, gxb, gyb, i, x - 1, y + 1, -wxy);
+                    scatter(c, lam, gxb, gyb, i, x - 1, y - 1, wxy);
+                }
             }
             /* collision, local */
             for (int k = 0; k < NV; ++k) {
