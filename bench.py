@@ -61,6 +61,7 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--n", type=int, default=4096, help="grid edge (default 4096)")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-lw2d", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
@@ -261,6 +262,36 @@ def run_reference(args):
 
 
 # ---------------------------------------------------------------------------
+def unsplit_operator(Bd, w, torch, stream, args, peak):
+    """The same workload stepped with MRT_ADV_LW2D: FP32 (HBM bound, the
+    same 128 B per cell-update) and FP64, CUDA events on the grid's stream."""
+    out = {}
+    cells = w.nx * w.ny
+    for prec, name, k in ((Bd.FP32, "fp32", max(20, min(1000, args.steps // 5))),
+                          (Bd.FP64, "fp64", max(5, min(60, args.steps // 25)))):
+        if prec == Bd.FP64 and args.no_fp64:
+            continue
+        with torch.cuda.stream(stream):
+            g = Bd.Grid.from_workload(w, precision=prec, kernel=Bd.KERNEL_TMA, stream=stream.cuda_stream,
+                                      advection=Bd.ADV_LW2D)
+        g.step(3)
+        torch.cuda.synchronize()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        g.step(k)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        ms = ev0.elapsed_time(ev1)
+        assert g.health() == Bd.MRT_OK
+        tile = g.info()["tile"]
+        g.close()
+        per = ms * 1e-3 / k
+        bpc = BYTES_PER_CELL_F32 if prec == Bd.FP32 else BYTES_PER_CELL_F64
+        out[name] = {"value": cells / per, "unit": "cell-updates/s", "steps": k, "tile": tile,
+                     "hbm_achieved_gbs": bpc * cells / per / 1e9, "hbm_frac": bpc * cells / per / 1e9 / peak}
+    return out
+
+
 def run_ours(args):
     import torch
     rank, world, local = dist_init(args.gpus)
@@ -349,6 +380,11 @@ def run_ours(args):
                                      "peak_source": "derived: 152 SMs x 2 FP64 lanes x 2 flops x max SM clock",
                                      "per_cell": {"fp64_pipe_inst": FP64_PIPE_INST_PER_CELL,
                                                   "flops": FP64_FLOPS_PER_CELL}}}
+
+    # the unsplit two-dimensional Lax-Wendroff operator (mixed term on the
+    # diagonal velocities), same workload and timing, FP32 and FP64
+    if not args.no_lw2d:
+        line["lw2d"] = unsplit_operator(Bd, w, torch, stream, args, peak)
 
     # adjoint / forward cost (smooth vortex 512^2, 500 FP32 steps, checkpoints
     # every 50; and the 4096^2 workload for the HBM-bound ratio)

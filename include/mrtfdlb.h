@@ -70,6 +70,20 @@ typedef enum mrt_bc { MRT_BC_PERIODIC = 0, MRT_BC_FIXED_EQ = 1, MRT_BC_REFLECT_F
  * run the same cell arithmetic; results agree to rounding. */
 typedef enum mrt_kernel { MRT_KERNEL_AUTO = 0, MRT_KERNEL_TMA = 1, MRT_KERNEL_DIRECT = 2 } mrt_kernel;
 
+/* Space discretisation of the advection term v_ia d_a f_i (Sect.
+ * "Construction of energy-conserving MRT LB model": Lax-Wendroff in space,
+ * forward Euler in time).  MRT_ADV_LW: the Lax-Wendroff operator applied
+ * axis by axis, per axis -(c/2)(f_+ - f_-) + (c^2/2)(f_+ - 2 f + f_-),
+ * c = v_a dt/dx (the method's default reading).  MRT_ADV_LW2D: the unsplit
+ * two-dimensional Lax-Wendroff operator, which adds to each diagonal
+ * velocity the mixed term (c_x c_y / 4)(f_{x+1,y+1} - f_{x+1,y-1} -
+ * f_{x-1,y+1} + f_{x-1,y-1}) of the second-order Taylor expansion in time
+ * (second order in time for those velocities; the split form is first order
+ * there).  Beyond two fixed ends the corner ghost holds the corner cell's
+ * initial f.  MRT_ADV_LW2D runs on the direct kernel and on TMA tiles 0, 1,
+ * 4 and 7; the reverse mode and batches take MRT_ADV_LW only. */
+typedef enum mrt_advection { MRT_ADV_LW = 0, MRT_ADV_LW2D = 1 } mrt_advection;
+
 typedef struct mrt_params {
     int nx, ny;         /* cells; each >= 3 */
     double dx;          /* cell size (dy = dx), > 0 */
@@ -90,6 +104,8 @@ typedef struct mrt_params {
                            variants of 5 and 4 whose CTAs take 8- or 32-row
                            work items from an atomic counter; other values
                            give MRT_EINVAL.  Results do not depend on it. */
+    int advection;      /* mrt_advection; 0 (MRT_ADV_LW) for the method's
+                           axis-by-axis Lax-Wendroff operator */
 } mrt_params;
 
 typedef struct mrt_grid mrt_grid;

@@ -20,6 +20,7 @@ MRT_OK, MRT_EINVAL, MRT_ENOMEM, MRT_ECUDA, MRT_EUNSTABLE, MRT_ETIMEOUT = range(6
 FP32, FP64 = 0, 1
 BC_PERIODIC, BC_FIXED_EQ, BC_REFLECT_FIXED = 0, 1, 2
 KERNEL_AUTO, KERNEL_TMA, KERNEL_DIRECT = 0, 1, 2
+ADV_LW, ADV_LW2D = 0, 1
 
 # every symbol include/mrtfdlb.h declares
 EXPORTED = ["mrt_create", "mrt_step", "mrt_get_macro", "mrt_conserved_totals", "mrt_get_f",
@@ -44,7 +45,8 @@ class Params(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("dx", ctypes.c_double),
                 ("dt", ctypes.c_double), ("gamma", ctypes.c_double), ("Pr", ctypes.c_double),
                 ("s", ctypes.c_double * 16), ("bc_x", ctypes.c_int), ("bc_y", ctypes.c_int),
-                ("precision", ctypes.c_int), ("kernel", ctypes.c_int), ("tile", ctypes.c_int)]
+                ("precision", ctypes.c_int), ("kernel", ctypes.c_int), ("tile", ctypes.c_int),
+                ("advection", ctypes.c_int)]
 
 
 _lib = None
@@ -125,13 +127,14 @@ def _torch_stream():
 
 
 def make_params(nx, ny, dx, dt, gamma, s, bc_x=BC_PERIODIC, bc_y=BC_PERIODIC, precision=FP32,
-                Pr=0.0, kernel=KERNEL_AUTO, tile=0) -> Params:
+                Pr=0.0, kernel=KERNEL_AUTO, tile=0, advection=0) -> Params:
     p = Params()
     p.nx, p.ny, p.dx, p.dt, p.gamma, p.Pr = int(nx), int(ny), float(dx), float(dt), float(gamma), float(Pr)
     for k in range(16):
         p.s[k] = float(s[k])
     p.bc_x, p.bc_y, p.precision, p.kernel = int(bc_x), int(bc_y), int(precision), int(kernel)
     p.tile = int(tile)
+    p.advection = int(advection)
     return p
 
 
@@ -178,8 +181,9 @@ class Grid:
         return g
 
     @classmethod
-    def from_workload(cls, w, precision=FP32, kernel=KERNEL_AUTO, stream=None, tile=0):
-        p = make_params(w.nx, w.ny, w.dx, w.dt, w.gamma, w.s, w.bc_x, w.bc_y, precision, 0.0, kernel, tile)
+    def from_workload(cls, w, precision=FP32, kernel=KERNEL_AUTO, stream=None, tile=0, advection=0):
+        p = make_params(w.nx, w.ny, w.dx, w.dt, w.gamma, w.s, w.bc_x, w.bc_y, precision, 0.0, kernel, tile,
+                        advection)
         return cls(p, w.rho, w.ux, w.uy, w.T, stream=stream)
 
     @property

@@ -49,6 +49,7 @@ extern "C" mrt_status mrt_adjoint_record(mrt_grid* g, const double* rho0, const 
     if (!g) return mrt_fail(MRT_EINVAL, "grid is NULL");
     if (nsteps < 1) return mrt_fail(MRT_EINVAL, "nsteps must be >= 1");
     if (ckpt_every < 1) return mrt_fail(MRT_EINVAL, "ckpt_every must be >= 1");
+    if (g->xt) return mrt_fail(MRT_EINVAL, "the reverse mode takes the axis-by-axis operator (MRT_ADV_LW)");
     if (!rho0 || !ux0 || !uy0 || !T0) return mrt_fail(MRT_EINVAL, "null field pointer");
     mrt_tape_free(g->tape);
     g->tape = nullptr;
@@ -292,6 +293,7 @@ extern "C" mrt_status mrt_adjoint_step(mrt_grid* g, const void* f, const void* l
                                        double g_s[16]) {
     if (!g) return mrt_fail(MRT_EINVAL, "grid is NULL");
     if (!f || !lam_next || !lam) return mrt_fail(MRT_EINVAL, "null state pointer");
+    if (g->xt) return mrt_fail(MRT_EINVAL, "the reverse mode takes the axis-by-axis operator (MRT_ADV_LW)");
     return g->fp64 ? adjoint_step_impl<double>(g, f, lam_next, lam, on_device, g_s)
                    : adjoint_step_impl<float>(g, f, lam_next, lam, on_device, g_s);
 }

@@ -120,6 +120,7 @@ int mrt_model_build(double dx, double dt, double b, const double s[16], Coef<dou
         const double c = kU(g) * dt / dx;
         k->lwp[g] = 0.5 * (c * c + c);
         k->lwq[g] = 0.5 * (c * c - c);
+        if (g >= 2) k->kxy[g - 2] = 0.25 * c * c;   // |c_x c_y| / 4 on a diagonal
     }
     for (int g = 0; g < 2; ++g)
         for (int j = 0; j < 2; ++j) {
@@ -228,11 +229,15 @@ __global__ void ghost_cols_kernel(Layout L, int lo, int hi, T* f) {
     }
 }
 
+// The ghost rows span the ghost columns too (x = -1 and nx), after those
+// were set: a corner then holds the ghost-row rule applied to the ghost
+// column, which is what the unsplit operator reads there.
 template <class T>
 __global__ void ghost_rows_kernel(Layout L, int lo, int hi, T* f) {
-    const long n = 16L * L.nx;
+    const long w = L.nx + 2;
+    const long n = 16L * w;
     for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < n; t += (long)gridDim.x * blockDim.x) {
-        const int i = (int)(t / L.nx), x = (int)(t % L.nx);
+        const int i = (int)(t / w), x = (int)(t % w) - 1;
         T* p = f + i * L.plane + L.G + x;
         if (lo == GH_COPY) p[0] = p[L.pitch];
         if (lo == GH_WRAP) p[0] = p[(long)L.ny * L.pitch];
@@ -439,6 +444,10 @@ static mrt_status validate(const mrt_params* p) {
     if (p->precision != MRT_FP32 && p->precision != MRT_FP64) return fail(MRT_EINVAL, "bad precision");
     if (p->kernel < MRT_KERNEL_AUTO || p->kernel > MRT_KERNEL_DIRECT) return fail(MRT_EINVAL, "bad kernel");
     if (p->tile < 0 || p->tile >= NUM_TILES) return fail(MRT_EINVAL, "bad tile %d", p->tile);
+    if (p->advection != MRT_ADV_LW && p->advection != MRT_ADV_LW2D)
+        return fail(MRT_EINVAL, "bad advection %d", p->advection);
+    if (p->advection == MRT_ADV_LW2D && p->kernel != MRT_KERNEL_DIRECT && !tile_supports_xt(p->tile))
+        return fail(MRT_EINVAL, "the unsplit operator runs on tiles 0, 1, 4 and 7 (it reads row r-1 from the ring)");
     return MRT_OK;
 }
 
@@ -483,7 +492,7 @@ static void launch_ghost_kernels(mrt_grid* g, T* f, bool creation) {
     if (xl != GH_KEEP || xh != GH_KEEP)
         ghost_cols_kernel<T><<<grid_for(16L * g->L.ny, 256), 256, 0, g->stream>>>(g->L, xl, xh, f);
     if (yl != GH_KEEP || yh != GH_KEEP)
-        ghost_rows_kernel<T><<<grid_for(16L * g->L.nx, 256), 256, 0, g->stream>>>(g->L, yl, yh, f);
+        ghost_rows_kernel<T><<<grid_for(16L * (g->L.nx + 2), 256), 256, 0, g->stream>>>(g->L, yl, yh, f);
 }
 
 template <class T>
@@ -520,6 +529,7 @@ extern "C" mrt_status mrt_create(const mrt_params* params, const double* rho, co
     g->p = *params;
     if (g->p.Pr > 0) g->p.s[7] = g->p.s[8] = g->p.Pr * g->p.s[5];
     g->fp64 = params->precision == MRT_FP64;
+    g->xt = params->advection == MRT_ADV_LW2D;
     g->elem = g->fp64 ? 8 : 4;
     g->b = 2.0 / (params->gamma - 1.0);
     g->stream = static_cast<cudaStream_t>(stream);
@@ -570,13 +580,13 @@ extern "C" mrt_status mrt_create(const mrt_params* params, const double* rho, co
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, g->device);
         const int strips = (params->nx + TMA_W - 1) / TMA_W;
         auto occupancy = [&](int tile, int* o) {
-            return g->fp64 ? tma_occupancy<double>(tile, o) : tma_occupancy<float>(tile, o);
+            return g->fp64 ? tma_occupancy<double>(tile, g->xt, o) : tma_occupancy<float>(tile, g->xt, o);
         };
         g->tile = params->tile;
         if (g->tile == 0) {
             // the work-queue tile when the grid gives every resident CTA at
             // least two items, else one static chunk of rows per CTA
-            const int qt = kQueueTile, qr = tile_cfg(qt).queue_rows;
+            const int qt = g->xt ? kQueueTileXT : kQueueTile, qr = tile_cfg(qt).queue_rows;
             if ((e = occupancy(qt, &occ)) != cudaSuccess)
                 return bail(fail(MRT_ECUDA, "occupancy query: %s", cudaGetErrorString(e)));
             const long items = (long)strips * ((params->ny + qr - 1) / qr);
@@ -706,8 +716,8 @@ mrt_status step_between(mrt_grid* g, const void* in, void* out, const CUtensorMa
     a.out = static_cast<T*>(out);
     queue_args(g, a);
     cudaError_t e = g->kernel == MRT_KERNEL_TMA
-        ? launch_step_tma<T>(g->tile, map_in, map_out, a, g->tma_grid_x, g->tma_grid_y, totals, g->stream)
-        : launch_step_direct<T>(a, totals, g->stream);
+        ? launch_step_tma<T>(g->tile, g->xt, map_in, map_out, a, g->tma_grid_x, g->tma_grid_y, totals, g->stream)
+        : launch_step_direct<T>(a, g->xt, totals, g->stream);
     if (e != cudaSuccess) return fail(MRT_ECUDA, "step launch: %s", cudaGetErrorString(e));
     return MRT_OK;
 }
@@ -734,10 +744,10 @@ static mrt_status step_impl(mrt_grid* g, long nsteps) {
         queue_args(g, a);
         cudaError_t e;
         if (g->kernel == MRT_KERNEL_TMA) {
-            e = launch_step_tma<T>(g->tile, &g->maps[g->cur], &g->maps_out[g->cur ^ 1], a, g->tma_grid_x,
+            e = launch_step_tma<T>(g->tile, g->xt, &g->maps[g->cur], &g->maps_out[g->cur ^ 1], a, g->tma_grid_x,
                                    g->tma_grid_y, totals, g->stream);
         } else {
-            e = launch_step_direct<T>(a, totals, g->stream);
+            e = launch_step_direct<T>(a, g->xt, totals, g->stream);
         }
         if (e != cudaSuccess) return fail(MRT_ECUDA, "step launch: %s", cudaGetErrorString(e));
         if (totals) CUDA_TRY(reduce_totals(g, g->parts));

@@ -233,8 +233,11 @@ extern "C" mrt_status mrt_batch_create(int n, const mrt_params* params, const do
     if (!out || !params || !rho || !ux || !uy || !T) return mrt_fail(MRT_EINVAL, "null argument");
     if (n < 1 || n > kCoefSlots) return mrt_fail(MRT_EINVAL, "batch size must be 1..%d", kCoefSlots);
     *out = nullptr;
-    for (int i = 0; i < n; ++i)
+    for (int i = 0; i < n; ++i) {
         if (params[i].precision != MRT_FP32) return mrt_fail(MRT_EINVAL, "batched instances are FP32 (instance %d)", i);
+        if (params[i].advection != MRT_ADV_LW)
+            return mrt_fail(MRT_EINVAL, "batched instances take the axis-by-axis operator (instance %d)", i);
+    }
     mrt_batch* b = new (std::nothrow) mrt_batch();
     if (!b) return mrt_fail(MRT_ENOMEM, "host allocation failed");
     b->n = n;

@@ -105,6 +105,9 @@ inline TileCfg tile_cfg(int tile) {
 constexpr int kQueueTile = 6;
 constexpr int kStaticTileF32 = 4;
 constexpr int kStaticTileF64 = 1;
+// The unsplit operator keeps row r-1 in the ring: its queue tile is 7.
+constexpr int kQueueTileXT = 7;
+inline bool tile_supports_xt(int tile) { return tile == 0 || tile == 1 || tile == 4 || tile == 7; }
 
 template <class T>
 inline size_t tma_smem_bytes(int tile) {
@@ -115,13 +118,14 @@ inline size_t tma_smem_bytes(int tile) {
 
 // Launchers (step_kernels.cu).  grid_y = number of row chunks for the TMA
 // kernel.  Return the launch status.
+// xt: the unsplit operator (MRT_ADV_LW2D; TMA tiles 1, 4 and 7 only).
 template <class T>
-cudaError_t launch_step_tma(int tile, const CUtensorMap* map_in, const CUtensorMap* map_out,
+cudaError_t launch_step_tma(int tile, bool xt, const CUtensorMap* map_in, const CUtensorMap* map_out,
                             const StepArgs<T>& a, int grid_x, int grid_y, bool totals, cudaStream_t st);
 template <class T>
-cudaError_t launch_step_direct(const StepArgs<T>& a, bool totals, cudaStream_t st);
+cudaError_t launch_step_direct(const StepArgs<T>& a, bool xt, bool totals, cudaStream_t st);
 template <class T>
-cudaError_t tma_occupancy(int tile, int* blocks_per_sm);
+cudaError_t tma_occupancy(int tile, bool xt, int* blocks_per_sm);
 template <class T>
 void direct_grid(const Layout& L, dim3* grid, dim3* block);
 
@@ -195,6 +199,7 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t,
 struct mrt_grid {
     mrt_params p;
     int fp64;
+    int xt = 0;                      // unsplit operator (MRT_ADV_LW2D)
     size_t elem;
     mrt::Layout L;
     void* f[2] = {nullptr, nullptr};

@@ -58,6 +58,9 @@ struct Coef {
     // Lax-Wendroff weights per group with c = u_g dt/dx:
     // p = (c^2 + c)/2 on the upwind neighbour, q = (c^2 - c)/2 on the other.
     T lwp[4], lwq[4];
+    // Mixed term of the unsplit two-dimensional operator on the diagonal
+    // groups 2, 3: |c_x c_y| / 4 = (u_g dt/dx)^2 / 4.
+    T kxy[2];
     T inv_b;      // 1/b
     T c14a;       // 2 (b + 2)
     T c14b;       // 6 + b
@@ -88,11 +91,13 @@ inline void coef_cast(const Coef<Src>& a, Coef<Dst>* o) {
         o->lwp[g] = (Dst)a.lwp[g];
         o->lwq[g] = (Dst)a.lwq[g];
     }
-    for (int g = 0; g < 2; ++g)
+    for (int g = 0; g < 2; ++g) {
         for (int j = 0; j < 2; ++j) {
             o->kQ[g][j] = (Dst)a.kQ[g][j];
             o->kX[g][j] = (Dst)a.kX[g][j];
         }
+        o->kxy[g] = (Dst)a.kxy[g];
+    }
     for (int k = 0; k < 12; ++k) o->sig[k] = (Dst)a.sig[k];
     o->inv_b = (Dst)a.inv_b;
     o->c14a = (Dst)a.c14a;
@@ -102,8 +107,9 @@ inline void coef_cast(const Coef<Src>& a, Coef<Dst>* o) {
 
 #ifdef __CUDACC__
 
-// Stencil positions handed to a fetch functor.
-enum Pos { C = 0, XM = 1, XP = 2, YM = 3, YP = 4 };
+// Stencil positions handed to a fetch functor; the four diagonal
+// neighbours are read only by the unsplit operator (XT).
+enum Pos { C = 0, XM = 1, XP = 2, YM = 3, YP = 4, XPYP = 5, XPYM = 6, XMYP = 7, XMYM = 8 };
 
 // Conserved moments (rho, jx, jy, e) of a 16-vector, from the group sums.
 template <class T>
@@ -135,7 +141,12 @@ __device__ __forceinline__ float recip<float>(float x) { return __fdividef(1.0f,
 // The Lax-Wendroff terms are accumulated as multiply-adds of neighbour
 // differences onto the collision increment, so a uniform state is left
 // exactly unchanged by the advection in any precision.
-template <class T, class Fetch>
+//
+// XT: the unsplit two-dimensional Lax-Wendroff operator, which adds to each
+// diagonal velocity the mixed term (c_x c_y / 4)(f(x+1,y+1) - f(x+1,y-1)
+// - f(x-1,y+1) + f(x-1,y-1)) of the second-order Taylor expansion in time
+// (c_x c_y > 0 for (+,+) and (-,-), < 0 for (-,+) and (+,-)).
+template <class T, bool XT = false, class Fetch>
 __device__ __forceinline__ void cell_update(const Fetch& F, const Coef<T>& k, T out[NV],
                                             T& rho_in, T& P_in) {
     T f[NV];
@@ -243,31 +254,45 @@ __device__ __forceinline__ void cell_update(const Fetch& F, const Coef<T>& k, T 
         } else {
             const T cXY = k.kX[g - 2][0] * d7 + k.kX[g - 2][1] * d15;
             const T t1 = cS + cXY, t2 = cS - cXY, s1 = cX + cY, s2 = cX - cY;
+            // XT: mixed terms, (f++ - f+-) - (f-+ - f--) scaled by |c_x c_y|/4
+            // and signed by c_x c_y; exactly 0 on a uniform state
+            T e0 = 0, e1 = 0, e2 = 0, e3 = 0;
+            auto with_mixed = [](T v, T e) -> T {
+                if constexpr (XT) return v + e; else return v;
+            };
+            if constexpr (XT) {
+                const T w = k.kxy[g - 2];
+                auto mixed = [&](int i) { return (F(i, XPYP) - F(i, XPYM)) - (F(i, XMYP) - F(i, XMYM)); };
+                e0 = w * mixed(i0 + 0);
+                e1 = -(w * mixed(i0 + 1));
+                e2 = w * mixed(i0 + 2);
+                e3 = -(w * mixed(i0 + 3));
+            }
             // |c_x| = |c_y| on a diagonal: pair the x and y neighbours that
             // carry the same weight, (a + b - 2 f) is exact for a uniform state
             {   // (+,+): p on x-1, y-1; q on x+1, y+1
                 const T fc = f[i0 + 0];
                 const T a = (F(i0 + 0, XM) + F(i0 + 0, YM)) - (fc + fc);
                 const T b = (F(i0 + 0, XP) + F(i0 + 0, YP)) - (fc + fc);
-                out[i0 + 0] = fc + (p * a + (qq * b + (t1 + s1)));
+                out[i0 + 0] = fc + (p * a + (qq * b + with_mixed((t1 + s1), e0)));
             }
             {   // (-,+): q on x-1, p on x+1; p on y-1, q on y+1
                 const T fc = f[i0 + 1];
                 const T a = (F(i0 + 1, XP) + F(i0 + 1, YM)) - (fc + fc);
                 const T b = (F(i0 + 1, XM) + F(i0 + 1, YP)) - (fc + fc);
-                out[i0 + 1] = fc + (p * a + (qq * b + (t2 - s2)));
+                out[i0 + 1] = fc + (p * a + (qq * b + with_mixed((t2 - s2), e1)));
             }
             {   // (-,-): q on x-1, y-1; p on x+1, y+1
                 const T fc = f[i0 + 2];
                 const T a = (F(i0 + 2, XP) + F(i0 + 2, YP)) - (fc + fc);
                 const T b = (F(i0 + 2, XM) + F(i0 + 2, YM)) - (fc + fc);
-                out[i0 + 2] = fc + (p * a + (qq * b + (t1 - s1)));
+                out[i0 + 2] = fc + (p * a + (qq * b + with_mixed((t1 - s1), e2)));
             }
             {   // (+,-): p on x-1, q on x+1; q on y-1, p on y+1
                 const T fc = f[i0 + 3];
                 const T a = (F(i0 + 3, XM) + F(i0 + 3, YP)) - (fc + fc);
                 const T b = (F(i0 + 3, XP) + F(i0 + 3, YM)) - (fc + fc);
-                out[i0 + 3] = fc + (p * a + (qq * b + (t2 + s2)));
+                out[i0 + 3] = fc + (p * a + (qq * b + with_mixed((t2 + s2), e3)));
             }
         }
     }

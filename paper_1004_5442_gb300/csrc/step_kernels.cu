@@ -44,7 +44,7 @@ using namespace tma;
 // item separate a slot's read from its next write).  Totals are reduced per
 // warp and item (one partial per warp of each item, without a CTA barrier),
 // so the fixed-order final sum does not depend on which CTA took which item.
-template <class T, bool TOTALS, int NS, bool TSTORE, bool YWIN>
+template <class T, bool TOTALS, int NS, bool TSTORE, bool YWIN, bool XT>
 __device__ __forceinline__ void step_queue(const CUtensorMap* map_in, const CUtensorMap* map_out,
                                            const StepArgs<T>& a, unsigned char* smem_raw) {
     __shared__ int s_item[2];
@@ -63,8 +63,8 @@ __device__ __forceinline__ void step_queue(const CUtensorMap* map_in, const CUte
         const int nrows = min(a.rows_per_cta, L.ny - y0);
         bool bad = false;
         Acc<T> acc[4];
-        if (!strip_chunk<T, TOTALS, NS, TSTORE, YWIN>(R, map_in, map_out, L, a.per_x, a.per_y, a.out, a.k, x0, y0,
-                                                      nrows, bad, acc)) {
+        if (!strip_chunk<T, TOTALS, NS, TSTORE, YWIN, XT>(R, map_in, map_out, L, a.per_x, a.per_y, a.out, a.k, x0,
+                                                          y0, nrows, bad, acc)) {
             strip_drain<T, NS>(R, a.flag);
             return;
         }
@@ -74,13 +74,13 @@ __device__ __forceinline__ void step_queue(const CUtensorMap* map_in, const CUte
     }
 }
 
-template <class T, bool TOTALS, int NS, bool TSTORE, int MINB, bool YWIN, bool QUEUE>
+template <class T, bool TOTALS, int NS, bool TSTORE, int MINB, bool YWIN, bool QUEUE, bool XT>
 __global__ void __launch_bounds__(TMA_W, MINB) step_tma(const __grid_constant__ CUtensorMap map_in,
                                                         const __grid_constant__ CUtensorMap map_out,
                                                         const StepArgs<T> a) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     if (QUEUE) {
-        step_queue<T, TOTALS, NS, TSTORE, YWIN>(&map_in, &map_out, a, smem_raw);
+        step_queue<T, TOTALS, NS, TSTORE, YWIN, XT>(&map_in, &map_out, a, smem_raw);
         return;
     }
     const Layout& L = a.L;
@@ -91,8 +91,8 @@ __global__ void __launch_bounds__(TMA_W, MINB) step_tma(const __grid_constant__ 
     StripRing<T> R = strip_ring_init<T, NS, TSTORE>(smem_raw);
     bool bad = false;
     Acc<T> acc[4];
-    if (!strip_chunk<T, TOTALS, NS, TSTORE, YWIN>(R, &map_in, &map_out, L, a.per_x, a.per_y, a.out, a.k, x0, y0,
-                                                  nrows, bad, acc)) {
+    if (!strip_chunk<T, TOTALS, NS, TSTORE, YWIN, XT>(R, &map_in, &map_out, L, a.per_x, a.per_y, a.out, a.k, x0,
+                                                      y0, nrows, bad, acc)) {
         strip_drain<T, NS>(R, a.flag);
         return;
     }
@@ -112,7 +112,7 @@ constexpr int DIR_BX = 32;
 // most in FP64, where one SM retires only two FP64 lanes per clock.
 constexpr long kDirectMinBlocks = 304;
 
-template <class T, bool TOTALS, int BY>
+template <class T, bool TOTALS, int BY, bool XT>
 __global__ void __launch_bounds__(DIR_BX* BY) step_direct(const StepArgs<T> a) {
     const Layout& L = a.L;
     const int x = blockIdx.x * DIR_BX + threadIdx.x;
@@ -130,14 +130,19 @@ __global__ void __launch_bounds__(DIR_BX* BY) step_direct(const StepArgs<T> a) {
                 case XM: return __ldg(in + o - 1);
                 case XP: return __ldg(in + o + 1);
                 case YM: return __ldg(in + o - L.pitch);
-                default: return __ldg(in + o + L.pitch);
+                case YP: return __ldg(in + o + L.pitch);
+                case XPYP: return __ldg(in + o + L.pitch + 1);
+                case XPYM: return __ldg(in + o - L.pitch + 1);
+                case XMYP: return __ldg(in + o + L.pitch - 1);
+                default: return __ldg(in + o - L.pitch - 1);
             }
         };
         T out[NV];
         T rho, P;
-        cell_update<T>(F, a.k, out, rho, P);
+        cell_update<T, XT>(F, a.k, out, rho, P);
         bad = !healthy(rho, P);
         store_cell<T>(a.out, L, a.per_x, a.per_y, x, y, out);
+        if (XT) store_corners<T>(a.out, L, a.per_x, a.per_y, x, y, [&](int j) { return out[j]; });
         if (TOTALS) conserved_moments<T>(out, q[0], q[1], q[2], q[3]);
     }
     if (__syncthreads_or(bad) && threadIdx.x == 0 && threadIdx.y == 0) atomicOr(a.flag, FLAG_UNSTABLE);
@@ -147,34 +152,44 @@ __global__ void __launch_bounds__(DIR_BX* BY) step_direct(const StepArgs<T> a) {
     }
 }
 
-template <class T, int NS, bool TSTORE, int MINB, bool YWIN = false, bool QUEUE = false>
+template <class T, int NS, bool TSTORE, int MINB, bool YWIN = false, bool QUEUE = false, bool XT = false>
 struct TmaKernels {
     static cudaError_t launch(const CUtensorMap* mi, const CUtensorMap* mo, const StepArgs<T>& a, dim3 grid,
                               size_t smem, bool totals, cudaStream_t st) {
         if (totals)
-            step_tma<T, true, NS, TSTORE, MINB, YWIN, QUEUE><<<grid, TMA_W, smem, st>>>(*mi, *mo, a);
+            step_tma<T, true, NS, TSTORE, MINB, YWIN, QUEUE, XT><<<grid, TMA_W, smem, st>>>(*mi, *mo, a);
         else
-            step_tma<T, false, NS, TSTORE, MINB, YWIN, QUEUE><<<grid, TMA_W, smem, st>>>(*mi, *mo, a);
+            step_tma<T, false, NS, TSTORE, MINB, YWIN, QUEUE, XT><<<grid, TMA_W, smem, st>>>(*mi, *mo, a);
         return cudaGetLastError();
     }
     static cudaError_t occupancy(size_t smem, int* occ) {
         cudaError_t e;
-        if ((e = cudaFuncSetAttribute(step_tma<T, true, NS, TSTORE, MINB, YWIN, QUEUE>,
+        if ((e = cudaFuncSetAttribute(step_tma<T, true, NS, TSTORE, MINB, YWIN, QUEUE, XT>,
                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
             return e;
-        if ((e = cudaFuncSetAttribute(step_tma<T, false, NS, TSTORE, MINB, YWIN, QUEUE>,
+        if ((e = cudaFuncSetAttribute(step_tma<T, false, NS, TSTORE, MINB, YWIN, QUEUE, XT>,
                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
             return e;
-        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, step_tma<T, false, NS, TSTORE, MINB, YWIN, QUEUE>,
-                                                             TMA_W, smem);
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+            occ, step_tma<T, false, NS, TSTORE, MINB, YWIN, QUEUE, XT>, TMA_W, smem);
     }
 };
 
 // FP64 rings are capped at 4 rows (16.9 KB per row).
 template <class T, int NS> constexpr int ring_depth() { return sizeof(T) == 8 && NS > 4 ? 4 : NS; }
 
+// The unsplit operator (xt) reads rows r-1 and r+1 at x +- 1 from the ring:
+// tiles 1, 4 and 7, which keep row r-1 resident.
 template <class T, class Fn>
-cudaError_t with_tile(int tile, Fn&& fn) {
+cudaError_t with_tile(int tile, bool xt, Fn&& fn) {
+    if (xt) {
+        switch (tile) {
+            case 1: return fn(TmaKernels<T, ring_depth<T, 6>(), false, 4, false, false, true>());
+            case 4: return fn(TmaKernels<T, ring_depth<T, 5>(), true, (sizeof(T) == 8 ? 2 : 3), false, false, true>());
+            case 7: return fn(TmaKernels<T, ring_depth<T, 5>(), true, (sizeof(T) == 8 ? 2 : 3), false, true, true>());
+            default: return cudaErrorInvalidValue;
+        }
+    }
     switch (tile) {
         case 1: return fn(TmaKernels<T, ring_depth<T, 6>(), false, 4>());
         case 2: return fn(TmaKernels<T, ring_depth<T, 4>(), true, (sizeof(T) == 8 ? 2 : 4)>());
@@ -190,16 +205,18 @@ cudaError_t with_tile(int tile, Fn&& fn) {
 }  // namespace
 
 template <class T>
-cudaError_t launch_step_tma(int tile, const CUtensorMap* map_in, const CUtensorMap* map_out, const StepArgs<T>& a,
-                            int grid_x, int grid_y, bool totals, cudaStream_t st) {
+cudaError_t launch_step_tma(int tile, bool xt, const CUtensorMap* map_in, const CUtensorMap* map_out,
+                            const StepArgs<T>& a, int grid_x, int grid_y, bool totals, cudaStream_t st) {
     const size_t smem = tma_smem_bytes<T>(tile);
-    return with_tile<T>(tile, [&](auto k) { return k.launch(map_in, map_out, a, dim3(grid_x, grid_y), smem, totals, st); });
+    return with_tile<T>(tile, xt, [&](auto k) {
+        return k.launch(map_in, map_out, a, dim3(grid_x, grid_y), smem, totals, st);
+    });
 }
 
 template <class T>
-cudaError_t tma_occupancy(int tile, int* blocks_per_sm) {
+cudaError_t tma_occupancy(int tile, bool xt, int* blocks_per_sm) {
     const size_t smem = tma_smem_bytes<T>(tile);
-    return with_tile<T>(tile, [&](auto k) { return k.occupancy(smem, blocks_per_sm); });
+    return with_tile<T>(tile, xt, [&](auto k) { return k.occupancy(smem, blocks_per_sm); });
 }
 
 template <class T>
@@ -211,35 +228,41 @@ void direct_grid(const Layout& L, dim3* grid, dim3* block) {
     *grid = dim3((unsigned)bx, (L.ny + by - 1) / by);
 }
 
-template <class T, int BY>
+template <class T, int BY, bool XT>
 static void launch_direct_by(const StepArgs<T>& a, bool totals, dim3 grid, cudaStream_t st) {
     if (totals)
-        step_direct<T, true, BY><<<grid, dim3(DIR_BX, BY), 0, st>>>(a);
+        step_direct<T, true, BY, XT><<<grid, dim3(DIR_BX, BY), 0, st>>>(a);
     else
-        step_direct<T, false, BY><<<grid, dim3(DIR_BX, BY), 0, st>>>(a);
+        step_direct<T, false, BY, XT><<<grid, dim3(DIR_BX, BY), 0, st>>>(a);
+}
+
+template <class T, bool XT>
+static void launch_direct_xt(const StepArgs<T>& a, bool totals, dim3 grid, int by, cudaStream_t st) {
+    switch (by) {
+        case 8: launch_direct_by<T, 8, XT>(a, totals, grid, st); break;
+        case 4: launch_direct_by<T, 4, XT>(a, totals, grid, st); break;
+        case 2: launch_direct_by<T, 2, XT>(a, totals, grid, st); break;
+        default: launch_direct_by<T, 1, XT>(a, totals, grid, st); break;
+    }
 }
 
 template <class T>
-cudaError_t launch_step_direct(const StepArgs<T>& a, bool totals, cudaStream_t st) {
+cudaError_t launch_step_direct(const StepArgs<T>& a, bool xt, bool totals, cudaStream_t st) {
     dim3 grid, block;
     direct_grid<T>(a.L, &grid, &block);
-    switch (block.y) {
-        case 8: launch_direct_by<T, 8>(a, totals, grid, st); break;
-        case 4: launch_direct_by<T, 4>(a, totals, grid, st); break;
-        case 2: launch_direct_by<T, 2>(a, totals, grid, st); break;
-        default: launch_direct_by<T, 1>(a, totals, grid, st); break;
-    }
+    if (xt) launch_direct_xt<T, true>(a, totals, grid, (int)block.y, st);
+    else launch_direct_xt<T, false>(a, totals, grid, (int)block.y, st);
     return cudaGetLastError();
 }
 
-template cudaError_t launch_step_tma<float>(int, const CUtensorMap*, const CUtensorMap*,
+template cudaError_t launch_step_tma<float>(int, bool, const CUtensorMap*, const CUtensorMap*,
                                             const StepArgs<float>&, int, int, bool, cudaStream_t);
-template cudaError_t launch_step_tma<double>(int, const CUtensorMap*, const CUtensorMap*,
+template cudaError_t launch_step_tma<double>(int, bool, const CUtensorMap*, const CUtensorMap*,
                                              const StepArgs<double>&, int, int, bool, cudaStream_t);
-template cudaError_t launch_step_direct<float>(const StepArgs<float>&, bool, cudaStream_t);
-template cudaError_t launch_step_direct<double>(const StepArgs<double>&, bool, cudaStream_t);
-template cudaError_t tma_occupancy<float>(int, int*);
-template cudaError_t tma_occupancy<double>(int, int*);
+template cudaError_t launch_step_direct<float>(const StepArgs<float>&, bool, bool, cudaStream_t);
+template cudaError_t launch_step_direct<double>(const StepArgs<double>&, bool, bool, cudaStream_t);
+template cudaError_t tma_occupancy<float>(int, bool, int*);
+template cudaError_t tma_occupancy<double>(int, bool, int*);
 template void direct_grid<float>(const Layout&, dim3*, dim3*);
 template void direct_grid<double>(const Layout&, dim3*, dim3*);
 

@@ -129,6 +129,34 @@ __device__ __forceinline__ void store_cell(T* __restrict__ out, const Layout& L,
     }
 }
 
+// Unsplit operator only: the corner ghosts that the step itself refreshes
+// (both axes periodic or reflecting), written by the cell whose ghost-column
+// copy they repeat along y.  A corner holds what the ghost-row rule gives
+// when applied to the ghost column: the wrapped row on a periodic y axis,
+// row 0 of the column with mirrored velocities behind a reflecting y wall.
+// Corners beyond a fixed end never change (set at creation).  v(i) is the
+// cell's output of plane i.
+template <class T, class V>
+__device__ __forceinline__ void store_corners(T* __restrict__ out, const Layout& L, int per_x, int per_y, int x,
+                                              int y, const V& v) {
+    long col = -1;
+    bool mx = false;
+    if (per_x) col = x == 0 ? L.G + L.nx : (x == L.nx - 1 ? L.G - 1 : -1);
+    else if (L.refl_x && x == 0) { col = L.G - 1; mx = true; }
+    if (col < 0) return;
+    long row = -1;
+    bool my = false;
+    if (per_y) row = y == 0 ? L.ny + 1 : (y == L.ny - 1 ? 0 : -1);
+    else if (L.refl_y && y == 0) { row = 0; my = true; }
+    if (row < 0) return;
+#pragma unroll
+    for (int i = 0; i < NV; ++i) {
+        const int j = mx ? (my ? mirror_plane(mirror_plane(i, 1), 0) : mirror_plane(i, 0))
+                         : (my ? mirror_plane(i, 1) : i);
+        out[i * L.plane + row * L.pitch + col] = v(j);
+    }
+}
+
 // --------------------------------------------------------------------------
 // TMA-staged strip kernel.
 // --------------------------------------------------------------------------
@@ -155,10 +183,13 @@ struct StripRing {
 // [y0, y0+nrows) of the field described by L, read through map_in and
 // written to out (map_out for whole-strip TMA row stores).  Returns false if
 // a bounded wait ran out (the caller drains and flags).
-template <class T, bool TOTALS, int NS, bool TSTORE, bool YWIN, class CoefT>
+// XT: the unsplit operator (diagonal neighbours from rows r-1 and r+1 of the
+// ring, so not with YWIN).
+template <class T, bool TOTALS, int NS, bool TSTORE, bool YWIN, bool XT = false, class CoefT>
 __device__ __forceinline__ bool strip_chunk(StripRing<T>& R, const CUtensorMap* map_in, const CUtensorMap* map_out,
                                             const Layout& L, int per_x, int per_y, T* __restrict__ out,
                                             const CoefT& k, int x0, int y0, int nrows, bool& bad, Acc<T>* acc) {
+    static_assert(!(XT && YWIN), "the unsplit operator reads row r-1 from the ring");
     constexpr int HALO = tma_halo<T>();
     constexpr int BOXW = tma_boxw<T>();
     constexpr uint32_t SLOT_BYTES = (uint32_t)tma_slot_bytes<T>();
@@ -236,12 +267,16 @@ __device__ __forceinline__ bool strip_chunk(StripRing<T>& R, const CUtensorMap* 
                     case XM: return sc[i * BOXW + col - 1];
                     case XP: return sc[i * BOXW + col + 1];
                     case YM: return YWIN ? ym[i] : sm[i * BOXW + col];
-                    default: return YWIN ? yp[i] : sp[i * BOXW + col];
+                    case YP: return YWIN ? yp[i] : sp[i * BOXW + col];
+                    case XPYP: return sp[i * BOXW + col + 1];
+                    case XPYM: return sm[i * BOXW + col + 1];
+                    case XMYP: return sp[i * BOXW + col - 1];
+                    default: return sm[i * BOXW + col - 1];
                 }
             };
             T o[NV];
             T rho, P;
-            cell_update<T>(F, k, o, rho, P);
+            cell_update<T, XT>(F, k, o, rho, P);
             if (YWIN) {
 #pragma unroll
                 for (int i = 0; i < NV; ++i) {
@@ -255,6 +290,7 @@ __device__ __forceinline__ bool strip_chunk(StripRing<T>& R, const CUtensorMap* 
                 for (int i = 0; i < NV; ++i) ob[i * TMA_W + tid] = o[i];
             } else {
                 store_cell<T>(out, L, per_x, per_y, x, y, o);
+                if (XT) store_corners<T>(out, L, per_x, per_y, x, y, [&](int j) { return o[j]; });
             }
             if (TOTALS) {
                 T q0, q1, q2, q3;
@@ -312,6 +348,7 @@ __device__ __forceinline__ bool strip_chunk(StripRing<T>& R, const CUtensorMap* 
 #pragma unroll 4
                 for (int i = 0; i < NV; ++i) out[i * L.plane + L.G + x] = ob[mirror_plane(i, 1) * TMA_W + tid];
             }
+            if (XT && active) store_corners<T>(out, L, per_x, per_y, x, y, [&](int j) { return ob[j * TMA_W + tid]; });
         }
     }
     if (tstore && tid == 0) bulk_wait_all();
