@@ -385,6 +385,10 @@ def run_ours(args):
     # diagonal velocities), same workload and timing, FP32 and FP64
     if not args.no_lw2d:
         line["lw2d"] = unsplit_operator(Bd, w, torch, stream, args, peak)
+        if not args.no_adjoint:
+            line["lw2d"]["adjoint"] = adjoint_costs(
+                Bd, W, torch, stream, advection=Bd.ADV_LW2D,
+                cases=[("smooth_vortex_512x512_fp32", W.smooth_vortex(n=512, nsteps=500), 500, 50)])
 
     # adjoint / forward cost (smooth vortex 512^2, 500 FP32 steps, checkpoints
     # every 50; and the 4096^2 workload for the HBM-bound ratio)
@@ -438,17 +442,18 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
-def adjoint_costs(Bd, W, torch, stream):
+def adjoint_costs(Bd, W, torch, stream, advection=0, cases=None):
     """Forward vs recorded-forward vs reverse-sweep time per step."""
     out = {}
-    cases = [("smooth_vortex_512x512_fp32", W.smooth_vortex(n=512, nsteps=500), 500, 50),
-             ("kelvin_helmholtz_4096x4096_fp32", W.kelvin_helmholtz(n=4096, nsteps=40), 40, 10)]
+    if cases is None:
+        cases = [("smooth_vortex_512x512_fp32", W.smooth_vortex(n=512, nsteps=500), 500, 50),
+                 ("kelvin_helmholtz_4096x4096_fp32", W.kelvin_helmholtz(n=4096, nsteps=40), 40, 10)]
     for name, w, nsteps, ck in cases:
         with torch.cuda.stream(stream):
             fields = [torch.tensor(np.ascontiguousarray(a), device="cuda") for a in (w.rho, w.ux, w.uy, w.T)]
             dL = torch.full((w.ny, w.nx), w.dx * w.dx, dtype=torch.float64, device="cuda")
             outs = [torch.empty_like(dL) for _ in range(4)]
-        g = Bd.Grid.from_workload(w, precision=Bd.FP32, stream=stream.cuda_stream)
+        g = Bd.Grid.from_workload(w, precision=Bd.FP32, stream=stream.cuda_stream, advection=advection)
         e = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
         g.step(5)
         torch.cuda.synchronize()

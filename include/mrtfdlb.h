@@ -81,7 +81,7 @@ typedef enum mrt_kernel { MRT_KERNEL_AUTO = 0, MRT_KERNEL_TMA = 1, MRT_KERNEL_DI
  * (second order in time for those velocities; the split form is first order
  * there).  Beyond two fixed ends the corner ghost holds the corner cell's
  * initial f.  MRT_ADV_LW2D runs on the direct kernel and on TMA tiles 0, 1,
- * 4 and 7; the reverse mode and batches take MRT_ADV_LW only. */
+ * 4 and 7, forward and in reverse mode; batches take MRT_ADV_LW only. */
 typedef enum mrt_advection { MRT_ADV_LW = 0, MRT_ADV_LW2D = 1 } mrt_advection;
 
 typedef struct mrt_params {

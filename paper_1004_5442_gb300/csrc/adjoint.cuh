@@ -122,6 +122,12 @@ __device__ __forceinline__ void butterfly(int g, const T* v, T& S, T& Dx, T& Dy,
     else { Dx = d02 - d13; Dy = d02 + d13; }
 }
 
+// |c_x c_y| / 4 of diagonal group g (2 or 3); 0 on the axis groups.
+template <class T>
+__device__ __forceinline__ T k_xy(const Coef<T>& k, int g) {
+    return g >= 2 ? k.kxy[g - 2] : (T)0;
+}
+
 // Forward Lax-Wendroff weight that plane i puts on its neighbour at pos
 // (the weight multiplies (f_pos - f_centre)).
 template <class T>
@@ -142,8 +148,10 @@ __device__ __forceinline__ T lw_weight(const Coef<T>& k, int i, int pos) {
 // One cell of the reverse step.  LF(i, pos) reads lam = dL/df^{n+1} on the
 // stencil (ghost values of fixed axes are zero), f[] is f^n at the cell.
 // Writes lam_out = dL/df^n at the cell and adds -mu_k (m_k - m^eq_k) to
-// gsig[k-5].
-template <class T, class LFetch>
+// gsig[k-5].  XT: the unsplit operator; its mixed term is symmetric (the
+// weight on f(x+a, y+b) is c_x c_y a b / 4 = the weight on f(x-a, y-b)), so
+// its transpose is the same term applied to lam.
+template <class T, bool XT = false, class LFetch>
 __device__ __forceinline__ void cell_adjoint(const LFetch& LF, const T f[NV], const Coef<T>& k, T lam_out[NV],
                                              T gsig[12]) {
     // ---- forward moments and equilibria of f^n ----------------------------
@@ -271,6 +279,11 @@ __device__ __forceinline__ void cell_adjoint(const LFetch& LF, const T f[NV], co
             } else {
                 t += wxm * (LF(i, XP) - lcen) + wxp * (LF(i, XM) - lcen);
                 t += wym * (LF(i, YP) - lcen) + wyp * (LF(i, YM) - lcen);
+                if constexpr (XT) {
+                    // c_x c_y > 0 for (+,+) and (-,-), < 0 for (-,+) and (+,-)
+                    const T wxy = (mm == 0 || mm == 2) ? k.kxy[g - 2] : -k.kxy[g - 2];
+                    t += wxy * ((LF(i, XPYP) - LF(i, XPYM)) - (LF(i, XMYP) - LF(i, XMYM)));
+                }
             }
             lam_out[i] = lcen + t;
         }

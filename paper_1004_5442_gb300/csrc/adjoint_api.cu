@@ -49,7 +49,6 @@ extern "C" mrt_status mrt_adjoint_record(mrt_grid* g, const double* rho0, const 
     if (!g) return mrt_fail(MRT_EINVAL, "grid is NULL");
     if (nsteps < 1) return mrt_fail(MRT_EINVAL, "nsteps must be >= 1");
     if (ckpt_every < 1) return mrt_fail(MRT_EINVAL, "ckpt_every must be >= 1");
-    if (g->xt) return mrt_fail(MRT_EINVAL, "the reverse mode takes the axis-by-axis operator (MRT_ADV_LW)");
     if (!rho0 || !ux0 || !uy0 || !T0) return mrt_fail(MRT_EINVAL, "null field pointer");
     mrt_tape_free(g->tape);
     g->tape = nullptr;
@@ -67,7 +66,7 @@ extern "C" mrt_status mrt_adjoint_record(mrt_grid* g, const double* rho0, const 
     if (g->kernel == MRT_KERNEL_TMA) {
         // TMA reverse step: its own occupancy decides the row chunks
         int occ = 0, sms = 0;
-        cudaError_t e = g->fp64 ? adjoint_tma_setup<double>(&occ) : adjoint_tma_setup<float>(&occ);
+        cudaError_t e = g->fp64 ? adjoint_tma_setup<double>(g->xt, &occ) : adjoint_tma_setup<float>(g->xt, &occ);
         if (e != cudaSuccess) return mrt_fail(MRT_ECUDA, "adjoint occupancy: %s", cudaGetErrorString(e));
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, g->device);
         if (occ < 1) occ = 1;
@@ -176,10 +175,11 @@ static mrt_status backward_impl(mrt_grid* g, const double* drho, double* outs[4]
             a.f = reinterpret_cast<const T*>(buf_at(t->seg, t->state_bytes, j));
             a.lam_out = static_cast<T*>(t->lam[cur ^ 1]);
             if (t->adj_tma)
-                A_TRY(launch_adjoint_tma<T>(&t->lam_in[cur], &t->seg_in[j], &t->lam_out[cur ^ 1], a, t->adj_gx,
+                A_TRY(launch_adjoint_tma<T>(&t->lam_in[cur], &t->seg_in[j], &t->lam_out[cur ^ 1], a, g->xt, t->adj_gx,
                                             t->adj_gy, t->adj_rows, g->stream));
             else
-                A_TRY(launch_adjoint_step<T>(a, g->stream));
+                A_TRY(launch_adjoint_step<T>(a, g->xt, g->stream));
+            if (g->xt) A_TRY(launch_ghost_gather_xt<T>(a, g->stream));
             cur ^= 1;
         }
     }
@@ -273,7 +273,9 @@ static mrt_status adjoint_step_impl(mrt_grid* g, const void* f, const void* lam_
     a.gpart = gpart;
     if constexpr (sizeof(T) == 8) a.k = g->kd; else a.k = g->kf;
     a.flag = g->flag;
-    if ((e = launch_adjoint_step<T>(a, g->stream)) == cudaSuccess) e = launch_sum_partials(gpart, nparts, sums, g->stream);
+    if ((e = launch_adjoint_step<T>(a, g->xt, g->stream)) == cudaSuccess && g->xt)
+        e = launch_ghost_gather_xt<T>(a, g->stream);
+    if (e == cudaSuccess) e = launch_sum_partials(gpart, nparts, sums, g->stream);
     for (int i = 0; i < 16 && e == cudaSuccess; ++i) {
         const size_t off = ((size_t)i * g->L.plane + g->L.pitch + g->L.G) * g->elem;
         const size_t uoff = (size_t)i * g->L.nx * g->L.ny * g->elem;
@@ -293,7 +295,6 @@ extern "C" mrt_status mrt_adjoint_step(mrt_grid* g, const void* f, const void* l
                                        double g_s[16]) {
     if (!g) return mrt_fail(MRT_EINVAL, "grid is NULL");
     if (!f || !lam_next || !lam) return mrt_fail(MRT_EINVAL, "null state pointer");
-    if (g->xt) return mrt_fail(MRT_EINVAL, "the reverse mode takes the axis-by-axis operator (MRT_ADV_LW)");
     return g->fp64 ? adjoint_step_impl<double>(g, f, lam_next, lam, on_device, g_s)
                    : adjoint_step_impl<float>(g, f, lam_next, lam, on_device, g_s);
 }

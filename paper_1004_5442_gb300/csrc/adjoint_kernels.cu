@@ -9,6 +9,7 @@
 //   sum_partials   fixed-order sum of the per-block rate partials
 #include "adjoint.cuh"
 #include "internal.h"
+#include "step_strip.cuh"
 #include "tma.cuh"
 
 namespace mrt {
@@ -42,7 +43,9 @@ __device__ __forceinline__ void store_plain(T* __restrict__ out, const Layout& L
     }
 }
 
-template <class T>
+// XT: the unsplit operator.  Its fixed-ghost adjoints are gathered by
+// ghost_gather_xt_kernel after the step instead of accumulated here.
+template <class T, bool XT>
 __global__ void __launch_bounds__(ABX* ABY) adjoint_step_kernel(AdjArgs<T> a) {
     const Layout& L = a.L;
     const int x = blockIdx.x * ABX + threadIdx.x;
@@ -60,25 +63,30 @@ __global__ void __launch_bounds__(ABX* ABY) adjoint_step_kernel(AdjArgs<T> a) {
                 case XM: return __ldg(lam + o - 1);
                 case XP: return __ldg(lam + o + 1);
                 case YM: return __ldg(lam + o - L.pitch);
-                default: return __ldg(lam + o + L.pitch);
+                case YP: return __ldg(lam + o + L.pitch);
+                case XPYP: return __ldg(lam + o + L.pitch + 1);
+                case XPYM: return __ldg(lam + o - L.pitch + 1);
+                case XMYP: return __ldg(lam + o + L.pitch - 1);
+                default: return __ldg(lam + o - L.pitch - 1);
             }
         };
         T f[NV];
 #pragma unroll
         for (int i = 0; i < NV; ++i) f[i] = __ldg(a.f + i * L.plane + base);
         T out[NV];
-        cell_adjoint<T>(LF, f, a.k, out, gs);
+        cell_adjoint<T, XT>(LF, f, a.k, out, gs);
         store_plain<T, true>(a.lam_out, L, a.per_x, a.per_y, x, y, out);
+        if (XT) store_corners<T>(a.lam_out, L, a.per_x, a.per_y, x, y, [&](int j) { return out[j]; });
         // a fixed ghost beyond an edge cell received the forward weight of
         // that neighbour position; accumulate its adjoint (one writer each)
-        if (!a.per_x && ((x == 0 && !L.refl_x) || x == L.nx - 1)) {
+        if (!XT && !a.per_x && ((x == 0 && !L.refl_x) || x == L.nx - 1)) {
             const int side = x == 0 ? 0 : 1;
             for (int i = 0; i < NV; ++i) {
                 const T wgt = lw_weight<T>(a.k, i, side == 0 ? XM : XP);
                 a.gxb[((long)i * 2 + side) * L.ny + y] += (double)(wgt * LF(i, C));
             }
         }
-        if (!a.per_y && ((y == 0 && !L.refl_y) || y == L.ny - 1)) {
+        if (!XT && !a.per_y && ((y == 0 && !L.refl_y) || y == L.ny - 1)) {
             const int side = y == 0 ? 0 : 1;
             for (int i = 0; i < NV; ++i) {
                 const T wgt = lw_weight<T>(a.k, i, side == 0 ? YM : YP);
@@ -120,7 +128,7 @@ constexpr size_t adj_tma_smem() {
     return (ADJ_NSL + ADJ_NSF) * tma_slot_bytes<T>() + 2 * tma_out_slot_bytes<T>() + 128;
 }
 
-template <class T>
+template <class T, bool XT>
 __global__ void __launch_bounds__(TMA_W) adjoint_tma_kernel(const __grid_constant__ CUtensorMap map_lam,
                                                             const __grid_constant__ CUtensorMap map_f,
                                                             const __grid_constant__ CUtensorMap map_out,
@@ -215,22 +223,26 @@ __global__ void __launch_bounds__(TMA_W) adjoint_tma_kernel(const __grid_constan
                     case XM: return sc[i * BOXW + col - 1];
                     case XP: return sc[i * BOXW + col + 1];
                     case YM: return sm[i * BOXW + col];
-                    default: return sp[i * BOXW + col];
+                    case YP: return sp[i * BOXW + col];
+                    case XPYP: return sp[i * BOXW + col + 1];
+                    case XPYM: return sm[i * BOXW + col + 1];
+                    case XMYP: return sp[i * BOXW + col - 1];
+                    default: return sm[i * BOXW + col - 1];
                 }
             };
             T f[NV];
 #pragma unroll
             for (int i = 0; i < NV; ++i) f[i] = sf[i * BOXW + col];
             T out[NV];
-            cell_adjoint<T>(LF, f, a.k, out, gs);
+            cell_adjoint<T, XT>(LF, f, a.k, out, gs);
 #pragma unroll
             for (int i = 0; i < NV; ++i) ob[i * TMA_W + tid] = out[i];
-            if (!a.per_x && ((x == 0 && !L.refl_x) || x == L.nx - 1)) {
+            if (!XT && !a.per_x && ((x == 0 && !L.refl_x) || x == L.nx - 1)) {
                 const int side = x == 0 ? 0 : 1;
                 for (int i = 0; i < NV; ++i)
                     a.gxb[((long)i * 2 + side) * L.ny + y] += (double)(lw_weight<T>(a.k, i, side == 0 ? XM : XP) * LF(i, C));
             }
-            if (!a.per_y && ((y == 0 && !L.refl_y) || y == L.ny - 1)) {
+            if (!XT && !a.per_y && ((y == 0 && !L.refl_y) || y == L.ny - 1)) {
                 const int side = y == 0 ? 0 : 1;
                 for (int i = 0; i < NV; ++i)
                     a.gyb[((long)i * 2 + side) * L.nx + x] += (double)(lw_weight<T>(a.k, i, side == 0 ? YM : YP) * LF(i, C));
@@ -277,6 +289,8 @@ __global__ void __launch_bounds__(TMA_W) adjoint_tma_kernel(const __grid_constan
 #pragma unroll 4
             for (int i = 0; i < NV; ++i) a.lam_out[i * L.plane + L.G + x] = ob[mirror_plane(i, 1) * TMA_W + tid];
         }
+        if (XT && active)
+            store_corners<T>(a.lam_out, L, a.per_x, a.per_y, x, y, [&](int j) { return ob[j * TMA_W + tid]; });
     }
     if (tid == 0) bulk_wait_all();
 
@@ -294,6 +308,75 @@ __global__ void __launch_bounds__(TMA_W) adjoint_tma_kernel(const __grid_constan
         double s = 0;
         for (int w = 0; w < TMA_W / 32; ++w) s += red[w][tid];
         a.gpart[(long)(blockIdx.y * gridDim.x + blockIdx.x) * 12 + tid] += s;
+    }
+}
+
+// Unsplit operator: adjoints of the fixed ghost values, gathered from every
+// read of each value in the forward step, one thread per value (one writer,
+// fixed order).  An x ghost (plane i, side, row) is read by the edge cell of
+// its row through the Lax-Wendroff neighbour, and through the mixed term by
+// the edge cells of the rows above and below, the other axis mapped as the
+// forward fetch maps it: wrapped (periodic y), clamped to the edge row (a
+// fixed y end: the corner holds the corner cell's f), or mirrored (a y wall:
+// velocity m1(i) of the edge cell reads plane i of the x ghost at row 0).  A
+// y ghost likewise, except that a read beyond a fixed x end is an x ghost
+// read (x is mapped first).  Added to gxb / gyb, whose layout is that of the
+// per-cell accumulation of the axis-by-axis operator.
+template <class T>
+__global__ void ghost_gather_xt_kernel(AdjArgs<T> a) {
+    const Layout& L = a.L;
+    const long nxg = a.per_x ? 0 : 32L * L.ny, nyg = a.per_y ? 0 : 32L * L.nx;
+    const long t = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    auto lam = [&](int i, int x, int y) -> T { return a.lam_in[i * L.plane + (long)(y + 1) * L.pitch + L.G + x]; };
+    // mixed-term weight of plane j on its neighbour (x + dx, y + dy)
+    auto wmix = [&](int j, int dx, int dy) -> T {
+        const int m = j & 3;
+        const T w = k_xy(a.k, j >> 2);
+        return ((m == 0 || m == 2) ? w : -w) * (T)(dx * dy);
+    };
+    if (t < nxg) {
+        const int i = (int)(t / (2L * L.ny)), side = (int)((t / L.ny) % 2), row = (int)(t % L.ny);
+        if (side == 0 && L.refl_x) return;  // a wall holds no ghost value
+        const int xb = side == 0 ? 0 : L.nx - 1, dx = side == 0 ? -1 : 1;
+        T acc = lw_weight<T>(a.k, i, side == 0 ? XM : XP) * lam(i, xb, row);
+        if (i >= 8) {
+            for (int dy = -1; dy <= 1; dy += 2) {
+                const int y = row - dy;  // inside: (xb, y) reads row y + dy = row
+                if (y >= 0 && y < L.ny) acc += wmix(i, dx, dy) * lam(i, xb, y);
+            }
+            // reads beyond a y end that map onto this row
+            if (a.per_y) {
+                if (row == L.ny - 1) acc += wmix(i, dx, -1) * lam(i, xb, 0);
+                if (row == 0) acc += wmix(i, dx, 1) * lam(i, xb, L.ny - 1);
+            } else {
+                if (row == 0) {
+                    const int j = L.refl_y ? mirror_plane(i, 1) : i;
+                    acc += wmix(j, dx, -1) * lam(j, xb, 0);
+                }
+                if (row == L.ny - 1) acc += wmix(i, dx, 1) * lam(i, xb, L.ny - 1);
+            }
+        }
+        a.gxb[t] += (double)acc;
+    } else if (t < nxg + nyg) {
+        const long u = t - nxg;
+        const int i = (int)(u / (2L * L.nx)), side = (int)((u / L.nx) % 2), c = (int)(u % L.nx);
+        if (side == 0 && L.refl_y) return;
+        const int yb = side == 0 ? 0 : L.ny - 1, dy = side == 0 ? -1 : 1;
+        T acc = lw_weight<T>(a.k, i, side == 0 ? YM : YP) * lam(i, c, yb);
+        if (i >= 8) {
+            for (int dx = -1; dx <= 1; dx += 2) {
+                const int x = c - dx;
+                if (x >= 0 && x < L.nx) acc += wmix(i, dx, dy) * lam(i, x, yb);
+            }
+            if (a.per_x) {
+                if (c == L.nx - 1) acc += wmix(i, -1, dy) * lam(i, 0, yb);
+                if (c == 0) acc += wmix(i, 1, dy) * lam(i, L.nx - 1, yb);
+            } else if (L.refl_x && c == 0) {
+                const int j = mirror_plane(i, 0);
+                acc += wmix(j, -1, dy) * lam(j, 0, yb);
+            }
+        }
+        a.gyb[u] += (double)acc;
     }
 }
 
@@ -412,10 +495,19 @@ void adjoint_grid(const Layout& L, dim3* grid, dim3* block) {
 }
 
 template <class T>
-cudaError_t launch_adjoint_step(const AdjArgs<T>& a, cudaStream_t st) {
+cudaError_t launch_adjoint_step(const AdjArgs<T>& a, bool xt, cudaStream_t st) {
     dim3 grid, block;
     adjoint_grid<T>(a.L, &grid, &block);
-    adjoint_step_kernel<T><<<grid, block, 0, st>>>(a);
+    if (xt) adjoint_step_kernel<T, true><<<grid, block, 0, st>>>(a);
+    else adjoint_step_kernel<T, false><<<grid, block, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+template <class T>
+cudaError_t launch_ghost_gather_xt(const AdjArgs<T>& a, cudaStream_t st) {
+    const long n = (a.per_x ? 0 : 32L * a.L.ny) + (a.per_y ? 0 : 32L * a.L.nx);
+    if (n == 0) return cudaSuccess;
+    ghost_gather_xt_kernel<T><<<blocks_for(n, 256), 256, 0, st>>>(a);
     return cudaGetLastError();
 }
 
@@ -452,19 +544,31 @@ cudaError_t launch_init_adjoint(const Layout& L, const InitCoef& ic, const Coef<
     return cudaGetLastError();
 }
 
-template <class T>
-cudaError_t adjoint_tma_setup(int* blocks_per_sm) {
+template <class T, bool XT>
+static cudaError_t adjoint_tma_setup_xt(int* blocks_per_sm) {
     const size_t smem = adj_tma_smem<T>();
-    cudaError_t e = cudaFuncSetAttribute(adjoint_tma_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(adjoint_tma_kernel<T, XT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
     if (e != cudaSuccess) return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, adjoint_tma_kernel<T>, TMA_W, smem);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, adjoint_tma_kernel<T, XT>, TMA_W, smem);
+}
+
+template <class T>
+cudaError_t adjoint_tma_setup(bool xt, int* blocks_per_sm) {
+    return xt ? adjoint_tma_setup_xt<T, true>(blocks_per_sm) : adjoint_tma_setup_xt<T, false>(blocks_per_sm);
 }
 
 template <class T>
 cudaError_t launch_adjoint_tma(const CUtensorMap* map_lam, const CUtensorMap* map_f, const CUtensorMap* map_out,
-                               const AdjArgs<T>& a, int grid_x, int grid_y, int rows_per_cta, cudaStream_t st) {
-    adjoint_tma_kernel<T><<<dim3(grid_x, grid_y), TMA_W, adj_tma_smem<T>(), st>>>(*map_lam, *map_f, *map_out, a,
-                                                                                  rows_per_cta);
+                               const AdjArgs<T>& a, bool xt, int grid_x, int grid_y, int rows_per_cta,
+                               cudaStream_t st) {
+    const dim3 grid(grid_x, grid_y);
+    if (xt)
+        adjoint_tma_kernel<T, true><<<grid, TMA_W, adj_tma_smem<T>(), st>>>(*map_lam, *map_f, *map_out, a,
+                                                                           rows_per_cta);
+    else
+        adjoint_tma_kernel<T, false><<<grid, TMA_W, adj_tma_smem<T>(), st>>>(*map_lam, *map_f, *map_out, a,
+                                                                            rows_per_cta);
     return cudaGetLastError();
 }
 
@@ -474,11 +578,12 @@ cudaError_t launch_sum_partials(const double* gpart, int nparts, double* out, cu
 }
 
 #define INST(T)                                                                                                 \
-    template cudaError_t adjoint_tma_setup<T>(int*);                                                            \
+    template cudaError_t adjoint_tma_setup<T>(bool, int*);                                                      \
     template cudaError_t launch_adjoint_tma<T>(const CUtensorMap*, const CUtensorMap*, const CUtensorMap*,      \
-                                               const AdjArgs<T>&, int, int, int, cudaStream_t);                 \
+                                               const AdjArgs<T>&, bool, int, int, int, cudaStream_t);           \
     template void adjoint_grid<T>(const Layout&, dim3*, dim3*);                                                 \
-    template cudaError_t launch_adjoint_step<T>(const AdjArgs<T>&, cudaStream_t);                               \
+    template cudaError_t launch_adjoint_step<T>(const AdjArgs<T>&, bool, cudaStream_t);                         \
+    template cudaError_t launch_ghost_gather_xt<T>(const AdjArgs<T>&, cudaStream_t);                            \
     template cudaError_t launch_lam_from_drho<T>(const Layout&, const double*, T*, cudaStream_t);               \
     template cudaError_t launch_ghost_adjoint<T>(const Layout&, int, int, const double*, const double*, T*,     \
                                                  cudaStream_t);                                                 \

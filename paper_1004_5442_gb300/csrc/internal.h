@@ -147,8 +147,12 @@ struct AdjArgs {
 
 template <class T>
 void adjoint_grid(const Layout& L, dim3* grid, dim3* block);
+// xt: the unsplit operator (its fixed-ghost adjoints then come from
+// launch_ghost_gather_xt, run after each reverse step).
 template <class T>
-cudaError_t launch_adjoint_step(const AdjArgs<T>& a, cudaStream_t st);
+cudaError_t launch_adjoint_step(const AdjArgs<T>& a, bool xt, cudaStream_t st);
+template <class T>
+cudaError_t launch_ghost_gather_xt(const AdjArgs<T>& a, cudaStream_t st);
 template <class T>
 cudaError_t launch_lam_from_drho(const Layout& L, const double* drho, T* lam, cudaStream_t st);
 template <class T>
@@ -160,10 +164,11 @@ cudaError_t launch_init_adjoint(const Layout& L, const InitCoef& ic, const Coef<
                                 double* g_rho, double* g_ux, double* g_uy, double* g_T, cudaStream_t st);
 cudaError_t launch_sum_partials(const double* gpart, int nparts, double* out, cudaStream_t st);
 template <class T>
-cudaError_t adjoint_tma_setup(int* blocks_per_sm);
+cudaError_t adjoint_tma_setup(bool xt, int* blocks_per_sm);
 template <class T>
 cudaError_t launch_adjoint_tma(const CUtensorMap* map_lam, const CUtensorMap* map_f, const CUtensorMap* map_out,
-                               const AdjArgs<T>& a, int grid_x, int grid_y, int rows_per_cta, cudaStream_t st);
+                               const AdjArgs<T>& a, bool xt, int grid_x, int grid_y, int rows_per_cta,
+                               cudaStream_t st);
 
 }  // namespace mrt
 

@@ -8,8 +8,9 @@ max|f| for one step from the GPU's own state and 1e-5 relative on smooth
 flow.  Cases span ragged 128-column strips, every boundary combination
 (the corner ghosts beyond two non-periodic ends included), the kernels that
 run it (direct; TMA tiles 1, 4 and 7; the automatic choice), the queue tile
-on a grid with enough work items, and the rejection of the combinations
-that do not take it."""
+on a grid with enough work items, the rejection of the combinations that
+do not take it, and the reverse mode (one reverse step and whole-run
+gradients against the oracle's reverse mode of the same operator)."""
 import numpy as np
 import pytest
 
@@ -145,7 +146,95 @@ def test_rejected_combinations():
     with pytest.raises(Bd.MrtError) as ei:
         Bd.Grid.from_workload(w, precision=Bd.FP32, advection=2)
     assert ei.value.code == Bd.MRT_EINVAL
-    with _gpu(w, Bd.FP32, Bd.KERNEL_AUTO, 0) as grid:
-        with pytest.raises(Bd.MrtError) as ei:
-            grid.adjoint_record(w.rho, w.ux, w.uy, w.T, 4, 2)
-        assert ei.value.code == Bd.MRT_EINVAL
+    # batches take the axis-by-axis operator only
+    import ctypes
+    L = Bd.load()
+    p = Bd.make_params(w.nx, w.ny, w.dx, w.dt, w.gamma, w.s, w.bc_x, w.bc_y, Bd.FP32, advection=Bd.ADV_LW2D)
+    params = (Bd.Params * 1)(p)
+    arrs = [np.ascontiguousarray(np.broadcast_to(a, (w.ny, w.nx)), dtype=np.float64)
+            for a in (w.rho, w.ux, w.uy, w.T)]
+    ptrs = [(ctypes.c_void_p * 1)(a.ctypes.data) for a in arrs]
+    h = ctypes.c_void_p()
+    rc = L.mrt_batch_create(1, params, *(ctypes.cast(q, ctypes.POINTER(ctypes.c_void_p)) for q in ptrs), 0,
+                            ctypes.byref(h))
+    assert rc == Bd.MRT_EINVAL
+
+
+# --------------------------------------------------------------------------
+# Reverse mode of the unsplit operator
+# --------------------------------------------------------------------------
+def _rel(a, b):
+    return np.linalg.norm(np.ravel(a - b)) / max(np.linalg.norm(np.ravel(b)), 1e-300)
+
+
+@pytest.mark.parametrize("prec,tol", [(Bd.FP64, 1e-12), (Bd.FP32, 2e-5)])
+@pytest.mark.parametrize("bcx,bcy", BCS)
+def test_adjoint_step_matches_oracle(prec, tol, bcx, bcy):
+    """One reverse step (direct kernel, mrt_adjoint_step) against the
+    oracle's transpose of the ADV_LW2D step: lam and the rate gradients."""
+    w = W.random_smooth(140, 21, seed=8, amp=0.1, bc_x=bcx, bc_y=bcy)
+    g = oracle.create(w.nx, w.ny, w.dx, w.dt, w.b, w.s, w.rho, w.ux, w.uy, w.T, w.bc_x, w.bc_y,
+                      advection=oracle.ADV_LW2D)
+    f = oracle.step(g)
+    rng = np.random.default_rng(3)
+    lam_next = rng.standard_normal(f.shape)
+    dt = np.float64 if prec == Bd.FP64 else np.float32
+    f_in, l_in = f.astype(dt), lam_next.astype(dt)
+    gs = np.zeros(16)
+    want = oracle.step_adjoint(g, f_in.astype(np.float64), l_in.astype(np.float64), np.zeros_like(g.gx),
+                               np.zeros_like(g.gy), gs)
+    with _gpu(w, prec, Bd.KERNEL_AUTO, 0) as grid:
+        got, gs_gpu = grid.adjoint_step(f_in, l_in)
+    assert np.max(np.abs(got - want)) <= tol * np.max(np.abs(want))
+    np.testing.assert_allclose(gs_gpu[4:], gs[4:], rtol=tol * 50, atol=tol * np.max(np.abs(gs)))
+
+
+def _loss(target, dx):
+    def lg(r):
+        d = r - target
+        return 0.5 * np.sum(d * d) * dx * dx, d * dx * dx
+    return lg
+
+
+@pytest.mark.parametrize("case", ["vortex", "tube", "quadrants", "walls", "wall_fixed"])
+def test_adjoint_run_matches_oracle(case):
+    """Gradients of L(rho_N) with respect to the initial fields and the
+    rates through 30 ADV_LW2D steps (checkpoints every 7), both kernels, both
+    precisions; the fixed-ghost adjoints (corners included) enter the
+    gradients of the boundary cells."""
+    if case == "vortex":
+        w = W.smooth_vortex(n=40, nsteps=30, r0=0.15)
+        target = W.vortex_target(w)
+    elif case == "tube":
+        w = W.sod_tube(nx=150, ny=5, nsteps=30)
+        target = w.rho * 0.97 + 0.01
+    elif case == "quadrants":
+        w = W.shrink(W.four_quadrant_riemann(n=48), 30)
+        target = w.rho * 0.97 + 0.01
+    elif case == "walls":
+        w = W.random_smooth(150, 37, seed=31, amp=0.1, bc_x=Bd.BC_REFLECT_FIXED, bc_y=Bd.BC_REFLECT_FIXED,
+                            nsteps=30)
+        target = w.rho * 0.98 + 0.02
+    else:
+        w = W.random_smooth(61, 37, seed=32, amp=0.1, bc_x=Bd.BC_FIXED_EQ, bc_y=Bd.BC_REFLECT_FIXED, nsteps=30)
+        target = w.rho * 0.98 + 0.02
+    lg = _loss(target, w.dx)
+    ref = oracle.adjoint_run(w.nx, w.ny, w.dx, w.dt, w.b, w.s, w.rho, w.ux, w.uy, w.T, w.nsteps, lg,
+                             w.bc_x, w.bc_y, ckpt=7, advection=oracle.ADV_LW2D)
+    for prec, tol in ((Bd.FP64, 1e-10), (Bd.FP32, 1e-3)):
+        for kernel in (Bd.KERNEL_TMA, Bd.KERNEL_DIRECT):
+            with _gpu(w, prec, kernel, 0) as grid:
+                grid.adjoint_record(w.rho, w.ux, w.uy, w.T, w.nsteps, 7)
+                L, dL = lg(grid.macro()[0])
+                got = grid.adjoint_backward(dL)
+            # L is half the squared misfit of two close fields: its error is
+            # bounded through the field tolerance (1e-12 FP64, 1e-5 FP32 of
+            # max|rho|) times sum |dL/drho|
+            rho_tol = 1e-12 if prec == Bd.FP64 else 1e-5
+            assert abs(L - ref[0]) <= rho_tol * np.max(np.abs(w.rho)) * 2 * np.sum(np.abs(dL)) + 1e-14 * abs(ref[0])
+            for name, a, b in zip(("rho", "ux", "uy", "T"), got[:4], ref[1:5]):
+                scale = max(np.linalg.norm(b), 1e-4 * max(np.linalg.norm(x) for x in ref[1:5]))
+                err = np.linalg.norm(a - b) / scale
+                assert err <= tol, (case, prec, kernel, name, err)
+            err = np.linalg.norm(got[4] - ref[5]) / np.linalg.norm(ref[5])
+            assert err <= tol, (case, prec, kernel, "rates", err)
