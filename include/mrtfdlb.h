@@ -81,7 +81,8 @@ typedef enum mrt_kernel { MRT_KERNEL_AUTO = 0, MRT_KERNEL_TMA = 1, MRT_KERNEL_DI
  * (second order in time for those velocities; the split form is first order
  * there).  Beyond two fixed ends the corner ghost holds the corner cell's
  * initial f.  MRT_ADV_LW2D runs on the direct kernel and on TMA tiles 0, 1,
- * 4 and 7, forward and in reverse mode; batches take MRT_ADV_LW only. */
+ * 4, 5, 6 and 7 (tiles 2 and 3 give MRT_EINVAL), forward and in reverse
+ * mode; batches take MRT_ADV_LW only. */
 typedef enum mrt_advection { MRT_ADV_LW = 0, MRT_ADV_LW2D = 1 } mrt_advection;
 
 typedef struct mrt_params {
@@ -138,6 +139,26 @@ mrt_status mrt_get_macro(mrt_grid *g, double *rho, double *ux, double *uy, doubl
  * out[4] is host memory; synchronises the grid's stream.  Returns
  * MRT_EUNSTABLE if the health flag has tripped (out is still written). */
 mrt_status mrt_conserved_totals(mrt_grid *g, double out[4]);
+
+/* The same totals without waiting: enqueues on the grid's stream a copy of
+ * the current state's totals and health flag word into dst[5], caller-owned
+ * page-locked host memory (cudaMallocHost / cudaHostAlloc /
+ * cudaHostRegister; pageable memory makes the copy synchronous), and
+ * returns at once with *ticket identifying the copy.  dst[0..3] are the
+ * totals; dst[4] is the flag word as a double (0: healthy; bit 0: a step
+ * met non-positive or non-finite rho or pressure; bit 1: a device-side
+ * wait ran out).  dst is valid once mrt_totals_wait(g, *ticket) returns
+ * MRT_OK (or after any synchronisation of the grid's stream), and must stay
+ * allocated until then.  Steps enqueued after the call do not disturb the
+ * copy (stream order), so a caller can launch step n+1 before it waits for
+ * the totals of step n and keep the GPU busy.  Errors: MRT_EINVAL (NULL
+ * argument), MRT_ECUDA. */
+mrt_status mrt_conserved_totals_async(mrt_grid *g, double *dst, long *ticket);
+/* Wait until the copy of a ticket has landed.  The grid keeps the last 8
+ * tickets' completion markers; waiting on an older ticket waits for a
+ * later copy instead (correct, possibly longer).  Errors: MRT_EINVAL
+ * (NULL grid, or a ticket that was never issued), MRT_ECUDA. */
+mrt_status mrt_totals_wait(mrt_grid *g, long ticket);
 
 /* Copy the raw state f [16][ny][nx] (grid precision) out of / into the grid;
  * for checkpoint/resume and tests.  Host copies synchronise. */

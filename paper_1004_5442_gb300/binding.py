@@ -28,7 +28,8 @@ EXPORTED = ["mrt_create", "mrt_step", "mrt_get_macro", "mrt_conserved_totals", "
             "mrt_last_error", "mrt_conserved_totals_static", "mrt_adjoint_record",
             "mrt_adjoint_backward", "mrt_adjoint_step", "mrt_batch_create", "mrt_batch_step",
             "mrt_batch_tune", "mrt_batch_grid", "mrt_batch_info", "mrt_batch_sync", "mrt_batch_stream",
-            "mrt_batch_destroy", "mrt_debug_padding", "mrt_debug_wait_timeout"]
+            "mrt_batch_destroy", "mrt_debug_padding", "mrt_debug_wait_timeout", "mrt_conserved_totals_async",
+            "mrt_totals_wait"]
 
 
 class MrtError(RuntimeError):
@@ -91,13 +92,16 @@ def load(path: str = LIB_PATH):
     L.mrt_batch_stream.argtypes = [vp, ctypes.POINTER(vp)]
     L.mrt_debug_padding.argtypes = [vp, ctypes.POINTER(ctypes.c_long)]
     L.mrt_debug_wait_timeout.argtypes = [vp]
+    L.mrt_conserved_totals_async.argtypes = [vp, vp, ctypes.POINTER(ctypes.c_long)]
+    L.mrt_totals_wait.argtypes = [vp, ctypes.c_long]
     L.mrt_batch_destroy.argtypes = [vp]
     L.mrt_batch_destroy.restype = None
     for name in ("mrt_create", "mrt_step", "mrt_get_macro", "mrt_conserved_totals", "mrt_get_f",
                  "mrt_set_f", "mrt_health", "mrt_info", "mrt_conserved_totals_static",
                  "mrt_adjoint_record", "mrt_adjoint_backward", "mrt_adjoint_step", "mrt_batch_create",
                  "mrt_batch_step", "mrt_batch_tune", "mrt_batch_grid", "mrt_batch_info", "mrt_batch_sync",
-                 "mrt_batch_stream", "mrt_debug_padding", "mrt_debug_wait_timeout"):
+                 "mrt_batch_stream", "mrt_debug_padding", "mrt_debug_wait_timeout", "mrt_conserved_totals_async",
+                 "mrt_totals_wait"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -205,6 +209,17 @@ class Grid:
         out = np.zeros(4)
         check(load().mrt_conserved_totals(self._h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
         return out
+
+    def totals_async(self, dst) -> int:
+        """Enqueue the totals and flag word into dst (5 doubles of page-locked
+        host memory: a pinned torch tensor or a numpy view of one); returns the
+        ticket to pass to totals_wait (mrt_conserved_totals_async)."""
+        t = ctypes.c_long()
+        check(load().mrt_conserved_totals_async(self._h, ctypes.c_void_p(_ptr(dst)), ctypes.byref(t)))
+        return t.value
+
+    def totals_wait(self, ticket: int) -> None:
+        check(load().mrt_totals_wait(self._h, int(ticket)))
 
     def get_f(self, out=None) -> np.ndarray:
         if out is None:

@@ -447,7 +447,7 @@ static mrt_status validate(const mrt_params* p) {
     if (p->advection != MRT_ADV_LW && p->advection != MRT_ADV_LW2D)
         return fail(MRT_EINVAL, "bad advection %d", p->advection);
     if (p->advection == MRT_ADV_LW2D && p->kernel != MRT_KERNEL_DIRECT && !tile_supports_xt(p->tile))
-        return fail(MRT_EINVAL, "the unsplit operator runs on tiles 0, 1, 4 and 7 (it reads row r-1 from the ring)");
+        return fail(MRT_EINVAL, "the unsplit operator runs on tiles 0, 1, 4, 5, 6 and 7");
     return MRT_OK;
 }
 
@@ -465,6 +465,8 @@ static void release(mrt_grid* g) {
     cudaFree(g->block_sums);
     cudaFree(g->qnext);
     cudaFreeHost(g->host_stage);
+    for (int k = 0; k < mrt_grid::kTotalsEvents; ++k)
+        if (g->tev[k]) cudaEventDestroy(g->tev[k]);
     cudaFree(g->macro_tmp);
     mrt_tape_free(g->tape);
     if (prev >= 0) cudaSetDevice(prev);
@@ -567,6 +569,9 @@ extern "C" mrt_status mrt_create(const mrt_params* params, const double* rho, co
         (e = cudaMalloc(&g->block_sums, 4 * sizeof(double) * FINAL_MAX_BLOCKS)) != cudaSuccess ||
         (e = cudaMallocHost(&g->host_stage, 8 * sizeof(double))) != cudaSuccess)
         return bail(fail(MRT_ENOMEM, "cudaMalloc: %s", cudaGetErrorString(e)));
+    for (int k = 0; k < mrt_grid::kTotalsEvents; ++k)
+        if ((e = cudaEventCreateWithFlags(&g->tev[k], cudaEventDisableTiming)) != cudaSuccess)
+            return bail(fail(MRT_ECUDA, "cudaEventCreate: %s", cudaGetErrorString(e)));
 
     // kernel choice and launch geometry
     // AUTO: the TMA strip kernel, except for small FP64 grids, where the
@@ -816,6 +821,27 @@ extern "C" mrt_status mrt_conserved_totals(mrt_grid* g, double out[4]) {
     const unsigned flag = (unsigned)g->host_stage[4];
     if (flag & FLAG_TIMEOUT) return fail(MRT_ETIMEOUT, "a device-side wait ran out");
     if (flag & FLAG_UNSTABLE) return fail(MRT_EUNSTABLE, "non-positive or non-finite rho or pressure");
+    return MRT_OK;
+}
+
+extern "C" mrt_status mrt_conserved_totals_async(mrt_grid* g, double* dst, long* ticket) {
+    if (!g || !dst || !ticket) return fail(MRT_EINVAL, "null argument");
+    if (!g->totals_fresh) {
+        mrt_status st = g->fp64 ? totals_impl<double>(g) : totals_impl<float>(g);
+        if (st != MRT_OK) return st;
+    }
+    CUDA_TRY(cudaMemcpyAsync(dst, g->totals_dev, 5 * sizeof(double), cudaMemcpyDeviceToHost, g->stream));
+    const long t = g->tickets;
+    CUDA_TRY(cudaEventRecord(g->tev[t % mrt_grid::kTotalsEvents], g->stream));
+    g->tickets = t + 1;
+    *ticket = t;
+    return MRT_OK;
+}
+
+extern "C" mrt_status mrt_totals_wait(mrt_grid* g, long ticket) {
+    if (!g) return fail(MRT_EINVAL, "grid is NULL");
+    if (ticket < 0 || ticket >= g->tickets) return fail(MRT_EINVAL, "ticket %ld was never issued", ticket);
+    CUDA_TRY(cudaEventSynchronize(g->tev[ticket % mrt_grid::kTotalsEvents]));
     return MRT_OK;
 }
 

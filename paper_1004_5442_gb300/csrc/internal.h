@@ -105,9 +105,10 @@ inline TileCfg tile_cfg(int tile) {
 constexpr int kQueueTile = 6;
 constexpr int kStaticTileF32 = 4;
 constexpr int kStaticTileF64 = 1;
-// The unsplit operator keeps row r-1 in the ring: its queue tile is 7.
-constexpr int kQueueTileXT = 7;
-inline bool tile_supports_xt(int tile) { return tile == 0 || tile == 1 || tile == 4 || tile == 7; }
+// The unsplit operator runs on every tile but 2 and 3; its queue tile is 6
+// (row r-1's diagonal x neighbours then come from registers).
+constexpr int kQueueTileXT = 6;
+inline bool tile_supports_xt(int tile) { return tile != 2 && tile != 3; }
 
 template <class T>
 inline size_t tma_smem_bytes(int tile) {
@@ -118,7 +119,7 @@ inline size_t tma_smem_bytes(int tile) {
 
 // Launchers (step_kernels.cu).  grid_y = number of row chunks for the TMA
 // kernel.  Return the launch status.
-// xt: the unsplit operator (MRT_ADV_LW2D; TMA tiles 1, 4 and 7 only).
+// xt: the unsplit operator (MRT_ADV_LW2D; TMA tiles 1, 4, 5, 6 and 7).
 template <class T>
 cudaError_t launch_step_tma(int tile, bool xt, const CUtensorMap* map_in, const CUtensorMap* map_out,
                             const StepArgs<T>& a, int grid_x, int grid_y, bool totals, cudaStream_t st);
@@ -217,6 +218,9 @@ struct mrt_grid {
     double* totals_dev = nullptr;    // 4 totals + a copy of the flag word, as doubles
     double* block_sums = nullptr;    // first-pass sums of the totals reduction
     double* host_stage = nullptr;    // pinned host copy of totals_dev (one small DMA per read)
+    static constexpr int kTotalsEvents = 8;
+    cudaEvent_t tev[kTotalsEvents] = {};  // completion markers of asynchronous totals copies
+    long tickets = 0;                // asynchronous totals copies issued
     bool totals_fresh = false;
     double* macro_tmp = nullptr;     // 4 fields, for host readout
     long steps = 0;

@@ -178,14 +178,17 @@ struct TmaKernels {
 // FP64 rings are capped at 4 rows (16.9 KB per row).
 template <class T, int NS> constexpr int ring_depth() { return sizeof(T) == 8 && NS > 4 ? 4 : NS; }
 
-// The unsplit operator (xt) reads rows r-1 and r+1 at x +- 1 from the ring:
-// tiles 1, 4 and 7, which keep row r-1 resident.
+// The unsplit operator (xt) reads rows r-1 and r+1 at x +- 1: tiles 1, 4
+// and 7 keep row r-1 in the ring, tiles 5 and 6 keep its diagonal planes'
+// x neighbours in registers.
 template <class T, class Fn>
 cudaError_t with_tile(int tile, bool xt, Fn&& fn) {
     if (xt) {
         switch (tile) {
             case 1: return fn(TmaKernels<T, ring_depth<T, 6>(), false, 4, false, false, true>());
             case 4: return fn(TmaKernels<T, ring_depth<T, 5>(), true, (sizeof(T) == 8 ? 2 : 3), false, false, true>());
+            case 5: return fn(TmaKernels<T, ring_depth<T, 4>(), true, (sizeof(T) == 8 ? 2 : 4), true, false, true>());
+            case 6: return fn(TmaKernels<T, ring_depth<T, 4>(), true, (sizeof(T) == 8 ? 2 : 4), true, true, true>());
             case 7: return fn(TmaKernels<T, ring_depth<T, 5>(), true, (sizeof(T) == 8 ? 2 : 3), false, true, true>());
             default: return cudaErrorInvalidValue;
         }

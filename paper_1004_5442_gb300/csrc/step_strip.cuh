@@ -183,13 +183,15 @@ struct StripRing {
 // [y0, y0+nrows) of the field described by L, read through map_in and
 // written to out (map_out for whole-strip TMA row stores).  Returns false if
 // a bounded wait ran out (the caller drains and flags).
-// XT: the unsplit operator (diagonal neighbours from rows r-1 and r+1 of the
-// ring, so not with YWIN).
+// XT: the unsplit operator (diagonal neighbours).  Row r+1 at x +- 1 comes
+// from the ring; row r-1 at x +- 1 from the ring, or with YWIN from
+// registers: the diagonal planes' x neighbours of row r, which the cell
+// update reads anyway, are kept for the next row.
 template <class T, bool TOTALS, int NS, bool TSTORE, bool YWIN, bool XT = false, class CoefT>
 __device__ __forceinline__ bool strip_chunk(StripRing<T>& R, const CUtensorMap* map_in, const CUtensorMap* map_out,
                                             const Layout& L, int per_x, int per_y, T* __restrict__ out,
                                             const CoefT& k, int x0, int y0, int nrows, bool& bad, Acc<T>* acc) {
-    static_assert(!(XT && YWIN), "the unsplit operator reads row r-1 from the ring");
+    constexpr bool XW = XT && YWIN;  // diagonal corners of row r-1 in registers
     constexpr int HALO = tma_halo<T>();
     constexpr int BOXW = tma_boxw<T>();
     constexpr uint32_t SLOT_BYTES = (uint32_t)tma_slot_bytes<T>();
@@ -229,6 +231,8 @@ __device__ __forceinline__ bool strip_chunk(StripRing<T>& R, const CUtensorMap* 
     if (!YWIN) ok = wait_row(2) && ok;
     const int col = tid + HALO;
     T ym[NV], fc[NV];  // YWIN: rows r-1 (y-moving planes) and r at this column
+    T dm[8], dp[8];    // XW: row r-1 at x-1 / x+1 of the diagonal planes 8..15
+    T nm[8], np[8];    // XW: row r at x-1 / x+1, captured for the next row
     if (YWIN && ok) {
         const T* s0 = ring + (size_t)slot_of(0) * NV * BOXW;
         const T* s1 = ring + (size_t)slot_of(1) * NV * BOXW;
@@ -236,6 +240,10 @@ __device__ __forceinline__ bool strip_chunk(StripRing<T>& R, const CUtensorMap* 
         for (int i = 0; i < NV; ++i) {
             if (moves_y<YWIN>(i)) ym[i] = s0[i * BOXW + col];
             fc[i] = s1[i * BOXW + col];
+            if (XW && i >= 8) {
+                dm[i - 8] = s0[i * BOXW + col - 1];
+                dp[i - 8] = s0[i * BOXW + col + 1];
+            }
         }
     }
     if (__syncthreads_or(!ok)) return false;
@@ -264,14 +272,22 @@ __device__ __forceinline__ bool strip_chunk(StripRing<T>& R, const CUtensorMap* 
             auto F = [&](int i, int pos) -> T {
                 switch (pos) {
                     case C: return YWIN ? fc[i] : sc[i * BOXW + col];
-                    case XM: return sc[i * BOXW + col - 1];
-                    case XP: return sc[i * BOXW + col + 1];
+                    case XM: {
+                        const T v = sc[i * BOXW + col - 1];
+                        if (XW && i >= 8) nm[i - 8] = v;
+                        return v;
+                    }
+                    case XP: {
+                        const T v = sc[i * BOXW + col + 1];
+                        if (XW && i >= 8) np[i - 8] = v;
+                        return v;
+                    }
                     case YM: return YWIN ? ym[i] : sm[i * BOXW + col];
                     case YP: return YWIN ? yp[i] : sp[i * BOXW + col];
                     case XPYP: return sp[i * BOXW + col + 1];
-                    case XPYM: return sm[i * BOXW + col + 1];
+                    case XPYM: return XW ? dp[i - 8] : sm[i * BOXW + col + 1];
                     case XMYP: return sp[i * BOXW + col - 1];
-                    default: return sm[i * BOXW + col - 1];
+                    default: return XW ? dm[i - 8] : sm[i * BOXW + col - 1];
                 }
             };
             T o[NV];
@@ -282,6 +298,13 @@ __device__ __forceinline__ bool strip_chunk(StripRing<T>& R, const CUtensorMap* 
                 for (int i = 0; i < NV; ++i) {
                     if (moves_y<YWIN>(i)) ym[i] = fc[i];
                     fc[i] = yp[i];
+                }
+            }
+            if (XW) {
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    dm[j] = nm[j];
+                    dp[j] = np[j];
                 }
             }
             bad |= !(rho > (T)0) | !(P > (T)0);

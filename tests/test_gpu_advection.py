@@ -7,7 +7,7 @@ step and 1e-12 relative for macroscopic fields over many steps, FP32 2e-6 of
 max|f| for one step from the GPU's own state and 1e-5 relative on smooth
 flow.  Cases span ragged 128-column strips, every boundary combination
 (the corner ghosts beyond two non-periodic ends included), the kernels that
-run it (direct; TMA tiles 1, 4 and 7; the automatic choice), the queue tile
+run it (direct; TMA tiles 1, 4, 5, 6 and 7; the automatic choice), the queue tile
 on a grid with enough work items, the rejection of the combinations that
 do not take it, and the reverse mode (one reverse step and whole-run
 gradients against the oracle's reverse mode of the same operator)."""
@@ -21,7 +21,7 @@ from _parity import assert_parity
 
 pytestmark = pytest.mark.gpu
 
-VARIANTS = [(Bd.KERNEL_TMA, t) for t in (0, 1, 4, 7)] + [(Bd.KERNEL_DIRECT, 0)]
+VARIANTS = [(Bd.KERNEL_TMA, t) for t in (0, 1, 4, 5, 6, 7)] + [(Bd.KERNEL_DIRECT, 0)]
 BCS = [(0, 0), (1, 0), (0, 1), (1, 1), (2, 0), (2, 1), (0, 2), (2, 2)]
 
 
@@ -87,15 +87,15 @@ def test_many_steps_parity(kernel, tile, bcx, bcy):
 
 
 def test_queue_tile_on_a_large_grid_and_totals():
-    """2048 x 2048 gives every resident CTA at least two 32-row items, so the
-    automatic choice is the queue tile 7 in both precisions; one FP64 step
+    """2048 x 2048 gives every resident CTA at least two 8-row items, so the
+    automatic choice is the queue tile 6 in both precisions; one FP64 step
     and its totals match the oracle."""
     w = W.random_smooth(2048, 2048, seed=3, amp=0.05)
     g = _oracle(w, 1)
     with _gpu(w, Bd.FP32, Bd.KERNEL_AUTO, 0) as grid:
-        assert grid.info()["tile"] == 7
+        assert grid.info()["tile"] == 6
     with _gpu(w, Bd.FP64, Bd.KERNEL_AUTO, 0) as grid:
-        assert grid.info()["tile"] == 7
+        assert grid.info()["tile"] == 6
         grid.step(1)
         f = grid.get_f()
         t = grid.totals()
@@ -117,8 +117,7 @@ def test_four_quadrants_corners():
             assert_parity(grid.macro(), want, l1=1e-4, label="fp32")
 
 
-@pytest.mark.parametrize("kernel,tile", [(Bd.KERNEL_TMA, 1), (Bd.KERNEL_TMA, 4), (Bd.KERNEL_TMA, 7),
-                                         (Bd.KERNEL_DIRECT, 0)])
+@pytest.mark.parametrize("kernel,tile", [(Bd.KERNEL_TMA, t) for t in (1, 4, 5, 6, 7)] + [(Bd.KERNEL_DIRECT, 0)])
 def test_guard_band_and_minimum_grid(kernel, tile):
     """No write lands outside the ghost ring (the corner stores included), and
     the 3 x 3 minimum grid, whose corner cells feed every ghost, matches."""
@@ -139,7 +138,7 @@ def test_guard_band_and_minimum_grid(kernel, tile):
 
 def test_rejected_combinations():
     w = W.random_smooth(64, 16, seed=1, amp=0.05)
-    for tile in (2, 3, 5, 6):
+    for tile in (2, 3):
         with pytest.raises(Bd.MrtError) as ei:
             _gpu(w, Bd.FP32, Bd.KERNEL_TMA, tile)
         assert ei.value.code == Bd.MRT_EINVAL
