@@ -165,6 +165,24 @@ mrt_status mrt_totals_wait(mrt_grid *g, long ticket);
 mrt_status mrt_get_f(mrt_grid *g, void *f, int on_device);
 mrt_status mrt_set_f(mrt_grid *g, const void *f, int on_device);
 
+/* Save the grid's state to a file and restore it (the paper has no
+ * counterpart; for checkpoint and resume of long runs).  The file holds a
+ * header (grid size, precision, advection operator, boundary kinds, dx,
+ * dt, gamma, the 16 rates as stepped, the step count, the padded layout and
+ * an FNV-1a checksum of the payload) and the current distribution buffer in
+ * the library's padded layout, fixed-equilibrium ghosts included, so a
+ * resumed run continues bit for bit whatever fields the loading grid was
+ * created from.  mrt_load requires a grid of the same size, precision,
+ * operator, boundary kinds, dx, dt, gamma and rates; it restores the state
+ * and the step count (mrt_info), not the health flag or a recorded
+ * reverse-mode run.  Both synchronise the grid's stream and stage the state
+ * in host memory.  Errors: MRT_EINVAL (NULL argument; a file that cannot be
+ * opened, is not a checkpoint of this library, is truncated, fails its
+ * checksum or does not match the grid, with the reason in mrt_last_error),
+ * MRT_ENOMEM (host staging), MRT_ECUDA. */
+mrt_status mrt_save(mrt_grid *g, const char *path);
+mrt_status mrt_load(mrt_grid *g, const char *path);
+
 /* Synchronise the grid's stream and report the health flag: MRT_OK,
  * MRT_EUNSTABLE (non-positive or non-finite rho or pressure met by a step),
  * MRT_ETIMEOUT (a device-side wait ran out) or MRT_ECUDA. */

@@ -29,7 +29,7 @@ EXPORTED = ["mrt_create", "mrt_step", "mrt_get_macro", "mrt_conserved_totals", "
             "mrt_adjoint_backward", "mrt_adjoint_step", "mrt_batch_create", "mrt_batch_step",
             "mrt_batch_tune", "mrt_batch_grid", "mrt_batch_info", "mrt_batch_sync", "mrt_batch_stream",
             "mrt_batch_destroy", "mrt_debug_padding", "mrt_debug_wait_timeout", "mrt_conserved_totals_async",
-            "mrt_totals_wait"]
+            "mrt_totals_wait", "mrt_save", "mrt_load"]
 
 
 class MrtError(RuntimeError):
@@ -94,6 +94,8 @@ def load(path: str = LIB_PATH):
     L.mrt_debug_wait_timeout.argtypes = [vp]
     L.mrt_conserved_totals_async.argtypes = [vp, vp, ctypes.POINTER(ctypes.c_long)]
     L.mrt_totals_wait.argtypes = [vp, ctypes.c_long]
+    L.mrt_save.argtypes = [vp, ctypes.c_char_p]
+    L.mrt_load.argtypes = [vp, ctypes.c_char_p]
     L.mrt_batch_destroy.argtypes = [vp]
     L.mrt_batch_destroy.restype = None
     for name in ("mrt_create", "mrt_step", "mrt_get_macro", "mrt_conserved_totals", "mrt_get_f",
@@ -101,7 +103,7 @@ def load(path: str = LIB_PATH):
                  "mrt_adjoint_record", "mrt_adjoint_backward", "mrt_adjoint_step", "mrt_batch_create",
                  "mrt_batch_step", "mrt_batch_tune", "mrt_batch_grid", "mrt_batch_info", "mrt_batch_sync",
                  "mrt_batch_stream", "mrt_debug_padding", "mrt_debug_wait_timeout", "mrt_conserved_totals_async",
-                 "mrt_totals_wait"):
+                 "mrt_totals_wait", "mrt_save", "mrt_load"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -220,6 +222,14 @@ class Grid:
 
     def totals_wait(self, ticket: int) -> None:
         check(load().mrt_totals_wait(self._h, int(ticket)))
+
+    def save(self, path) -> None:
+        """Write the state, fixed ghosts and step count to a file (mrt_save)."""
+        check(load().mrt_save(self._h, os.fsencode(path)))
+
+    def load(self, path) -> None:
+        """Restore a state written by save into this matching grid (mrt_load)."""
+        check(load().mrt_load(self._h, os.fsencode(path)))
 
     def get_f(self, out=None) -> np.ndarray:
         if out is None:

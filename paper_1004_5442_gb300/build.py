@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libmrtfdlb.so")
 SOURCES = ["api.cu", "step_kernels.cu", "noalloc.cu", "adjoint_kernels.cu", "adjoint_api.cu", "batch.cu",
-           "diag.cu"]
+           "diag.cu", "checkpoint.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
