@@ -198,36 +198,66 @@ __global__ void __launch_bounds__(TMA_W) adjoint_tma_kernel(const __grid_constan
             bulk_wait_all();
         }
     };
+    // Row r-1 of lam lives in registers (the y-moving planes at this column
+    // and, for the unsplit operator, the diagonal planes at x -+ 1), so only
+    // rows r and r+1 must be resident and the 4-slot ring keeps two rows in
+    // flight: the slot of row r is released as soon as row r is done.
+    const int col = tid + HALO;
+    T ym[NV];          // lam row r-1 at this column (y-moving planes)
+    T dm[8], dp[8];    // XT: lam row r-1 at x-1 / x+1 (diagonal planes 8..15)
+    T nym[NV], nm[8], np[8];  // the same of row r, captured for the next row
     bool ok = wait_l(0);
     ok = wait_l(1) && ok;
-    ok = wait_l(2) && ok;
+    if (ok && active) {
+        const T* s0 = lring;  // row 0 sits in slot 0
+#pragma unroll
+        for (int i = 0; i < NV; ++i) {
+            if (moves_y<true>(i)) ym[i] = s0[i * BOXW + col];
+            if (XT && i >= 8) {
+                dm[i - 8] = s0[i * BOXW + col - 1];
+                dp[i - 8] = s0[i * BOXW + col + 1];
+            }
+        }
+    }
     if (__syncthreads_or(!ok)) { drain(); return; }  // drain() raises FLAG_TIMEOUT
+    if (tid == 0 && ADJ_NSL < nload) { issue_l(ADJ_NSL); issuedL = ADJ_NSL + 1; }  // row 0 is in registers
 
     T gs[12];
 #pragma unroll
     for (int j = 0; j < 12; ++j) gs[j] = 0;
-    const int col = tid + HALO;
 #pragma unroll 1
     for (int r = 1; r <= nrows; ++r) {
         const int y = y0 + r - 1;
         T* ob = outbuf + (size_t)(r & 1) * NV * TMA_W;
         ok = wait_f(r - 1);
+        ok = wait_l(r + 1) && ok;
         if (active && ok) {
-            const T* sm = lring + (size_t)((r - 1) % ADJ_NSL) * NV * BOXW;
             const T* sc = lring + (size_t)(r % ADJ_NSL) * NV * BOXW;
             const T* sp = lring + (size_t)((r + 1) % ADJ_NSL) * NV * BOXW;
             const T* sf = fring + (size_t)((r - 1) % ADJ_NSF) * NV * BOXW;
             auto LF = [&](int i, int pos) -> T {
                 switch (pos) {
-                    case C: return sc[i * BOXW + col];
-                    case XM: return sc[i * BOXW + col - 1];
-                    case XP: return sc[i * BOXW + col + 1];
-                    case YM: return sm[i * BOXW + col];
+                    case C: {
+                        const T v = sc[i * BOXW + col];
+                        if (moves_y<true>(i)) nym[i] = v;
+                        return v;
+                    }
+                    case XM: {
+                        const T v = sc[i * BOXW + col - 1];
+                        if (XT && i >= 8) nm[i - 8] = v;
+                        return v;
+                    }
+                    case XP: {
+                        const T v = sc[i * BOXW + col + 1];
+                        if (XT && i >= 8) np[i - 8] = v;
+                        return v;
+                    }
+                    case YM: return ym[i];
                     case YP: return sp[i * BOXW + col];
                     case XPYP: return sp[i * BOXW + col + 1];
-                    case XPYM: return sm[i * BOXW + col + 1];
+                    case XPYM: return dp[i - 8];
                     case XMYP: return sp[i * BOXW + col - 1];
-                    default: return sm[i * BOXW + col - 1];
+                    default: return dm[i - 8];
                 }
             };
             T f[NV];
@@ -247,10 +277,22 @@ __global__ void __launch_bounds__(TMA_W) adjoint_tma_kernel(const __grid_constan
                 for (int i = 0; i < NV; ++i)
                     a.gyb[((long)i * 2 + side) * L.nx + x] += (double)(lw_weight<T>(a.k, i, side == 0 ? YM : YP) * LF(i, C));
             }
+            // cell_adjoint read every plane's centre and the diagonal
+            // planes' x neighbours of row r: keep them as the next row's r-1
+#pragma unroll
+            for (int i = 0; i < NV; ++i)
+                if (moves_y<true>(i)) ym[i] = nym[i];
+            if (XT) {
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    dm[j] = nm[j];
+                    dp[j] = np[j];
+                }
+            }
         }
         fence_async_shared();
         if (tid == 0) bulk_wait_read_all();
-        if (r + 2 < nload) ok = wait_l(r + 2) && ok;
+        // every thread is done with row r's slot and with this output row
         if (__syncthreads_or(!ok)) { drain(); return; }
         if (tid == 0) {
             if (tstore) {
@@ -259,7 +301,7 @@ __global__ void __launch_bounds__(TMA_W) adjoint_tma_kernel(const __grid_constan
                 if (a.per_y && y == L.ny - 1) tma_store_3d(&map_out, ob, L.G + x0, 0, 0);
                 bulk_commit();
             }
-            const int l = r - 1 + ADJ_NSL;
+            const int l = r + ADJ_NSL;  // into the slot of row r
             if (l < nload) { issue_l(l); issuedL = l + 1; }
             const int j = r - 1 + ADJ_NSF;
             if (j < nrows) { issue_f(j); issuedF = j + 1; }
