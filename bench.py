@@ -62,6 +62,9 @@ def parse():
     ap.add_argument("--n", type=int, default=4096, help="grid edge (default 4096)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-lw2d", action="store_true")
+    ap.add_argument("--adjoint-n", type=int, default=0,
+                    help="time the reverse mode on one n x n shear layer (8 steps, checkpoints every 4) "
+                         "instead of the default cases (for profiler captures)")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
@@ -393,7 +396,11 @@ def run_ours(args):
     # adjoint / forward cost (smooth vortex 512^2, 500 FP32 steps, checkpoints
     # every 50; and the 4096^2 workload for the HBM-bound ratio)
     if not args.no_adjoint:
-        line["adjoint"] = adjoint_costs(Bd, W, torch, stream)
+        cases = None
+        if args.adjoint_n > 0:
+            n = args.adjoint_n
+            cases = [(f"kelvin_helmholtz_{n}x{n}_fp32", W.kelvin_helmholtz(n=n, nsteps=8), 8, 4)]
+        line["adjoint"] = adjoint_costs(Bd, W, torch, stream, cases=cases)
 
     # the paper's tube and 2-D problems: throughput next to error vs exact
     if not args.no_problems:

@@ -22,7 +22,7 @@
  *                Sect. "Numerical Simulation and Analysis")
  *   Sect. (b)    boundary nodes held at f^eq = Minv fhat^eq; y periodic
  *
- * Readings where the paper is silent (each listed in the design doc):
+ * Readings where the paper is silent:
  *   - order inside the "cyc" groups: (1,0),(0,1),(-1,0),(0,-1) and
  *     (1,1),(-1,1),(-1,-1),(1,-1) times the group speed factor;
  *   - "first-order upwind" in time is forward Euler; the Lax-Wendroff space

@@ -1,9 +1,10 @@
 """Build the CUDA library libmrtfdlb.so in-tree for sm_103a with nvcc.
 
-The two translation units are compiled in parallel and linked into
+The translation units in SOURCES are compiled in parallel and linked into
 ``paper_1004_5442_gb300/_build/libmrtfdlb.so``; the CUDA runtime is linked
-statically and the driver's tensor-map encoder is resolved at run time, so
-the library needs nothing but the NVIDIA driver to load.
+statically and cuTensorMapEncodeTiled is looked up in the CUDA driver
+library at run time, so the library needs nothing but the NVIDIA kernel
+driver to load.
 """
 from __future__ import annotations
 

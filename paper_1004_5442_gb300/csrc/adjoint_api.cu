@@ -79,7 +79,8 @@ extern "C" mrt_status mrt_adjoint_record(mrt_grid* g, const double* rho0, const 
         t->adj_gx = strips;
         t->adj_gy = (g->L.ny + t->adj_rows - 1) / t->adj_rows;
         t->adj_tma = 1;
-        t->nparts = std::max(t->nparts, t->adj_gx * t->adj_gy);
+        // only the TMA reverse step runs: one rate-partial slot per CTA
+        t->nparts = t->adj_gx * t->adj_gy;
     }
     A_TRY(cudaMalloc(&t->ck, t->state_bytes * (size_t)t->nck));
     A_TRY(cudaMalloc(&t->seg, t->state_bytes * (size_t)t->K));
