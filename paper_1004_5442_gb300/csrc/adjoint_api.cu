@@ -107,10 +107,13 @@ extern "C" mrt_status mrt_adjoint_record(mrt_grid* g, const double* rho0, const 
             if (st != MRT_OK) return st;
         }
     }
-    // every segment buffer carries the fixed-equilibrium ghosts of f^0
-    for (int j = 0; j < t->K; ++j)
-        A_TRY(cudaMemcpyAsync(buf_at(t->seg, t->state_bytes, j), g->f[g->cur], t->state_bytes,
-                              cudaMemcpyDeviceToDevice, g->stream));
+    // every segment buffer carries the fixed-equilibrium ghosts of f^0 (on
+    // periodic axes the recompute steps write every ghost they later read,
+    // and segment buffer 0 is a full checkpoint copy)
+    if (g->p.bc_x != MRT_BC_PERIODIC || g->p.bc_y != MRT_BC_PERIODIC)
+        for (int j = 0; j < t->K; ++j)
+            A_TRY(cudaMemcpyAsync(buf_at(t->seg, t->state_bytes, j), g->f[g->cur], t->state_bytes,
+                                  cudaMemcpyDeviceToDevice, g->stream));
     if (t->adj_tma)
         for (int b = 0; b < 2; ++b) {
             st = mrt_encode_maps(g, t->lam[b], &t->lam_in[b], &t->lam_out[b]);

@@ -237,3 +237,34 @@ def test_adjoint_run_matches_oracle(case):
                 assert err <= tol, (case, prec, kernel, name, err)
             err = np.linalg.norm(got[4] - ref[5]) / np.linalg.norm(ref[5])
             assert err <= tol, (case, prec, kernel, "rates", err)
+
+
+def test_full_size_kh_sampled_windows():
+    """The bench's unsplit-operator leg: 4096^2 Kelvin-Helmholtz in FP32 on
+    the automatic choice (tile 6).  After 3 steps, 12 seeded 48^2 windows
+    (the periodic corners, whose cells read the diagonally wrapped corner
+    ghosts, and strip/item seams among them) of step 3 -> 4 match one
+    ADV_LW2D oracle step on the window (exact in its interior, the stencil
+    reaching one cell, diagonals included)."""
+    w = W.kelvin_helmholtz(n=4096, nsteps=0)
+    rng = np.random.default_rng(1)
+    n = 48
+    corners = [(0, 0), (w.ny - n, w.nx - n), (0, w.nx - n), (w.ny - n, 0), (2000, 128 * 16 - 24)]
+    wins = corners + [(int(rng.integers(0, w.ny - n)), int(rng.integers(0, w.nx - n))) for _ in range(7)]
+    with _gpu(w, Bd.FP32, Bd.KERNEL_TMA, 0) as grid:
+        assert grid.info()["tile"] == 6
+        grid.step(3)
+        f3 = grid.get_f()
+        grid.step(1)
+        f4 = grid.get_f()
+    for (y0, x0) in wins:
+        ys = np.arange(y0 - 1, y0 + n + 1) % w.ny
+        xs = np.arange(x0 - 1, x0 + n + 1) % w.nx
+        fw = np.ascontiguousarray(f3[:, ys][:, :, xs].astype(np.float64))
+        g = oracle.Grid(n + 2, n + 2, w.dx, w.dt, w.b, w.s, oracle.BC_PERIODIC, oracle.BC_PERIODIC,
+                        oracle.ADV_LW2D)
+        g.gx = np.zeros((16, 2, n + 2))
+        g.gy = np.zeros((16, 2, n + 2))
+        want = oracle.step(g, fw)[:, 1:-1, 1:-1]
+        got = f4[:, y0:y0 + n, x0:x0 + n].astype(np.float64)
+        assert np.max(np.abs(got - want)) <= 2e-6 * np.max(np.abs(want)), (y0, x0)
