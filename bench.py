@@ -41,13 +41,13 @@ KERNEL_SOURCES = ["paper_1004_5442_gb300/csrc/step_kernels.cu", "paper_1004_5442
                   "paper_1004_5442_gb300/csrc/tma.cuh", "paper_1004_5442_gb300/csrc/model.cuh",
                   "paper_1004_5442_gb300/csrc/internal.h"]
 PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "step_tma_f32_kh4096.md")
-# FP64 step, per cell-update (ncu instruction counters of step_tma<double>,
-# profiles/step_tma_f64_kh2048.md): FP64-pipe thread instructions and flops
-# (DADD + DMUL + 2 DFMA).  The FP64 pipe issues 2 thread instructions per
-# clock per SM (152 SMs; 2 x 2 flops x 152 x 2.07 GHz = 1.26 TFLOP/s, the
-# part's FP64 rate).
-FP64_PIPE_INST_PER_CELL = 327.3
-FP64_FLOPS_PER_CELL = 436.3
+# FP64 step, per cell-update (ncu instruction counters of a plain
+# step_tma<double> launch, tile 6, profiles/step_tma_f64_kh2048.md):
+# FP64-pipe thread instructions and flops (DADD + DMUL + 2 DFMA).  The FP64
+# pipe issues 2 thread instructions per clock per SM (152 SMs; 2 x 2 flops x
+# 152 x 2.07 GHz = 1.26 TFLOP/s, the part's FP64 rate).
+FP64_PIPE_INST_PER_CELL = 286.0
+FP64_FLOPS_PER_CELL = 386.0
 FP64_LANES_PER_SM = 2
 N_SMS = 152
 EXACT_PROFILES = os.path.join(ROOT, "tests", "golden", "riemann_exact_profiles.json")
@@ -190,16 +190,19 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def profiled_traffic():
+def profiled_traffic(n):
     """DRAM bytes per launch from the committed ncu summary, if it was taken
-    on the current kernel source."""
+    on the current kernel source and states them for an n x n launch."""
     try:
         text = open(PROFILE_SUMMARY).read()
     except OSError:
         return None
     m = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", text)
     hsh = re.search(r"kernel_source_hash:\s*([0-9a-f]+)", text)
+    size = re.search(r"traffic_grid:\s*(\d+)", text)
     if not m or not hsh or hsh.group(1) != kernel_source_hash():
+        return None
+    if not size or int(size.group(1)) != n:
         return None
     return float(m.group(1))
 
@@ -335,7 +338,7 @@ def run_ours(args):
     per_launch_s = ms * 1e-3 / args.steps
     peak, peak_kind = measured_peak_hbm()
     achieved = BYTES_PER_CELL_F32 * cells / per_launch_s / 1e9
-    traffic = profiled_traffic()
+    traffic = profiled_traffic(w.nx if w.nx == w.ny else -1)
     grid.close()
 
     line = {"metric": "cell_updates_per_s", "value": value, "unit": "cell-updates/s", "n_gpus": world,

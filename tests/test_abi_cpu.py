@@ -47,7 +47,7 @@ def _params(**kw):
 @pytest.mark.parametrize("field,value", [("nx", 2), ("ny", 1), ("dx", 0.0), ("dt", -1.0),
                                          ("gamma", 1.0), ("precision", 7), ("bc_x", 3),
                                          ("kernel", 9), ("tile", 8), ("tile", -1),
-                                         ("Pr", float("nan"))])
+                                         ("Pr", float("nan")), ("advection", 2), ("advection", -1)])
 def test_invalid_params_rejected(lib, field, value):
     p, w = _params(**{field: value})
     h = ctypes.c_void_p()
@@ -76,6 +76,29 @@ def test_null_pointers_rejected(lib):
     assert lib.mrt_step(None, 1) == Bd.MRT_EINVAL
     assert lib.mrt_health(None) == Bd.MRT_EINVAL
     lib.mrt_destroy(None)
+
+
+def test_unsplit_operator_tiles_rejected(lib):
+    """The unsplit operator reads diagonal neighbours that tiles 2 and 3 do
+    not keep; the check runs before anything touches the device."""
+    for tile in (2, 3):
+        p, w = _params(advection=Bd.ADV_LW2D, kernel=Bd.KERNEL_TMA, tile=tile)
+        h = ctypes.c_void_p()
+        arr = [np.ascontiguousarray(a) for a in (w.rho, w.ux, w.uy, w.T)]
+        rc = lib.mrt_create(ctypes.byref(p), *(ctypes.c_void_p(a.ctypes.data) for a in arr), 0, None,
+                            ctypes.byref(h))
+        assert rc == Bd.MRT_EINVAL and "unsplit" in lib.mrt_last_error().decode()
+
+
+def test_null_handles_of_later_entry_points_rejected(lib):
+    t = ctypes.c_long()
+    n = ctypes.c_long()
+    assert lib.mrt_conserved_totals_async(None, None, ctypes.byref(t)) == Bd.MRT_EINVAL
+    assert lib.mrt_totals_wait(None, 0) == Bd.MRT_EINVAL
+    assert lib.mrt_save(None, b"/nonexistent/x") == Bd.MRT_EINVAL
+    assert lib.mrt_load(None, b"/nonexistent/x") == Bd.MRT_EINVAL
+    assert lib.mrt_debug_padding(None, ctypes.byref(n)) == Bd.MRT_EINVAL
+    assert lib.mrt_debug_wait_timeout(None) == Bd.MRT_EINVAL
 
 
 def test_status_strings(lib):
