@@ -21,7 +21,8 @@ class MRTRun(torch.autograd.Function):
         p = Bd.make_params(params["nx"], params["ny"], params["dx"], params["dt"], params["gamma"],
                            s.detach().cpu().numpy().astype(np.float64), params.get("bc_x", 0),
                            params.get("bc_y", 0), params.get("precision", Bd.FP32), 0.0,
-                           params.get("kernel", Bd.KERNEL_AUTO), params.get("tile", 0))
+                           params.get("kernel", Bd.KERNEL_AUTO), params.get("tile", 0),
+                           params.get("advection", Bd.ADV_LW))
         fields = [t.detach().to(dtype=torch.float64).contiguous() for t in (rho0, ux0, uy0, T0)]
         grid = Bd.Grid(p, *fields)
         grid.adjoint_record(*fields, nsteps, ckpt_every)
@@ -46,5 +47,9 @@ class MRTRun(torch.autograd.Function):
 
 
 def mrt_run(rho0, ux0, uy0, T0, s, params: dict, nsteps: int, ckpt_every: int = 50):
-    """rho after nsteps steps from f^eq(rho0, u0, T0), differentiable in all inputs."""
+    """rho after nsteps steps from f^eq(rho0, u0, T0), differentiable in all inputs.
+
+    params: nx, ny, dx, dt, gamma, and optionally bc_x, bc_y, precision,
+    kernel, tile and advection (Bd.ADV_LW, the method's operator, or
+    Bd.ADV_LW2D, the unsplit one)."""
     return MRTRun.apply(rho0, ux0, uy0, T0, s, params, nsteps, ckpt_every)

@@ -268,3 +268,42 @@ def test_full_size_kh_sampled_windows():
         want = oracle.step(g, fw)[:, 1:-1, 1:-1]
         got = f4[:, y0:y0 + n, x0:x0 + n].astype(np.float64)
         assert np.max(np.abs(got - want)) <= 2e-6 * np.max(np.abs(want)), (y0, x0)
+
+
+def test_autograd_function_with_the_unsplit_operator():
+    """torch.autograd through mrt_run(advection=ADV_LW2D) in FP64 gives the
+    oracle's ADV_LW2D gradients, and a central difference of the GPU loss in
+    one rate (s_6, relative step 1e-4) agrees with the rate gradient."""
+    import torch
+
+    from paper_1004_5442_gb300.autograd import mrt_run
+    w = W.smooth_vortex(n=40, nsteps=20, r0=0.15)
+    tgt = W.vortex_target(w)
+    dev = lambda a: torch.tensor(np.ascontiguousarray(a), device="cuda", requires_grad=True)
+    rho0, ux0, uy0, T0 = dev(w.rho), dev(w.ux), dev(w.uy), dev(w.T)
+    s = torch.tensor(w.s, device="cuda", requires_grad=True)
+    params = dict(nx=w.nx, ny=w.ny, dx=w.dx, dt=w.dt, gamma=w.gamma, precision=Bd.FP64,
+                  advection=Bd.ADV_LW2D)
+    target = torch.tensor(tgt, device="cuda")
+    rhoN = mrt_run(rho0, ux0, uy0, T0, s, params, w.nsteps, 6)
+    L = 0.5 * torch.sum((rhoN - target) ** 2) * w.dx ** 2
+    L.backward()
+    lg = _loss(tgt, w.dx)
+    ref = oracle.adjoint_run(w.nx, w.ny, w.dx, w.dt, w.b, w.s, w.rho, w.ux, w.uy, w.T, w.nsteps, lg,
+                             ckpt=6, advection=oracle.ADV_LW2D)
+    for t, r in zip((rho0, ux0, uy0, T0), ref[1:5]):
+        assert _rel(t.grad.cpu().numpy(), r) <= 1e-10
+    assert _rel(s.grad.cpu().numpy(), ref[5]) <= 1e-10
+
+    def loss_of(sv):
+        with torch.no_grad():
+            r = mrt_run(rho0, ux0, uy0, T0, torch.tensor(sv, device="cuda"), params, w.nsteps, 6)
+            return float(0.5 * torch.sum((r - target) ** 2) * w.dx ** 2)
+    k, h = 5, 1e-4
+    sp, sm = np.array(w.s), np.array(w.s)
+    sp[k] *= 1 + h
+    sm[k] *= 1 - h
+    fd = (loss_of(sp) - loss_of(sm)) / (2 * h * w.s[k])
+    got = float(s.grad[k])
+    scale = float(torch.max(torch.abs(s.grad * s.detach())))
+    assert abs(got - fd) * w.s[k] <= 1e-4 * abs(fd) * w.s[k] + 1e-6 * scale, (got, fd)
