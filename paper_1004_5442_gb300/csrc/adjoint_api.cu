@@ -38,6 +38,7 @@ void mrt_tape_free(mrt_tape* t) {
     cudaFree(t->scratch);
     delete[] t->seg_in;
     delete[] t->seg_out;
+    delete[] t->ck_in;
     delete t;
 }
 
@@ -83,7 +84,7 @@ extern "C" mrt_status mrt_adjoint_record(mrt_grid* g, const double* rho0, const 
         t->nparts = t->adj_gx * t->adj_gy;
     }
     A_TRY(cudaMalloc(&t->ck, t->state_bytes * (size_t)t->nck));
-    A_TRY(cudaMalloc(&t->seg, t->state_bytes * (size_t)t->K));
+    A_TRY(cudaMalloc(&t->seg, t->state_bytes * (size_t)std::max(t->K - 1, 1)));
     A_TRY(cudaMalloc(&t->lam[0], t->state_bytes));
     A_TRY(cudaMalloc(&t->lam[1], t->state_bytes));
     A_TRY(cudaMalloc(&t->gxb, sizeof(double) * 32 * (size_t)g->L.ny));
@@ -101,9 +102,15 @@ extern "C" mrt_status mrt_adjoint_record(mrt_grid* g, const double* rho0, const 
     if (g->kernel == MRT_KERNEL_TMA) {
         t->seg_in = new (std::nothrow) CUtensorMap[t->K];
         t->seg_out = new (std::nothrow) CUtensorMap[t->K];
-        if (!t->seg_in || !t->seg_out) return mrt_fail(MRT_ENOMEM, "host allocation failed");
-        for (int j = 0; j < t->K; ++j) {
-            st = mrt_encode_maps(g, buf_at(t->seg, t->state_bytes, j), &t->seg_in[j], &t->seg_out[j]);
+        t->ck_in = new (std::nothrow) CUtensorMap[t->nck];
+        if (!t->seg_in || !t->seg_out || !t->ck_in) return mrt_fail(MRT_ENOMEM, "host allocation failed");
+        for (int j = 1; j < t->K; ++j) {
+            st = mrt_encode_maps(g, buf_at(t->seg, t->state_bytes, j - 1), &t->seg_in[j], &t->seg_out[j]);
+            if (st != MRT_OK) return st;
+        }
+        for (int c = 0; c < t->nck; ++c) {
+            CUtensorMap unused;
+            st = mrt_encode_maps(g, buf_at(t->ck, t->state_bytes, c), &t->ck_in[c], &unused);
             if (st != MRT_OK) return st;
         }
     }
@@ -111,7 +118,7 @@ extern "C" mrt_status mrt_adjoint_record(mrt_grid* g, const double* rho0, const 
     // periodic axes the recompute steps write every ghost they later read,
     // and segment buffer 0 is a full checkpoint copy)
     if (g->p.bc_x != MRT_BC_PERIODIC || g->p.bc_y != MRT_BC_PERIODIC)
-        for (int j = 0; j < t->K; ++j)
+        for (int j = 0; j + 1 < t->K; ++j)
             A_TRY(cudaMemcpyAsync(buf_at(t->seg, t->state_bytes, j), g->f[g->cur], t->state_bytes,
                                   cudaMemcpyDeviceToDevice, g->stream));
     if (t->adj_tma)
@@ -166,20 +173,26 @@ static mrt_status backward_impl(mrt_grid* g, const double* drho, double* outs[4]
     for (int c = t->nck - 1; c >= 0; --c) {
         const long s0 = (long)c * t->K;
         const int len = (int)std::min<long>(t->K, t->nsteps - s0);
-        A_TRY(cudaMemcpyAsync(t->seg, buf_at(t->ck, t->state_bytes, c), t->state_bytes, cudaMemcpyDeviceToDevice,
-                              g->stream));
+        // state j of the segment: the checkpoint itself for j = 0 (read only,
+        // never copied), a recomputed buffer for j >= 1
+        auto state = [&](int j) -> char* {
+            return j == 0 ? buf_at(t->ck, t->state_bytes, c) : buf_at(t->seg, t->state_bytes, j - 1);
+        };
+        auto load_map = [&](int j) -> const CUtensorMap* {
+            if (!t->seg_in) return nullptr;
+            return j == 0 ? &t->ck_in[c] : &t->seg_in[j];
+        };
         for (int j = 0; j + 1 < len; ++j) {
-            st = step_between<T>(g, buf_at(t->seg, t->state_bytes, j), buf_at(t->seg, t->state_bytes, j + 1),
-                                 t->seg_in ? &t->seg_in[j] : nullptr, t->seg_out ? &t->seg_out[j + 1] : nullptr,
+            st = step_between<T>(g, state(j), state(j + 1), load_map(j), t->seg_out ? &t->seg_out[j + 1] : nullptr,
                                  false);
             if (st != MRT_OK) return st;
         }
         for (int j = len - 1; j >= 0; --j) {
             a.lam_in = static_cast<const T*>(t->lam[cur]);
-            a.f = reinterpret_cast<const T*>(buf_at(t->seg, t->state_bytes, j));
+            a.f = reinterpret_cast<const T*>(state(j));
             a.lam_out = static_cast<T*>(t->lam[cur ^ 1]);
             if (t->adj_tma)
-                A_TRY(launch_adjoint_tma<T>(&t->lam_in[cur], &t->seg_in[j], &t->lam_out[cur ^ 1], a, g->xt, t->adj_gx,
+                A_TRY(launch_adjoint_tma<T>(&t->lam_in[cur], load_map(j), &t->lam_out[cur ^ 1], a, g->xt, t->adj_gx,
                                             t->adj_gy, t->adj_rows, g->stream));
             else
                 A_TRY(launch_adjoint_step<T>(a, g->xt, g->stream));

@@ -184,9 +184,11 @@ struct mrt_tape {
     int nck = 0;                // checkpoints: f at steps 0, K, 2K, ...
     size_t state_bytes = 0;     // one padded buffer
     void* ck = nullptr;         // nck buffers
-    void* seg = nullptr;        // K buffers for a recomputed segment
-    CUtensorMap* seg_in = nullptr;   // load maps of the segment buffers
-    CUtensorMap* seg_out = nullptr;  // store maps of the segment buffers
+    void* seg = nullptr;        // K - 1 buffers: states 1 .. K-1 of a recomputed segment
+                                // (state 0 is read from its checkpoint buffer)
+    CUtensorMap* seg_in = nullptr;   // load maps of the segment states, index 1 .. K-1
+    CUtensorMap* seg_out = nullptr;  // store maps of the segment states, index 1 .. K-1
+    CUtensorMap* ck_in = nullptr;    // load maps of the checkpoint buffers
     void* lam[2] = {nullptr, nullptr};
     double* gxb = nullptr;
     double* gyb = nullptr;
