@@ -201,21 +201,25 @@ mrt_status mrt_info(const mrt_grid *g, long *steps, long *pitch, long *plane_str
  *   dL/df^n     = lam + Adv^T(lam) - M^T (I - J)^T S mu,
  *   dL/dsigma_k += -mu_k (fhat_k - fhat^eq_k)      (sigma_k = s_k dt),
  * where J = d fhat^eq / d fhat (Appendix equilibria, non-zero only through
- * rho, j, e) and Adv^T is the Lax-Wendroff stencil with c -> -c.  Fixed
+ * rho, j, e) and Adv^T is the Lax-Wendroff stencil with c -> -c (the
+ * unsplit operator's mixed term is its own transpose).  Fixed
  * ghosts hold the initial f of their cells, so their adjoints are added to
  * dL/df^0 there; f^0 = M^-1 fhat^eq(rho, u, T) is differentiated last.
  *
  * mrt_adjoint_record: sets f = f^eq(rho0, ux0, uy0, T0) (fields [ny][nx]
  * doubles, on the device if on_device), runs nsteps >= 1 steps keeping f
  * every ckpt_every >= 1 steps on the device (memory: ceil(nsteps/ckpt_every)
- * + ckpt_every + 2 states), and leaves f^N in the grid.  Synchronises once.
+ * checkpoints + max(ckpt_every - 1, 1) recomputed segment states + 2 adjoint
+ * states), and leaves f^N in the grid.  Synchronises once.  With
+ * MRT_ADV_LW2D the reverse sweep transposes the unsplit operator.
  *
  * mrt_adjoint_backward: after a record, from dL/drho_N ([ny][nx] doubles)
  * writes dL/drho_0, dL/dux_0, dL/duy_0, dL/dT_0 ([ny][nx] doubles; any may
  * be NULL) and g_s[16] = dL/ds_1..16 (host; g_s[0..3] = 0: those rates act
  * on conserved moments).  Each segment of ckpt_every steps is recomputed
  * from its checkpoint before its reverse sweep.  Gradients are with respect
- * to the 16 rates as used (after the Pr rule of mrt_params).  Synchronises.
+ * to the 16 rates as used (after the Pr rule of mrt_params).  The first
+ * state of a segment is read from its checkpoint in place.  Synchronises.
  *
  * mrt_adjoint_step: one reverse step on caller states f^n and lam_next =
  * dL/df^{n+1} ([16][ny][nx], grid precision), writing lam = dL/df^n and
