@@ -12,7 +12,7 @@
 #include <cstring>
 #include <new>
 
-#include "internal.h"
+#include "host_state.h"
 
 using namespace mrt;
 

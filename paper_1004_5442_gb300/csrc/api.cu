@@ -9,7 +9,7 @@
 #include <new>
 
 #include "../../include/mrtfdlb.h"
-#include "internal.h"
+#include "host_state.h"
 
 using namespace mrt;
 

@@ -17,7 +17,7 @@
 #include <new>
 #include <vector>
 
-#include "internal.h"
+#include "host_state.h"
 #include "step_strip.cuh"
 
 using namespace mrt;

@@ -13,7 +13,7 @@
 #include <cstring>
 #include <vector>
 
-#include "internal.h"
+#include "host_state.h"
 
 using namespace mrt;
 

@@ -11,7 +11,7 @@
 //    its 2 s limit) and sets the timeout flag, which mrt_health reports as
 //    MRT_ETIMEOUT.  It exercises the failure path of every TMA kernel without
 //    a fault, a trap or an unbounded wait.
-#include "internal.h"
+#include "host_state.h"
 #include "tma.cuh"
 
 using namespace mrt;
