@@ -140,7 +140,9 @@ mrt_status mrt_get_macro(mrt_grid *g, double *rho, double *ux, double *uy, doubl
  * MRT_EUNSTABLE if the health flag has tripped (out is still written). */
 mrt_status mrt_conserved_totals(mrt_grid *g, double out[4]);
 
-/* The same totals without waiting: enqueues on the grid's stream a copy of
+/* The same totals without waiting.  The library reduces the totals of a
+ * step on a side stream of the grid, so the grid's stream goes on with the
+ * next steps meanwhile; this call enqueues, behind that reduction, a copy of
  * the current state's totals and health flag word into dst[5], caller-owned
  * page-locked host memory (cudaMallocHost / cudaHostAlloc /
  * cudaHostRegister; pageable memory makes the copy synchronous), and
@@ -150,8 +152,8 @@ mrt_status mrt_conserved_totals(mrt_grid *g, double out[4]);
  * wait ran out).  dst is valid once mrt_totals_wait(g, *ticket) returns
  * MRT_OK (or after any synchronisation of the grid's stream), and must stay
  * allocated until then.  Steps enqueued after the call do not disturb the
- * copy (stream order), so a caller can launch step n+1 before it waits for
- * the totals of step n and keep the GPU busy.  Errors: MRT_EINVAL (NULL
+ * copy, so a caller can launch step n+1 before it waits for the totals of
+ * step n and keep the GPU busy.  Errors: MRT_EINVAL (NULL
  * argument), MRT_ECUDA. */
 mrt_status mrt_conserved_totals_async(mrt_grid *g, double *dst, long *ticket);
 /* Wait until the copy of a ticket has landed.  The grid keeps the last 8

@@ -359,8 +359,10 @@ __global__ void __launch_bounds__(FINAL_THREADS) totals_final_kernel(const doubl
     if (threadIdx.x == 0) out[4] = (double)*flag;
 }
 
-// Both passes on the grid's stream; result in g->totals_dev.
-static cudaError_t reduce_totals(mrt_grid* g, int nparts) {
+// Both passes on the grid's side stream: partials buffer b into totals
+// buffer b (block_sums is used by one reduction at a time, in the side
+// stream's order).
+static cudaError_t reduce_totals_on(mrt_grid* g, int b, int nparts) {
     int chunk = FINAL_PER_BLOCK;
     int blocks = (nparts + chunk - 1) / chunk;
     if (blocks > FINAL_MAX_BLOCKS) {
@@ -368,10 +370,38 @@ static cudaError_t reduce_totals(mrt_grid* g, int nparts) {
         chunk = (nparts + blocks - 1) / blocks;
     }
     if (blocks < 1) blocks = 1;
-    totals_pass_kernel<<<blocks, FINAL_THREADS, 0, g->stream>>>(g->partials, nparts, chunk, g->block_sums);
-    totals_final_kernel<<<1, FINAL_THREADS, 0, g->stream>>>(g->block_sums, blocks, g->p.dx * g->p.dx, g->flag,
-                                                            g->totals_dev);
+    totals_pass_kernel<<<blocks, FINAL_THREADS, 0, g->tstream>>>(g->partials + (size_t)b * 4 * g->max_parts, nparts,
+                                                                 chunk, g->block_sums);
+    totals_final_kernel<<<1, FINAL_THREADS, 0, g->tstream>>>(g->block_sums, blocks, g->p.dx * g->p.dx, g->flag,
+                                                             g->totals_dev + 5 * b);
     return cudaGetLastError();
+}
+
+// Partials buffer for the next totals reduction: the grid's stream first
+// waits until the side stream has finished reading it.
+static cudaError_t begin_totals(mrt_grid* g, double** partials) {
+    const int b = g->tnext;
+    if (g->red_pending[b]) {
+        cudaError_t e = cudaStreamWaitEvent(g->stream, g->ev_red[b], 0);
+        if (e != cudaSuccess) return e;
+    }
+    *partials = g->partials + (size_t)b * 4 * g->max_parts;
+    return cudaSuccess;
+}
+
+// After the partials of the next reduction were enqueued on the grid's
+// stream: the side stream waits for them and reduces them.
+static cudaError_t end_totals(mrt_grid* g, int nparts) {
+    const int b = g->tnext;
+    cudaError_t e;
+    if ((e = cudaEventRecord(g->ev_step[b], g->stream)) != cudaSuccess) return e;
+    if ((e = cudaStreamWaitEvent(g->tstream, g->ev_step[b], 0)) != cudaSuccess) return e;
+    if ((e = reduce_totals_on(g, b, nparts)) != cudaSuccess) return e;
+    if ((e = cudaEventRecord(g->ev_red[b], g->tstream)) != cudaSuccess) return e;
+    g->red_pending[b] = true;
+    g->tlast = b;
+    g->tnext = b ^ 1;
+    return cudaSuccess;
 }
 
 int grid_for(long n, int threads, int cap = 4096) {
@@ -457,6 +487,7 @@ static void release(mrt_grid* g) {
     cudaGetDevice(&prev);
     cudaSetDevice(g->device);
     if (g->stream) cudaStreamSynchronize(g->stream);
+    if (g->tstream) cudaStreamSynchronize(g->tstream);
     cudaFree(g->f[0]);
     cudaFree(g->f[1]);
     cudaFree(g->flag);
@@ -467,6 +498,11 @@ static void release(mrt_grid* g) {
     cudaFreeHost(g->host_stage);
     for (int k = 0; k < mrt_grid::kTotalsEvents; ++k)
         if (g->tev[k]) cudaEventDestroy(g->tev[k]);
+    for (int b = 0; b < 2; ++b) {
+        if (g->ev_step[b]) cudaEventDestroy(g->ev_step[b]);
+        if (g->ev_red[b]) cudaEventDestroy(g->ev_red[b]);
+    }
+    if (g->tstream) cudaStreamDestroy(g->tstream);
     cudaFree(g->macro_tmp);
     mrt_tape_free(g->tape);
     if (prev >= 0) cudaSetDevice(prev);
@@ -565,13 +601,19 @@ extern "C" mrt_status mrt_create(const mrt_params* params, const double* rho, co
         return bail(fail(MRT_ECUDA, "memset: %s", cudaGetErrorString(e)));
     if ((e = cudaMalloc(&g->flag, sizeof(unsigned))) != cudaSuccess ||
         (e = cudaMemsetAsync(g->flag, 0, sizeof(unsigned), g->stream)) != cudaSuccess ||
-        (e = cudaMalloc(&g->totals_dev, 5 * sizeof(double))) != cudaSuccess ||
+        (e = cudaMalloc(&g->totals_dev, 2 * 5 * sizeof(double))) != cudaSuccess ||
         (e = cudaMalloc(&g->block_sums, 4 * sizeof(double) * FINAL_MAX_BLOCKS)) != cudaSuccess ||
         (e = cudaMallocHost(&g->host_stage, 8 * sizeof(double))) != cudaSuccess)
         return bail(fail(MRT_ENOMEM, "cudaMalloc: %s", cudaGetErrorString(e)));
     for (int k = 0; k < mrt_grid::kTotalsEvents; ++k)
         if ((e = cudaEventCreateWithFlags(&g->tev[k], cudaEventDisableTiming)) != cudaSuccess)
             return bail(fail(MRT_ECUDA, "cudaEventCreate: %s", cudaGetErrorString(e)));
+    for (int b = 0; b < 2; ++b)
+        if ((e = cudaEventCreateWithFlags(&g->ev_step[b], cudaEventDisableTiming)) != cudaSuccess ||
+            (e = cudaEventCreateWithFlags(&g->ev_red[b], cudaEventDisableTiming)) != cudaSuccess)
+            return bail(fail(MRT_ECUDA, "cudaEventCreate: %s", cudaGetErrorString(e)));
+    if ((e = cudaStreamCreateWithFlags(&g->tstream, cudaStreamNonBlocking)) != cudaSuccess)
+        return bail(fail(MRT_ECUDA, "cudaStreamCreate: %s", cudaGetErrorString(e)));
 
     // kernel choice and launch geometry
     // AUTO: the TMA strip kernel, except for small FP64 grids, where the
@@ -633,7 +675,7 @@ extern "C" mrt_status mrt_create(const mrt_params* params, const double* rho, co
     g->parts = parts;
     const int red_parts = grid_for((long)params->nx * params->ny, RED_THREADS, 1024);
     g->max_parts = parts > red_parts ? parts : red_parts;
-    if ((e = cudaMalloc(&g->partials, 4 * sizeof(double) * (size_t)g->max_parts)) != cudaSuccess)
+    if ((e = cudaMalloc(&g->partials, 2 * 4 * sizeof(double) * (size_t)g->max_parts)) != cudaSuccess)
         return bail(fail(MRT_ENOMEM, "cudaMalloc partials: %s", cudaGetErrorString(e)));
 
     if (kernel == MRT_KERNEL_TMA) {
@@ -747,6 +789,7 @@ static mrt_status step_impl(mrt_grid* g, long nsteps) {
         a.in = static_cast<const T*>(g->f[g->cur]);
         a.out = static_cast<T*>(g->f[g->cur ^ 1]);
         queue_args(g, a);
+        if (totals) CUDA_TRY(begin_totals(g, &a.partials));
         cudaError_t e;
         if (g->kernel == MRT_KERNEL_TMA) {
             e = launch_step_tma<T>(g->tile, g->xt, &g->maps[g->cur], &g->maps_out[g->cur ^ 1], a, g->tma_grid_x,
@@ -755,7 +798,7 @@ static mrt_status step_impl(mrt_grid* g, long nsteps) {
             e = launch_step_direct<T>(a, g->xt, totals, g->stream);
         }
         if (e != cudaSuccess) return fail(MRT_ECUDA, "step launch: %s", cudaGetErrorString(e));
-        if (totals) CUDA_TRY(reduce_totals(g, g->parts));
+        if (totals) CUDA_TRY(end_totals(g, g->parts));
         g->cur ^= 1;
         g->steps++;
     }
@@ -801,10 +844,12 @@ template <class T>
 static mrt_status totals_impl(mrt_grid* g) {
     const long n = (long)g->L.nx * g->L.ny;
     const int blocks = grid_for(n, RED_THREADS, 1024);
+    double* parts = nullptr;
+    CUDA_TRY(begin_totals(g, &parts));
     totals_partial_kernel<T><<<blocks, RED_THREADS, 0, g->stream>>>(g->L, static_cast<const T*>(g->f[g->cur]),
-                                                                     g->partials);
+                                                                     parts);
     CUDA_TRY(cudaGetLastError());
-    CUDA_TRY(reduce_totals(g, blocks));
+    CUDA_TRY(end_totals(g, blocks));
     g->totals_fresh = true;
     return MRT_OK;
 }
@@ -815,7 +860,9 @@ extern "C" mrt_status mrt_conserved_totals(mrt_grid* g, double out[4]) {
         mrt_status st = g->fp64 ? totals_impl<double>(g) : totals_impl<float>(g);
         if (st != MRT_OK) return st;
     }
-    CUDA_TRY(cudaMemcpyAsync(g->host_stage, g->totals_dev, 5 * sizeof(double), cudaMemcpyDeviceToHost, g->stream));
+    CUDA_TRY(cudaMemcpyAsync(g->host_stage, g->totals_dev + 5 * g->tlast, 5 * sizeof(double),
+                             cudaMemcpyDeviceToHost, g->tstream));
+    CUDA_TRY(cudaStreamSynchronize(g->tstream));
     CUDA_TRY(cudaStreamSynchronize(g->stream));
     for (int k = 0; k < 4; ++k) out[k] = g->host_stage[k];
     const unsigned flag = (unsigned)g->host_stage[4];
@@ -830,9 +877,12 @@ extern "C" mrt_status mrt_conserved_totals_async(mrt_grid* g, double* dst, long*
         mrt_status st = g->fp64 ? totals_impl<double>(g) : totals_impl<float>(g);
         if (st != MRT_OK) return st;
     }
-    CUDA_TRY(cudaMemcpyAsync(dst, g->totals_dev, 5 * sizeof(double), cudaMemcpyDeviceToHost, g->stream));
+    // on the side stream, after the reduction of the latest totals; the
+    // grid's stream runs on meanwhile
+    CUDA_TRY(cudaMemcpyAsync(dst, g->totals_dev + 5 * g->tlast, 5 * sizeof(double), cudaMemcpyDeviceToHost,
+                             g->tstream));
     const long t = g->tickets;
-    CUDA_TRY(cudaEventRecord(g->tev[t % mrt_grid::kTotalsEvents], g->stream));
+    CUDA_TRY(cudaEventRecord(g->tev[t % mrt_grid::kTotalsEvents], g->tstream));
     g->tickets = t + 1;
     *ticket = t;
     return MRT_OK;

@@ -46,9 +46,19 @@ struct mrt_grid {
     int device = 0;
     cudaStream_t stream = nullptr;
     unsigned* flag = nullptr;        // device flag word
-    double* partials = nullptr;      // 4 doubles per CTA
+    double* partials = nullptr;      // 2 buffers of max_parts x 4 doubles (block / warp partials)
     int max_parts = 0;
-    double* totals_dev = nullptr;    // 4 totals + a copy of the flag word, as doubles
+    double* totals_dev = nullptr;    // 2 buffers of 4 totals + a copy of the flag word, as doubles
+    // The totals reduction and its read-back run on a side stream: a step
+    // that reduces totals writes its partials into buffer tnext and goes on;
+    // the side stream waits for it (ev_step), sums the partials into
+    // totals_dev buffer tnext (ev_red), while the next steps already run.
+    // A later totals step writing the same partials buffer waits for ev_red.
+    cudaStream_t tstream = nullptr;
+    cudaEvent_t ev_step[2] = {}, ev_red[2] = {};
+    bool red_pending[2] = {false, false};
+    int tnext = 0;                   // buffer of the next totals reduction
+    int tlast = 0;                   // buffer holding the latest totals
     double* block_sums = nullptr;    // first-pass sums of the totals reduction
     double* host_stage = nullptr;    // pinned host copy of totals_dev (one small DMA per read)
     static constexpr int kTotalsEvents = 8;
