@@ -124,7 +124,10 @@ mrt_status mrt_create(const mrt_params *params, const double *rho, const double 
 
 /* Advance nsteps >= 0 time steps (Eq. 3, forward Euler + Lax-Wendroff).
  * Asynchronous.  The conserved totals of the final state are reduced in the
- * same pass (FP64 block partials) and kept for mrt_conserved_totals. */
+ * same pass (FP64 block partials) and kept for mrt_conserved_totals.  All
+ * but the last step of a call are replayed from CUDA graphs of two steps,
+ * captured on the first call that needs them (a grid keeps up to four);
+ * the results do not depend on it. */
 mrt_status mrt_step(mrt_grid *g, long nsteps);
 
 /* Macroscopic fields of the current state: rho = fhat_1, u = j/rho,

@@ -503,6 +503,9 @@ static void release(mrt_grid* g) {
         if (g->ev_red[b]) cudaEventDestroy(g->ev_red[b]);
     }
     if (g->tstream) cudaStreamDestroy(g->tstream);
+    for (int c = 0; c < 2; ++c)
+        for (int q = 0; q < 2; ++q)
+            if (g->pair_exec[c][q]) cudaGraphExecDestroy(g->pair_exec[c][q]);
     cudaFree(g->macro_tmp);
     mrt_tape_free(g->tape);
     if (prev >= 0) cudaSetDevice(prev);
@@ -774,8 +777,30 @@ template mrt_status step_between<double>(mrt_grid*, const void*, void*, const CU
 mrt_status mrt_reinit(mrt_grid* g, const double* rho, const double* ux, const double* uy, const double* T,
                       int on_device);
 
+// One step of the grid on stream st (the last one of a call also reduces
+// totals), advancing cur, the queue parity and the step count.
 template <class T>
-static mrt_status step_impl(mrt_grid* g, long nsteps) {
+static mrt_status enqueue_step(mrt_grid* g, StepArgs<T>& a, bool totals, cudaStream_t st) {
+    a.in = static_cast<const T*>(g->f[g->cur]);
+    a.out = static_cast<T*>(g->f[g->cur ^ 1]);
+    queue_args(g, a);
+    if (totals) CUDA_TRY(begin_totals(g, &a.partials));
+    cudaError_t e;
+    if (g->kernel == MRT_KERNEL_TMA) {
+        e = launch_step_tma<T>(g->tile, g->xt, &g->maps[g->cur], &g->maps_out[g->cur ^ 1], a, g->tma_grid_x,
+                               g->tma_grid_y, totals, st);
+    } else {
+        e = launch_step_direct<T>(a, g->xt, totals, st);
+    }
+    if (e != cudaSuccess) return fail(MRT_ECUDA, "step launch: %s", cudaGetErrorString(e));
+    if (totals) CUDA_TRY(end_totals(g, g->parts));
+    g->cur ^= 1;
+    g->steps++;
+    return MRT_OK;
+}
+
+template <class T>
+static StepArgs<T> step_args(mrt_grid* g) {
     StepArgs<T> a;
     a.L = g->L;
     a.per_x = g->p.bc_x == MRT_BC_PERIODIC;
@@ -784,25 +809,63 @@ static mrt_status step_impl(mrt_grid* g, long nsteps) {
     a.partials = g->partials;
     a.flag = g->flag;
     if constexpr (sizeof(T) == 8) a.k = g->kd; else a.k = g->kf;
-    for (long s = 0; s < nsteps; ++s) {
-        const bool totals = s == nsteps - 1;
-        a.in = static_cast<const T*>(g->f[g->cur]);
-        a.out = static_cast<T*>(g->f[g->cur ^ 1]);
-        queue_args(g, a);
-        if (totals) CUDA_TRY(begin_totals(g, &a.partials));
-        cudaError_t e;
-        if (g->kernel == MRT_KERNEL_TMA) {
-            e = launch_step_tma<T>(g->tile, g->xt, &g->maps[g->cur], &g->maps_out[g->cur ^ 1], a, g->tma_grid_x,
-                                   g->tma_grid_y, totals, g->stream);
-        } else {
-            e = launch_step_direct<T>(a, g->xt, totals, g->stream);
-        }
-        if (e != cudaSuccess) return fail(MRT_ECUDA, "step launch: %s", cudaGetErrorString(e));
-        if (totals) CUDA_TRY(end_totals(g, g->parts));
-        g->cur ^= 1;
-        g->steps++;
+    return a;
+}
+
+// Graph of two plain steps from the grid's present (cur, queue parity),
+// captured on the side stream (never the legacy stream) and instantiated;
+// after two steps cur and the parity are back where they started, so one
+// graph serves every pair of steps begun in that state.
+template <class T>
+static mrt_status pair_graph(mrt_grid* g, cudaGraphExec_t* out) {
+    const int cur0 = g->cur, q0 = g->qpar;
+    const long steps0 = g->steps;
+    StepArgs<T> a = step_args<T>(g);
+    cudaGraph_t graph = nullptr;
+    CUDA_TRY(cudaStreamBeginCapture(g->tstream, cudaStreamCaptureModeThreadLocal));
+    mrt_status st = enqueue_step<T>(g, a, false, g->tstream);
+    if (st == MRT_OK) st = enqueue_step<T>(g, a, false, g->tstream);
+    const cudaError_t e = cudaStreamEndCapture(g->tstream, &graph);
+    g->cur = cur0;
+    g->qpar = q0;
+    g->steps = steps0;
+    if (st != MRT_OK || e != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        return st != MRT_OK ? st : fail(MRT_ECUDA, "step graph capture: %s", cudaGetErrorString(e));
     }
-    if (nsteps > 0) g->totals_fresh = true;
+    const cudaError_t ei = cudaGraphInstantiate(out, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ei != cudaSuccess) return fail(MRT_ECUDA, "step graph: %s", cudaGetErrorString(ei));
+    return MRT_OK;
+}
+
+// All but the last step of a call replay two-step graphs (fewer launch gaps
+// on small grids); the last step, which also reduces totals, and an odd one
+// before it are launched directly.
+template <class T>
+static mrt_status step_impl(mrt_grid* g, long nsteps) {
+    StepArgs<T> a = step_args<T>(g);
+    long plain = nsteps - 1;
+    if (plain >= 2) {
+        cudaGraphExec_t& ex = g->pair_exec[g->cur][g->qpar & 1];
+        if (!ex) {
+            mrt_status st = pair_graph<T>(g, &ex);
+            if (st != MRT_OK) return st;
+        }
+        const long pairs = plain / 2;
+        for (long k = 0; k < pairs; ++k) CUDA_TRY(cudaGraphLaunch(ex, g->stream));
+        g->steps += 2 * pairs;
+        plain -= 2 * pairs;
+    }
+    for (long s = 0; s < plain; ++s) {
+        mrt_status st = enqueue_step<T>(g, a, false, g->stream);
+        if (st != MRT_OK) return st;
+    }
+    if (nsteps > 0) {
+        mrt_status st = enqueue_step<T>(g, a, true, g->stream);
+        if (st != MRT_OK) return st;
+        g->totals_fresh = true;
+    }
     return MRT_OK;
 }
 

@@ -58,6 +58,9 @@ struct mrt_grid {
     cudaEvent_t ev_step[2] = {}, ev_red[2] = {};
     bool red_pending[2] = {false, false};
     int tnext = 0;                   // buffer of the next totals reduction
+    // Graphs of two plain steps, by (cur, queue parity) at their start
+    // (mrt_step replays them for all but the last step of a call).
+    cudaGraphExec_t pair_exec[2][2] = {};
     int tlast = 0;                   // buffer holding the latest totals
     double* block_sums = nullptr;    // first-pass sums of the totals reduction
     double* host_stage = nullptr;    // pinned host copy of totals_dev (one small DMA per read)

@@ -31,10 +31,13 @@ struct Acc<double> {
     __device__ __forceinline__ double value() const { return hi; }
 };
 
-// CTA-wide FP64 sum of 4 values; thread 0 writes them to dst[0..3].
+// CTA-wide FP64 sum of 4 values; thread 0 writes them to dst[0..3].  Lanes
+// and warps follow the linear thread index, so 2-D blocks (the direct
+// kernel's 32 x BY) reduce correctly.
 __device__ __forceinline__ void block_sum4(double v[4], double* dst) {
     __shared__ double red[32][4];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int t = threadIdx.y * blockDim.x + threadIdx.x;
+    const int lane = t & 31, warp = t >> 5;
     const int nwarps = (blockDim.x * blockDim.y + 31) >> 5;
 #pragma unroll
     for (int q = 0; q < 4; ++q)
@@ -42,7 +45,7 @@ __device__ __forceinline__ void block_sum4(double v[4], double* dst) {
     if (lane == 0)
         for (int q = 0; q < 4; ++q) red[warp][q] = v[q];
     __syncthreads();
-    if (threadIdx.x == 0) {
+    if (t == 0) {
         for (int q = 0; q < 4; ++q) {
             double s = 0.0;
             for (int w = 0; w < nwarps; ++w) s += red[w][q];

@@ -341,3 +341,51 @@ def test_grids_on_concurrent_streams():
     finally:
         ga.close()
         gb.close()
+
+
+@pytest.mark.parametrize("kernel,tile", [(Bd.KERNEL_TMA, 4), (Bd.KERNEL_TMA, 6), (Bd.KERNEL_DIRECT, 0)])
+@pytest.mark.parametrize("prec", [Bd.FP32, Bd.FP64])
+def test_graph_replayed_steps_match_single_steps(kernel, tile, prec):
+    """mrt_step(n) replays two-step CUDA graphs for all but its last step;
+    the states are bit for bit those of n calls of one step each (every
+    step launched directly), for odd and even n, and after a reverse-mode
+    run has shifted the work-queue counter parity against the buffer index
+    (a graph is kept per starting state)."""
+    w = W.random_smooth(700, 150, seed=11, amp=0.1, bc_x=Bd.BC_FIXED_EQ)
+    with Bd.Grid.from_workload(w, precision=prec, kernel=kernel, tile=tile) as a, \
+            Bd.Grid.from_workload(w, precision=prec, kernel=kernel, tile=tile) as b:
+        for n in (7, 6, 5):
+            a.step(n)
+            for _ in range(n):
+                b.step(1)
+            np.testing.assert_array_equal(a.get_f(), b.get_f())
+            np.testing.assert_array_equal(a.totals(), b.totals())
+        f = a.get_f()
+        for g in (a, b):
+            # the record's steps move cur and the parity together; the
+            # backward's segment recompute moves the parity alone
+            g.adjoint_record(w.rho, w.ux, w.uy, w.T, 3, 2)
+            g.adjoint_backward(np.full((w.ny, w.nx), w.dx * w.dx))
+            g.set_f(f)
+        a.step(9)
+        for _ in range(9):
+            b.step(1)
+        np.testing.assert_array_equal(a.get_f(), b.get_f())
+        assert a.health() == Bd.MRT_OK and a.info()["steps"] == b.info()["steps"]
+
+
+@pytest.mark.parametrize("prec,tol", [(Bd.FP64, 1e-12), (Bd.FP32, 1e-6)])
+def test_direct_kernel_totals_with_multi_row_blocks(prec, tol):
+    """The direct kernel runs 32 x BY blocks (BY up to 8); the totals its
+    last step reduces match the oracle's totals of the same state (a block
+    reduction that took warps from threadIdx.x alone summed one warp of
+    each block and stale shared memory)."""
+    for nx, ny in ((700, 150), (360, 100)):
+        w = W.random_smooth(nx, ny, seed=5, amp=0.1)
+        g = run_oracle(w, 3)
+        want = oracle.totals(g)
+        _, _, _, M, _ = oracle.model()
+        scale = np.array([np.sum(np.abs(np.tensordot(M[k], g.f, 1))) * w.dx ** 2 for k in range(4)])
+        with run_gpu(w, prec, Bd.KERNEL_DIRECT, nsteps=3) as grid:
+            got = grid.totals()
+        assert np.all(np.abs(got - want) <= tol * scale), (nx, ny, got, want)
