@@ -351,10 +351,11 @@ def run_ours(args):
                          "frac": achieved / peak, "traffic": traffic,
                          "peak_source": f"{peak_kind} hbm_gbs",
                          "algorithmic_bytes_per_launch": BYTES_PER_CELL_F32 * cells,
-                         "timing": "CUDA events on the launching stream over K step launches (the last one also "
-                      "reduces totals) and the two totals passes"},
-            # K step launches, the last one reducing totals, and the two
-            # passes of the totals reduction
+                         "timing": "CUDA events on the grid's stream over K steps (K - 1 replayed from two-step "
+                                   "CUDA graphs, the last one also computing the totals partials, whose two-pass "
+                                   "reduction the library enqueues on the grid's side stream)"},
+            # K step kernels, the last one computing the totals partials, and
+            # the two passes of the totals reduction (side stream)
             "gpu_launches": args.steps + 2,
             "clocks": clk.summary()}
 
