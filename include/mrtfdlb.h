@@ -127,7 +127,16 @@ mrt_status mrt_create(const mrt_params *params, const double *rho, const double 
  * same pass (FP64 block partials) and kept for mrt_conserved_totals.  All
  * but the last step of a call are replayed from CUDA graphs of two steps,
  * captured on the first call that needs them (a grid keeps up to four);
- * the results do not depend on it. */
+ * the results do not depend on it.
+ * While the grid's stream is being captured into a caller's CUDA graph, the
+ * call instead launches every step directly and reduces the totals on that
+ * stream.  Such a graph repeats the captured kernels on the same buffers:
+ * replayed on the grid's stream, with no other call stepping the grid in
+ * between, each replay advances the state by nsteps steps if nsteps is even
+ * (the state is back in the buffer it started from; an odd count is not
+ * replayable).  The grid's step count advances at capture only; after a
+ * replay mrt_conserved_totals returns that replay's totals.  The totals
+ * readers return MRT_EINVAL inside a capture. */
 mrt_status mrt_step(mrt_grid *g, long nsteps);
 
 /* Macroscopic fields of the current state: rho = fhat_1, u = j/rho,
@@ -153,11 +162,13 @@ mrt_status mrt_conserved_totals(mrt_grid *g, double out[4]);
  * totals; dst[4] is the flag word as a double (0: healthy; bit 0: a step
  * met non-positive or non-finite rho or pressure; bit 1: a device-side
  * wait ran out).  dst is valid once mrt_totals_wait(g, *ticket) returns
- * MRT_OK (or after any synchronisation of the grid's stream), and must stay
- * allocated until then.  Steps enqueued after the call do not disturb the
- * copy, so a caller can launch step n+1 before it waits for the totals of
- * step n and keep the GPU busy.  Errors: MRT_EINVAL (NULL
- * argument), MRT_ECUDA. */
+ * MRT_OK, or once a later mrt_conserved_totals or mrt_destroy returns (a
+ * synchronisation of the grid's stream alone does not cover the side
+ * stream's copy), and must stay allocated until then.  Steps enqueued
+ * after the call do not disturb the copy, so a caller can launch step n+1
+ * before it waits for the totals of step n and keep the GPU busy.
+ * Errors: MRT_EINVAL (NULL argument, or the grid's stream is being
+ * captured), MRT_ECUDA. */
 mrt_status mrt_conserved_totals_async(mrt_grid *g, double *dst, long *ticket);
 /* Wait until the copy of a ticket has landed.  The grid keeps the last 8
  * tickets' completion markers; waiting on an older ticket waits for a
@@ -323,7 +334,7 @@ void mrt_batch_destroy(mrt_batch *b);
 mrt_status mrt_debug_padding(mrt_grid *g, long *nonzero);
 mrt_status mrt_debug_wait_timeout(mrt_grid *g);
 
-/* Release every device resource of the grid (synchronises its stream). */
+/* Release every device resource of the grid (synchronises its streams). */
 void mrt_destroy(mrt_grid *g);
 
 const char *mrt_status_str(mrt_status s);

@@ -362,7 +362,7 @@ __global__ void __launch_bounds__(FINAL_THREADS) totals_final_kernel(const doubl
 // Both passes on the grid's side stream: partials buffer b into totals
 // buffer b (block_sums is used by one reduction at a time, in the side
 // stream's order).
-static cudaError_t reduce_totals_on(mrt_grid* g, int b, int nparts) {
+static cudaError_t reduce_totals_on(mrt_grid* g, int b, int nparts, cudaStream_t st) {
     int chunk = FINAL_PER_BLOCK;
     int blocks = (nparts + chunk - 1) / chunk;
     if (blocks > FINAL_MAX_BLOCKS) {
@@ -370,19 +370,29 @@ static cudaError_t reduce_totals_on(mrt_grid* g, int b, int nparts) {
         chunk = (nparts + blocks - 1) / blocks;
     }
     if (blocks < 1) blocks = 1;
-    totals_pass_kernel<<<blocks, FINAL_THREADS, 0, g->tstream>>>(g->partials + (size_t)b * 4 * g->max_parts, nparts,
-                                                                 chunk, g->block_sums);
-    totals_final_kernel<<<1, FINAL_THREADS, 0, g->tstream>>>(g->block_sums, blocks, g->p.dx * g->p.dx, g->flag,
-                                                             g->totals_dev + 5 * b);
+    totals_pass_kernel<<<blocks, FINAL_THREADS, 0, st>>>(g->partials + (size_t)b * 4 * g->max_parts, nparts, chunk,
+                                                         g->block_sums);
+    totals_final_kernel<<<1, FINAL_THREADS, 0, st>>>(g->block_sums, blocks, g->p.dx * g->p.dx, g->flag,
+                                                     g->totals_dev + 5 * b);
     return cudaGetLastError();
 }
 
+// The side stream waits for everything enqueued on the grid's stream so far
+// (a read of the totals comes after the steps that produced them, also when
+// those ran inside a graph the caller captured and launched there).
+static cudaError_t tail_to_side(mrt_grid* g) {
+    cudaError_t e = cudaEventRecord(g->ev_tail, g->stream);
+    if (e != cudaSuccess) return e;
+    return cudaStreamWaitEvent(g->tstream, g->ev_tail, 0);
+}
+
 // Partials buffer for the next totals reduction: the grid's stream first
-// waits until the side stream has finished reading it.
-static cudaError_t begin_totals(mrt_grid* g, double** partials) {
+// waits until the side stream has finished reading it (inside a capture as
+// an external wait, as the event was recorded outside it).
+static cudaError_t begin_totals(mrt_grid* g, double** partials, bool capturing) {
     const int b = g->tnext;
     if (g->red_pending[b]) {
-        cudaError_t e = cudaStreamWaitEvent(g->stream, g->ev_red[b], 0);
+        cudaError_t e = cudaStreamWaitEvent(g->stream, g->ev_red[b], capturing ? cudaEventWaitExternal : 0);
         if (e != cudaSuccess) return e;
     }
     *partials = g->partials + (size_t)b * 4 * g->max_parts;
@@ -390,13 +400,25 @@ static cudaError_t begin_totals(mrt_grid* g, double** partials) {
 }
 
 // After the partials of the next reduction were enqueued on the grid's
-// stream: the side stream waits for them and reduces them.
-static cudaError_t end_totals(mrt_grid* g, int nparts) {
+// stream: the side stream waits for them and reduces them.  While the
+// grid's stream is being captured into a caller's graph the reduction stays
+// on that stream (a fork to the side stream would leave the capture
+// unjoined).
+static cudaError_t end_totals(mrt_grid* g, int nparts, bool capturing) {
     const int b = g->tnext;
     cudaError_t e;
+    if (capturing) {
+        // no event: later work on buffer b is ordered behind it on the
+        // grid's stream, where the caller launches the graph
+        if ((e = reduce_totals_on(g, b, nparts, g->stream)) != cudaSuccess) return e;
+        g->red_pending[b] = false;
+        g->tlast = b;
+        g->tnext = b ^ 1;
+        return cudaSuccess;
+    }
     if ((e = cudaEventRecord(g->ev_step[b], g->stream)) != cudaSuccess) return e;
     if ((e = cudaStreamWaitEvent(g->tstream, g->ev_step[b], 0)) != cudaSuccess) return e;
-    if ((e = reduce_totals_on(g, b, nparts)) != cudaSuccess) return e;
+    if ((e = reduce_totals_on(g, b, nparts, g->tstream)) != cudaSuccess) return e;
     if ((e = cudaEventRecord(g->ev_red[b], g->tstream)) != cudaSuccess) return e;
     g->red_pending[b] = true;
     g->tlast = b;
@@ -498,6 +520,7 @@ static void release(mrt_grid* g) {
     cudaFreeHost(g->host_stage);
     for (int k = 0; k < mrt_grid::kTotalsEvents; ++k)
         if (g->tev[k]) cudaEventDestroy(g->tev[k]);
+    if (g->ev_tail) cudaEventDestroy(g->ev_tail);
     for (int b = 0; b < 2; ++b) {
         if (g->ev_step[b]) cudaEventDestroy(g->ev_step[b]);
         if (g->ev_red[b]) cudaEventDestroy(g->ev_red[b]);
@@ -611,6 +634,8 @@ extern "C" mrt_status mrt_create(const mrt_params* params, const double* rho, co
     for (int k = 0; k < mrt_grid::kTotalsEvents; ++k)
         if ((e = cudaEventCreateWithFlags(&g->tev[k], cudaEventDisableTiming)) != cudaSuccess)
             return bail(fail(MRT_ECUDA, "cudaEventCreate: %s", cudaGetErrorString(e)));
+    if ((e = cudaEventCreateWithFlags(&g->ev_tail, cudaEventDisableTiming)) != cudaSuccess)
+        return bail(fail(MRT_ECUDA, "cudaEventCreate: %s", cudaGetErrorString(e)));
     for (int b = 0; b < 2; ++b)
         if ((e = cudaEventCreateWithFlags(&g->ev_step[b], cudaEventDisableTiming)) != cudaSuccess ||
             (e = cudaEventCreateWithFlags(&g->ev_red[b], cudaEventDisableTiming)) != cudaSuccess)
@@ -780,11 +805,11 @@ mrt_status mrt_reinit(mrt_grid* g, const double* rho, const double* ux, const do
 // One step of the grid on stream st (the last one of a call also reduces
 // totals), advancing cur, the queue parity and the step count.
 template <class T>
-static mrt_status enqueue_step(mrt_grid* g, StepArgs<T>& a, bool totals, cudaStream_t st) {
+static mrt_status enqueue_step(mrt_grid* g, StepArgs<T>& a, bool totals, cudaStream_t st, bool capturing = false) {
     a.in = static_cast<const T*>(g->f[g->cur]);
     a.out = static_cast<T*>(g->f[g->cur ^ 1]);
     queue_args(g, a);
-    if (totals) CUDA_TRY(begin_totals(g, &a.partials));
+    if (totals) CUDA_TRY(begin_totals(g, &a.partials, capturing));
     cudaError_t e;
     if (g->kernel == MRT_KERNEL_TMA) {
         e = launch_step_tma<T>(g->tile, g->xt, &g->maps[g->cur], &g->maps_out[g->cur ^ 1], a, g->tma_grid_x,
@@ -793,7 +818,7 @@ static mrt_status enqueue_step(mrt_grid* g, StepArgs<T>& a, bool totals, cudaStr
         e = launch_step_direct<T>(a, g->xt, totals, st);
     }
     if (e != cudaSuccess) return fail(MRT_ECUDA, "step launch: %s", cudaGetErrorString(e));
-    if (totals) CUDA_TRY(end_totals(g, g->parts));
+    if (totals) CUDA_TRY(end_totals(g, g->parts, capturing));
     g->cur ^= 1;
     g->steps++;
     return MRT_OK;
@@ -845,8 +870,13 @@ static mrt_status pair_graph(mrt_grid* g, cudaGraphExec_t* out) {
 template <class T>
 static mrt_status step_impl(mrt_grid* g, long nsteps) {
     StepArgs<T> a = step_args<T>(g);
+    // while a caller captures the grid's stream, every step is launched
+    // directly and the totals are reduced on that stream
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    CUDA_TRY(cudaStreamIsCapturing(g->stream, &cs));
+    const bool capturing = cs != cudaStreamCaptureStatusNone;
     long plain = nsteps - 1;
-    if (plain >= 2) {
+    if (plain >= 2 && !capturing) {
         cudaGraphExec_t& ex = g->pair_exec[g->cur][g->qpar & 1];
         if (!ex) {
             mrt_status st = pair_graph<T>(g, &ex);
@@ -862,7 +892,7 @@ static mrt_status step_impl(mrt_grid* g, long nsteps) {
         if (st != MRT_OK) return st;
     }
     if (nsteps > 0) {
-        mrt_status st = enqueue_step<T>(g, a, true, g->stream);
+        mrt_status st = enqueue_step<T>(g, a, true, g->stream, capturing);
         if (st != MRT_OK) return st;
         g->totals_fresh = true;
     }
@@ -908,21 +938,32 @@ static mrt_status totals_impl(mrt_grid* g) {
     const long n = (long)g->L.nx * g->L.ny;
     const int blocks = grid_for(n, RED_THREADS, 1024);
     double* parts = nullptr;
-    CUDA_TRY(begin_totals(g, &parts));
+    CUDA_TRY(begin_totals(g, &parts, false));
     totals_partial_kernel<T><<<blocks, RED_THREADS, 0, g->stream>>>(g->L, static_cast<const T*>(g->f[g->cur]),
                                                                      parts);
     CUDA_TRY(cudaGetLastError());
-    CUDA_TRY(end_totals(g, blocks));
+    CUDA_TRY(end_totals(g, blocks, false));
     g->totals_fresh = true;
+    return MRT_OK;
+}
+
+// The totals readers copy on the side stream, which a capture of the grid's
+// stream cannot take in: they refuse to run inside one.
+static mrt_status refuse_in_capture(mrt_grid* g) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    CUDA_TRY(cudaStreamIsCapturing(g->stream, &cs));
+    if (cs != cudaStreamCaptureStatusNone) return fail(MRT_EINVAL, "the grid's stream is being captured");
     return MRT_OK;
 }
 
 extern "C" mrt_status mrt_conserved_totals(mrt_grid* g, double out[4]) {
     if (!g || !out) return fail(MRT_EINVAL, "null argument");
+    if (mrt_status st = refuse_in_capture(g); st != MRT_OK) return st;
     if (!g->totals_fresh) {
         mrt_status st = g->fp64 ? totals_impl<double>(g) : totals_impl<float>(g);
         if (st != MRT_OK) return st;
     }
+    CUDA_TRY(tail_to_side(g));
     CUDA_TRY(cudaMemcpyAsync(g->host_stage, g->totals_dev + 5 * g->tlast, 5 * sizeof(double),
                              cudaMemcpyDeviceToHost, g->tstream));
     CUDA_TRY(cudaStreamSynchronize(g->tstream));
@@ -936,12 +977,14 @@ extern "C" mrt_status mrt_conserved_totals(mrt_grid* g, double out[4]) {
 
 extern "C" mrt_status mrt_conserved_totals_async(mrt_grid* g, double* dst, long* ticket) {
     if (!g || !dst || !ticket) return fail(MRT_EINVAL, "null argument");
+    if (mrt_status st = refuse_in_capture(g); st != MRT_OK) return st;
     if (!g->totals_fresh) {
         mrt_status st = g->fp64 ? totals_impl<double>(g) : totals_impl<float>(g);
         if (st != MRT_OK) return st;
     }
     // on the side stream, after the reduction of the latest totals; the
     // grid's stream runs on meanwhile
+    CUDA_TRY(tail_to_side(g));
     CUDA_TRY(cudaMemcpyAsync(dst, g->totals_dev + 5 * g->tlast, 5 * sizeof(double), cudaMemcpyDeviceToHost,
                              g->tstream));
     const long t = g->tickets;

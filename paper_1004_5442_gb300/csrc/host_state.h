@@ -56,6 +56,7 @@ struct mrt_grid {
     // A later totals step writing the same partials buffer waits for ev_red.
     cudaStream_t tstream = nullptr;
     cudaEvent_t ev_step[2] = {}, ev_red[2] = {};
+    cudaEvent_t ev_tail = nullptr;   // the grid's stream tail, for readers on the side stream
     bool red_pending[2] = {false, false};
     int tnext = 0;                   // buffer of the next totals reduction
     // Graphs of two plain steps, by (cur, queue parity) at their start

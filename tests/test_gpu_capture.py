@@ -1,0 +1,60 @@
+"""mrt_step inside a caller's CUDA graph capture of the grid's stream.
+
+Inside a capture the library launches every step directly and reduces the
+totals on the grid's stream (its own two-step graphs and the side-stream
+reduction stay out of the caller's graph).  Replays of an even step count on
+the grid's stream advance the state bit for bit as direct calls do, and the
+totals read after a replay are that replay's.  A side-stream reduction
+pending when the capture starts enters the graph as an external event wait.
+"""
+import numpy as np
+import pytest
+
+from paper_1004_5442_gb300 import binding as Bd
+from paper_1004_5442_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    Bd.load()
+    yield
+
+
+@pytest.mark.parametrize("kernel,tile", [(Bd.KERNEL_TMA, 6), (Bd.KERNEL_TMA, 4), (Bd.KERNEL_DIRECT, 0)])
+@pytest.mark.parametrize("prec", [Bd.FP32, Bd.FP64])
+def test_captured_steps_replay_like_direct_calls(kernel, tile, prec):
+    import torch
+    w = W.random_smooth(700, 150, seed=13, amp=0.1, bc_x=Bd.BC_FIXED_EQ)
+    s = torch.cuda.Stream()
+    with Bd.Grid.from_workload(w, precision=prec, kernel=kernel, tile=tile, stream=s.cuda_stream) as a, \
+            Bd.Grid.from_workload(w, precision=prec, kernel=kernel, tile=tile) as b:
+        # two calls: both partials buffers have a side-stream reduction
+        # recorded before the capture starts
+        for g in (a, b):
+            g.step(3)
+            g.step(1)
+        cg = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(cg, stream=s):
+            a.step(4)
+            with pytest.raises(Bd.MrtError):
+                a.totals()
+        assert a.info()["steps"] == 8
+        with torch.cuda.stream(s):
+            for _ in range(3):
+                cg.replay()
+                b.step(4)
+                np.testing.assert_array_equal(a.get_f(), b.get_f())
+                np.testing.assert_array_equal(a.totals(), b.totals())
+            # direct calls on the same grid after the replays go on from the
+            # replayed state
+            a.step(5)
+            b.step(5)
+            np.testing.assert_array_equal(a.get_f(), b.get_f())
+            np.testing.assert_array_equal(a.totals(), b.totals())
+        assert a.health() == Bd.MRT_OK and b.health() == Bd.MRT_OK
+        assert a.info()["steps"] == 13 and b.info()["steps"] == 21
