@@ -268,9 +268,8 @@ mrt_status mrt_adjoint_step(mrt_grid *g, const void *f, const void *lam_next, vo
  * every GPU that loads the library until the process exits.  It limits
  * nx * ny to 67,108,864 cells (8192 x 8192); larger sizes return MRT_EINVAL.
  * The first call on a device looks the array's device address up with
- * cudaGetSymbolAddress while that device is current; make that first call
- * before any stream capture.  No cudaMalloc, cudaFree or other allocating
- * call is made.  Every call uses the same array: calls whose kernels can run
+ * cudaGetSymbolAddress while that device is current.  No cudaMalloc,
+ * cudaFree or other allocating call is made.  Every call uses the same array: calls whose kernels can run
  * at the same time on the GPU (unordered streams) race and return wrong
  * totals, so order them.  Each call writes every scratch slot it reads, so
  * what an earlier call left behind does not matter.
