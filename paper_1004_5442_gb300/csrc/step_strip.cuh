@@ -252,6 +252,18 @@ __device__ __forceinline__ bool strip_chunk(StripRing<T>& R, const CUtensorMap* 
     if (__syncthreads_or(!ok)) return false;
     if (YWIN && tid == 0 && NS < nload) issue(NS);  // row 0 now lives in registers
 
+    // TOTALS: the conserved moments are linear in f, so each thread sums its
+    // column's 16 outputs over runs of at most kFoldRows rows in plain
+    // arithmetic and folds the moments of those sums into acc (error-free
+    // for FP32) at the end of each run: 16 additions per cell instead of
+    // the moments and four error-free additions.
+    constexpr int kFoldRows = 8;
+    T fs[TOTALS ? NV : 1];
+    if (TOTALS) {
+#pragma unroll
+        for (int i = 0; i < NV; ++i) fs[i] = (T)0;
+    }
+
 #pragma unroll 1
     for (int r = 1; r <= nrows; ++r) {
         const int y = y0 + r - 1;
@@ -319,10 +331,16 @@ __device__ __forceinline__ bool strip_chunk(StripRing<T>& R, const CUtensorMap* 
                 if (XT) store_corners<T>(out, L, per_x, per_y, x, y, [&](int j) { return o[j]; });
             }
             if (TOTALS) {
-                T q0, q1, q2, q3;
-                conserved_moments<T>(o, q0, q1, q2, q3);
-                acc[0].add(q0); acc[1].add(q1); acc[2].add(q2); acc[3].add(q3);
+#pragma unroll
+                for (int i = 0; i < NV; ++i) fs[i] += o[i];
             }
+        }
+        if (TOTALS && (r % kFoldRows == 0 || r == nrows)) {
+            T q0, q1, q2, q3;
+            conserved_moments<T>(fs, q0, q1, q2, q3);
+            acc[0].add(q0); acc[1].add(q1); acc[2].add(q2); acc[3].add(q3);
+#pragma unroll
+            for (int i = 0; i < NV; ++i) fs[i] = (T)0;
         }
         if (tstore) {
             fence_async_shared();                // make this thread's row visible to the TMA engine

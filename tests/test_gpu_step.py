@@ -389,3 +389,23 @@ def test_direct_kernel_totals_with_multi_row_blocks(prec, tol):
         with run_gpu(w, prec, Bd.KERNEL_DIRECT, nsteps=3) as grid:
             got = grid.totals()
         assert np.all(np.abs(got - want) <= tol * scale), (nx, ny, got, want)
+
+
+@pytest.mark.parametrize("tile", [1, 2, 3, 4, 5, 6, 7])
+@pytest.mark.parametrize("prec,tol", [(Bd.FP64, 1e-13), (Bd.FP32, 1e-6)])
+def test_tma_totals_fold_row_runs(tile, prec, tol):
+    """The strip kernels sum each column's 16 outputs over runs of at most 8
+    rows and fold the conserved moments of those sums into the totals; on
+    row bands and items whose heights are not multiples of 8 (150 rows,
+    ragged last strip) the fused totals match the oracle's totals of the
+    same state."""
+    w = W.random_smooth(700, 150, seed=8, amp=0.1, bc_x=Bd.BC_FIXED_EQ)
+    g = run_oracle(w, 3)
+    want = oracle.totals(g)
+    _, _, _, M, _ = oracle.model()
+    scale = np.array([np.sum(np.abs(np.tensordot(M[k], g.f, 1))) * w.dx ** 2 for k in range(4)])
+    with Bd.Grid.from_workload(w, precision=prec, kernel=Bd.KERNEL_TMA, tile=tile) as grid:
+        grid.step(3)
+        got = grid.totals()
+        assert grid.info()["tile"] == tile
+    assert np.all(np.abs(got - want) <= tol * scale), (tile, got, want)
