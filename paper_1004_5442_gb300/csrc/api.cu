@@ -313,9 +313,12 @@ __global__ void __launch_bounds__(RED_THREADS) totals_partial_kernel(Layout L, c
 // out[4] takes the flag word, so one copy brings back totals and health.
 // Two passes spread the FP64 additions over many SMs (one SM of this part
 // retires only two FP64 lanes per clock): block b of the first pass sums
-// partials [b*chunk, (b+1)*chunk) - thread t those at t, t+256, ... - and a
-// fixed tree; the second pass sums the block results the same way.
-constexpr int FINAL_THREADS = 256;
+// partials [b*chunk, (b+1)*chunk) - thread t those at t, t+FINAL_THREADS,
+// ... - and a fixed tree; the second pass sums the block results the same
+// way.  Blocks of 128 threads (32 registers each, 4 KB of shared memory)
+// fit beside a step kernel's resident CTAs, so the side-stream reduction of
+// one step runs while the next step does.
+constexpr int FINAL_THREADS = 128;
 constexpr int FINAL_PER_BLOCK = 4 * FINAL_THREADS;  // partials per first-pass block
 constexpr int FINAL_MAX_BLOCKS = 1024;
 
@@ -331,8 +334,8 @@ __device__ __forceinline__ void tree_sum4(double acc[4], double (*red)[4], doubl
         for (int k = 0; k < 4; ++k) dst[k] = red[0][k] * scale;
 }
 
-__global__ void __launch_bounds__(FINAL_THREADS) totals_pass_kernel(const double* partials, int nparts, int chunk,
-                                                                    double* block_sums) {
+__global__ void __launch_bounds__(FINAL_THREADS, 16) totals_pass_kernel(const double* partials, int nparts,
+                                                                        int chunk, double* block_sums) {
     __shared__ double red[FINAL_THREADS][4];
     double acc[4] = {0, 0, 0, 0};
     const int p0 = blockIdx.x * chunk, p1 = min(nparts, p0 + chunk);
@@ -348,9 +351,9 @@ __global__ void __launch_bounds__(FINAL_THREADS) totals_pass_kernel(const double
     tree_sum4(acc, red, block_sums + 4 * blockIdx.x, 1.0);
 }
 
-__global__ void __launch_bounds__(FINAL_THREADS) totals_final_kernel(const double* block_sums, int nblocks,
-                                                                     double scale, const unsigned* flag,
-                                                                     double* out) {
+__global__ void __launch_bounds__(FINAL_THREADS, 16) totals_final_kernel(const double* block_sums, int nblocks,
+                                                                         double scale, const unsigned* flag,
+                                                                         double* out) {
     __shared__ double red[FINAL_THREADS][4];
     double acc[4] = {0, 0, 0, 0};
     for (int p = threadIdx.x; p < nblocks; p += FINAL_THREADS)
