@@ -173,6 +173,97 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+class NvmlClocks:
+    """SM clock, power and clock-event reasons read through NVML (read-only
+    queries, nothing is set) every `period` seconds in a thread, plus one
+    read on demand (`sample()`), so that a timed region of a few milliseconds
+    still has samples.  Falls back to ClockSampler if NVML cannot be loaded."""
+    REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown",
+               0x40: "hw_thermal_slowdown", 0x80: "hw_power_brake_slowdown"}
+
+    def __init__(self, local, period=0.001):
+        import ctypes
+        import threading
+        self.period = period
+        self.samples = []
+        self.fallback = None
+        self._stop = threading.Event()
+        self._thread = None
+        self.nv = None
+        self.h = None
+        try:
+            nv = ctypes.CDLL("libnvidia-ml.so.1")
+            if nv.nvmlInit_v2() != 0:
+                raise OSError("nvmlInit")
+            h = ctypes.c_void_p()
+            bus = self._pci_bus_id(local)
+            rc = nv.nvmlDeviceGetHandleByPciBusId_v2(bus.encode(), ctypes.byref(h)) if bus else 1
+            if rc != 0:
+                rc = nv.nvmlDeviceGetHandleByIndex_v2(ctypes.c_uint(local), ctypes.byref(h))
+            if rc != 0:
+                raise OSError("nvml handle")
+            self.nv, self.h = nv, h
+            self.reason_fn = getattr(nv, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+                nv.nvmlDeviceGetCurrentClocksThrottleReasons
+            mx = ctypes.c_uint()
+            self.max_mhz = float(mx.value) if nv.nvmlDeviceGetMaxClockInfo(h, 1, ctypes.byref(mx)) == 0 else None
+        except Exception:
+            self.fallback = ClockSampler(local)
+
+    @staticmethod
+    def _pci_bus_id(local):
+        try:
+            import torch
+            p = torch.cuda.get_device_properties(local)
+            return "%08X:%02X:%02X.0" % (p.pci_domain_id, p.pci_bus_id, p.pci_device_id)
+        except Exception:
+            return None
+
+    def sample(self):
+        import ctypes
+        if self.nv is None:
+            return
+        mhz, mw, r = ctypes.c_uint(), ctypes.c_uint(), ctypes.c_ulonglong()
+        if self.nv.nvmlDeviceGetClockInfo(self.h, 1, ctypes.byref(mhz)) != 0:
+            return
+        self.nv.nvmlDeviceGetPowerUsage(self.h, ctypes.byref(mw))
+        self.reason_fn(self.h, ctypes.byref(r))
+        self.samples.append((float(mhz.value), mw.value / 1e3, int(r.value)))
+
+    def _run(self):
+        while not self._stop.is_set():
+            self.sample()
+            self._stop.wait(self.period)
+
+    def __enter__(self):
+        if self.fallback is not None:
+            self.fallback.__enter__()
+            return self
+        import threading
+        self._thread = threading.Thread(target=self._run, daemon=True)
+        self._thread.start()
+        return self
+
+    def __exit__(self, *exc):
+        if self.fallback is not None:
+            return self.fallback.__exit__(*exc)
+        self._stop.set()
+        self._thread.join()
+
+    def summary(self):
+        if self.fallback is not None:
+            out = self.fallback.summary()
+            out["source"] = "nvidia-smi -lms 100"
+            return out
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": self.max_mhz, "reasons": [], "samples": 0, "source": "nvml"}
+        reasons = sorted({nm for _, _, r in self.samples for bit, nm in self.REASONS.items() if r & bit})
+        return {"sm_mhz": statistics.median(m for m, _, _ in self.samples), "sm_max_mhz": self.max_mhz,
+                "sm_mhz_min": min(m for m, _, _ in self.samples),
+                "power_w_max": max(p for _, p, _ in self.samples), "reasons": reasons,
+                "samples": len(self.samples), "source": "nvml read-only queries every 1 ms"}
+
+
 def measured_peak_hbm():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -324,10 +415,11 @@ def run_ours(args):
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     barrier(world)
     torch.cuda.synchronize()
-    with ClockSampler(local) as clk:
+    with NvmlClocks(local) as clk:
         ev0.record(stream)
         grid.step(args.steps)
         ev1.record(stream)
+        clk.sample()          # the steps are queued: the GPU is busy now
         torch.cuda.synchronize()
     barrier(world)
     ms = ev0.elapsed_time(ev1)

@@ -131,23 +131,33 @@ mrt_status mrt_create(const mrt_params *params, const double *rho, const double 
  * While the grid's stream is being captured into a caller's CUDA graph, the
  * call instead launches every step directly and reduces the totals on that
  * stream.  Such a graph repeats the captured kernels on the same buffers:
- * replayed on the grid's stream, with no other call stepping the grid in
- * between, each replay advances the state by nsteps steps if nsteps is even
- * (the state is back in the buffer it started from; an odd count is not
- * replayable).  The grid's step count advances at capture only; after a
- * replay mrt_conserved_totals returns that replay's totals.  The totals
- * readers return MRT_EINVAL inside a capture. */
+ * replayed on the grid's stream, each replay advances the state by nsteps
+ * steps if nsteps is even (the state is back in the buffer it started from;
+ * an odd count is not replayable).  Replays may alternate with direct calls
+ * of even step counts, which leave the buffers and work counters where a
+ * replay expects them.  A captured graph reduces its totals into a slot of
+ * its own (scratch it shares with no side-stream reduction), and from the
+ * first capture on each totals-producing step stamps its place in the
+ * grid's stream order, so the totals readers return those of the latest
+ * step, replayed or direct.  The grid's step count advances at capture
+ * only.  The totals readers return MRT_EINVAL inside a capture. */
 mrt_status mrt_step(mrt_grid *g, long nsteps);
 
-/* Macroscopic fields of the current state: rho = fhat_1, u = j/rho,
- * T = (e - j^2/rho)/(b rho) (R = 1).  Outputs are [ny][nx] doubles, on the
+/* Macroscopic fields of the current state: rho = fhat_1, j = (fhat_2,
+ * fhat_3), u = j/rho, and T from the closure stated with Eq. 12 (P = rho R T,
+ * e = fhat_4 = b rho R T + j^2/rho, R = 1 as in Sect. "Numerical Simulation
+ * and Analysis"): T = (e - j^2/rho)/(b rho).  Outputs are [ny][nx] doubles, on the
  * device if dst_on_device (asynchronous on the grid's stream), else on the
  * host (synchronises).  Any output pointer may be NULL to skip it. */
 mrt_status mrt_get_macro(mrt_grid *g, double *rho, double *ux, double *uy, double *T,
                          int dst_on_device);
 
 /* Conserved totals sum_cells (rho, j_x, j_y, e) * dx * dy of the current
- * state, accumulated in FP64 with a fixed summation order (deterministic).
+ * state: the moments fhat_1..4 that the collision leaves unchanged
+ * (fhat_k = fhat^eq_k for k <= 4, Sect. "Construction of energy-conserving
+ * MRT LB model" and the Appendix rows m_1..m_4), so on a periodic grid they
+ * are invariants of the step.  Accumulated in FP64 with a fixed summation
+ * order (deterministic).
  * out[4] is host memory; synchronises the grid's stream.  Returns
  * MRT_EUNSTABLE if the health flag has tripped (out is still written). */
 mrt_status mrt_conserved_totals(mrt_grid *g, double out[4]);
@@ -332,6 +342,19 @@ void mrt_batch_destroy(mrt_batch *b);
  * Errors: MRT_EINVAL (null pointers), MRT_ENOMEM, MRT_ECUDA. */
 mrt_status mrt_debug_padding(mrt_grid *g, long *nonzero);
 mrt_status mrt_debug_wait_timeout(mrt_grid *g);
+
+/* mrt_debug_fma_rate: fused multiply-add throughput of the current device in
+ * FP32 or FP64 (precision = mrt_precision), the arithmetic roof of the
+ * steps that are bound by the FP64 pipe.  One launch of blocks_per_sm (1..8)
+ * blocks of 256 threads per SM, each thread running 8 independent chains
+ * a <- a * 1/2 + 1/2 for 16 * iters multiply-adds each, is timed with CUDA
+ * events after one untimed launch of the same shape; *flops_per_s =
+ * 2 * multiply-adds / time, *ms (may be NULL) the timed launch's duration.
+ * Allocates a small output buffer (stream-ordered) and synchronises.
+ * Errors: MRT_EINVAL (precision, iters < 1, blocks_per_sm out of range,
+ * NULL flops_per_s), MRT_ECUDA. */
+mrt_status mrt_debug_fma_rate(int precision, long iters, int blocks_per_sm, double *flops_per_s,
+                              double *ms);
 
 /* Release every device resource of the grid (synchronises its streams). */
 void mrt_destroy(mrt_grid *g);

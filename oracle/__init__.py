@@ -34,6 +34,9 @@ ADV_LW = 0
 ADV_LW2D = 1
 ADV_MINMOD = 2
 ADV_VANLEER = 3
+# another reading of the time scheme: the Lax-Wendroff (second-order Taylor)
+# step of the whole kinetic equation, collision term included (forward only)
+ADV_LWFULL = 4
 NV = 16
 
 
@@ -232,6 +235,8 @@ def feq_moments_via_cplx(rho, jx, jy, e, b) -> np.ndarray:
 def step_adjoint(g: Grid, f: np.ndarray, lam_next: np.ndarray, gxb: np.ndarray, gyb: np.ndarray,
                  gs: np.ndarray) -> np.ndarray:
     """dL/df^n from f^n and dL/df^{n+1}; accumulates ghost and rate adjoints."""
+    if g.advection == ADV_LWFULL:
+        raise ValueError("ADV_LWFULL has no reverse mode")
     f = np.ascontiguousarray(f, dtype=np.float64)
     lam_next = np.ascontiguousarray(lam_next, dtype=np.float64)
     out = np.zeros_like(f)

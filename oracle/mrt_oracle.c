@@ -75,8 +75,18 @@ typedef struct {
  *                   limiters only as earlier work on stabilising LB
  *                   schemes): per velocity and axis the Lax-Wendroff flux is
  *                   the first-order upwind flux plus a correction scaled by
- *                   a limiter phi (Sweby's form); phi = 1 gives ORC_ADV_LW. */
-enum { ORC_ADV_LW = 0, ORC_ADV_LW2D = 1, ORC_ADV_MINMOD = 2, ORC_ADV_VANLEER = 3 };
+ *                   a limiter phi (Sweby's form); phi = 1 gives ORC_ADV_LW;
+ *   ORC_ADV_LWFULL  another reading of the time scheme: the Lax-Wendroff
+ *                   (second-order Taylor) step of the whole kinetic
+ *                   equation, Eq. 3 including its collision term:
+ *                     f^{n+1} = f + dt f_t + (dt^2/2) f_tt,
+ *                     f_t  = -v.grad f + Omega(f),
+ *                     f_tt = (v.grad)^2 f - v.grad Omega + J (-v.grad f + Omega),
+ *                   J = dOmega/df at the cell; v.grad by central differences,
+ *                   (v.grad)^2 as in ORC_ADV_LW2D (second differences and the
+ *                   four-corner mixed term), so with S = 0 it is ORC_ADV_LW2D.
+ *                   Forward step only (no reverse mode). */
+enum { ORC_ADV_LW = 0, ORC_ADV_LW2D = 1, ORC_ADV_MINMOD = 2, ORC_ADV_VANLEER = 3, ORC_ADV_LWFULL = 4 };
 
 /* ------------------------------------------------------------------------ */
 /* Model: velocity set, eta_i, M and its inverse.                            */
@@ -437,10 +447,17 @@ static double adv_limited(const orc_cfg *c, const double *f, const double *gx, c
  *           c = v_ia dt/dx, f_+- the neighbours at +-1 along a
  *   f_i^{n+1} = f_i + Adv_i + dt Omega_i
  * gx/gy are the fixed-equilibrium ghosts (ignored on periodic axes). */
+static void step_lwfull(const orc_cfg *c, const double *f, const double *gx, const double *gy,
+                        double *fnew);
+
 void orc_step(const orc_cfg *c, const double *f, const double *gx, const double *gy,
               double *fnew)
 {
     ensure_model();
+    if (c->advection == ORC_ADV_LWFULL) {
+        step_lwfull(c, f, gx, gy, fnew);
+        return;
+    }
     const int nx = c->nx, ny = c->ny;
     const size_t n = (size_t)nx * (size_t)ny;
     const double lam = c->dt / c->dx;
@@ -617,6 +634,93 @@ void orc_feq_jacobian(double rho, double jx, double jy, double e, double b, doub
         double complex out[NV];
         feq_moments_cplx(m[0], m[1], m[2], m[3], b, out);
         for (int k = 0; k < NV; ++k) J[k * 4 + j] = cimag(out[k]) / h;
+    }
+}
+
+/* Collision term of Eq. 3 for one cell's 16 values:
+ * Omega = -Minv S (M f - fhat^eq(M f)). */
+static void collision(const orc_cfg *c, const double fl[NV], double om[NV])
+{
+    double fh[NV], fe[NV], delta[NV];
+    for (int k = 0; k < NV; ++k) {
+        double acc = 0.0;
+        for (int i = 0; i < NV; ++i) acc += g_M[k * NV + i] * fl[i];
+        fh[k] = acc;
+    }
+    orc_feq_moments(fh[0], fh[1], fh[2], fh[3], c->b, fe);
+    for (int k = 0; k < NV; ++k) delta[k] = c->s[k] * (fh[k] - fe[k]);
+    for (int i = 0; i < NV; ++i) {
+        double acc = 0.0;
+        for (int k = 0; k < NV; ++k) acc += g_Minv[i * NV + k] * delta[k];
+        om[i] = -acc;
+    }
+}
+
+/* J w = (dOmega/df) w at f, by a complex step: Omega is analytic in f, and
+ * Im Omega(f + i h w) / h = J w with no subtractive cancellation. */
+static void collision_dir(const orc_cfg *c, const double fl[NV], const double w[NV], double Jw[NV])
+{
+    const double h = 1e-30;
+    double complex fh[NV], fe[NV], delta[NV];
+    for (int k = 0; k < NV; ++k) {
+        double complex acc = 0.0;
+        for (int i = 0; i < NV; ++i) acc += g_M[k * NV + i] * (fl[i] + I * h * w[i]);
+        fh[k] = acc;
+    }
+    feq_moments_cplx(fh[0], fh[1], fh[2], fh[3], c->b, fe);
+    for (int k = 0; k < NV; ++k) delta[k] = c->s[k] * (fh[k] - fe[k]);
+    for (int i = 0; i < NV; ++i) {
+        double complex acc = 0.0;
+        for (int k = 0; k < NV; ++k) acc += g_Minv[i * NV + k] * delta[k];
+        Jw[i] = -cimag(acc) / h;
+    }
+}
+
+/* One ORC_ADV_LWFULL step (see the enum): per cell and velocity i, with
+ * c_a = v_ia dt/dx, the neighbours' Omega computed from their own f (the
+ * ghosts' f on fixed and wall sides, as every read goes through fat), and
+ * w = dt (-v.grad f + Omega) at the cell:
+ *   f_i^{n+1} = f_i + [the ORC_ADV_LW2D advection of f_i] + dt Omega_i
+ *             - (dt/4) [c_x (Omega_i(x+1) - Omega_i(x-1)) + c_y (Omega_i(y+1) - Omega_i(y-1))]
+ *             + (dt/2) (J w)_i. */
+static void step_lwfull(const orc_cfg *c, const double *f, const double *gx, const double *gy,
+                        double *fnew)
+{
+    const int nx = c->nx, ny = c->ny;
+    const size_t n = (size_t)nx * (size_t)ny;
+    const double lam = c->dt / c->dx;
+    static const int off[4][2] = {{1, 0}, {-1, 0}, {0, 1}, {0, -1}};
+#pragma omp parallel for schedule(static)
+    for (int y = 0; y < ny; ++y) {
+        for (int x = 0; x < nx; ++x) {
+            double fl[NV], om[NV], fn[4][NV], omn[4][NV], w[NV], Jw[NV];
+            for (int i = 0; i < NV; ++i) fl[i] = f[(size_t)i * n + (size_t)y * nx + x];
+            collision(c, fl, om);
+            for (int q = 0; q < 4; ++q) {
+                for (int i = 0; i < NV; ++i) fn[q][i] = fat(c, f, gx, gy, i, x + off[q][0], y + off[q][1]);
+                collision(c, fn[q], omn[q]);
+            }
+            for (int i = 0; i < NV; ++i) {
+                const double cx = g_vx[i] * lam, cy = g_vy[i] * lam;
+                w[i] = -0.5 * cx * (fn[0][i] - fn[1][i]) - 0.5 * cy * (fn[2][i] - fn[3][i]) + c->dt * om[i];
+            }
+            collision_dir(c, fl, w, Jw);
+            for (int i = 0; i < NV; ++i) {
+                const double f0 = fl[i];
+                const double cx = g_vx[i] * lam, cy = g_vy[i] * lam;
+                const double fxp = fn[0][i], fxm = fn[1][i], fyp = fn[2][i], fym = fn[3][i];
+                const double adv_x = -0.5 * cx * (fxp - fxm) + 0.5 * cx * cx * (fxp - 2.0 * f0 + fxm);
+                const double adv_y = -0.5 * cy * (fyp - fym) + 0.5 * cy * cy * (fyp - 2.0 * f0 + fym);
+                double adv_xy = 0.0;
+                if (cx != 0.0 && cy != 0.0)
+                    adv_xy = 0.25 * cx * cy * (fat(c, f, gx, gy, i, x + 1, y + 1) - fat(c, f, gx, gy, i, x + 1, y - 1)
+                                               - fat(c, f, gx, gy, i, x - 1, y + 1) + fat(c, f, gx, gy, i, x - 1, y - 1));
+                const double src = c->dt * om[i]
+                                 - 0.25 * c->dt * (cx * (omn[0][i] - omn[1][i]) + cy * (omn[2][i] - omn[3][i]))
+                                 + 0.5 * c->dt * Jw[i];
+                fnew[(size_t)i * n + (size_t)y * nx + x] = f0 + adv_x + adv_y + adv_xy + src;
+            }
+        }
     }
 }
 

@@ -6,6 +6,11 @@ reverse sweep (mrt_adjoint_backward: checkpointed recomputation + transposed
 step) and returns gradients for the four initial fields and the 16 rates.
 Only marshalling happens here: every step of the forward and the reverse
 sweep runs in the CUDA library.
+
+The recorded run (its checkpoints on the device) belongs to the autograd
+graph of the output and is freed with it, so ``backward(retain_graph=True)``
+followed by a second backward gives the same gradients again; without
+``retain_graph`` a second backward raises PyTorch's usual error.
 """
 from __future__ import annotations
 
@@ -38,10 +43,14 @@ class MRTRun(torch.autograd.Function):
         (s,) = ctx.saved_tensors
         g = g_rhoN.detach().to(dtype=torch.float64).contiguous()
         outs = [torch.empty_like(g) for _ in range(4)]
-        torch.cuda.current_stream().synchronize()
+        # the reverse sweep runs on the grid's stream: it waits for the work
+        # that produced g (and allocated outs) on the caller's stream; the
+        # call returns once that stream holds the results
+        cur = torch.cuda.current_stream()
+        if grid.stream != cur.cuda_stream:
+            own = torch.cuda.ExternalStream(grid.stream) if grid.stream else torch.cuda.default_stream()
+            own.wait_stream(cur)
         *_, gs = grid.adjoint_backward(g, outs)
-        grid.close()
-        ctx.grid = None
         g_s = torch.as_tensor(gs, dtype=s.dtype, device=s.device)
         return outs[0], outs[1], outs[2], outs[3], g_s, None, None, None
 

@@ -29,7 +29,7 @@ EXPORTED = ["mrt_create", "mrt_step", "mrt_get_macro", "mrt_conserved_totals", "
             "mrt_adjoint_backward", "mrt_adjoint_step", "mrt_batch_create", "mrt_batch_step",
             "mrt_batch_tune", "mrt_batch_grid", "mrt_batch_info", "mrt_batch_sync", "mrt_batch_stream",
             "mrt_batch_destroy", "mrt_debug_padding", "mrt_debug_wait_timeout", "mrt_conserved_totals_async",
-            "mrt_totals_wait", "mrt_save", "mrt_load"]
+            "mrt_totals_wait", "mrt_save", "mrt_load", "mrt_debug_fma_rate"]
 
 
 class MrtError(RuntimeError):
@@ -96,6 +96,7 @@ def load(path: str = LIB_PATH):
     L.mrt_totals_wait.argtypes = [vp, ctypes.c_long]
     L.mrt_save.argtypes = [vp, ctypes.c_char_p]
     L.mrt_load.argtypes = [vp, ctypes.c_char_p]
+    L.mrt_debug_fma_rate.argtypes = [ip, ctypes.c_long, ip, dp, dp]
     L.mrt_batch_destroy.argtypes = [vp]
     L.mrt_batch_destroy.restype = None
     for name in ("mrt_create", "mrt_step", "mrt_get_macro", "mrt_conserved_totals", "mrt_get_f",
@@ -103,7 +104,7 @@ def load(path: str = LIB_PATH):
                  "mrt_adjoint_record", "mrt_adjoint_backward", "mrt_adjoint_step", "mrt_batch_create",
                  "mrt_batch_step", "mrt_batch_tune", "mrt_batch_grid", "mrt_batch_info", "mrt_batch_sync",
                  "mrt_batch_stream", "mrt_debug_padding", "mrt_debug_wait_timeout", "mrt_conserved_totals_async",
-                 "mrt_totals_wait", "mrt_save", "mrt_load"):
+                 "mrt_totals_wait", "mrt_save", "mrt_load", "mrt_debug_fma_rate"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -151,6 +152,17 @@ def conserved_totals_static(f, precision: int, nx: int, ny: int, dx: float, out,
         stream = _torch_stream()
     check(load().mrt_conserved_totals_static(ctypes.c_void_p(_ptr(f)), int(precision), int(nx), int(ny),
                                              float(dx), ctypes.c_void_p(_ptr(out)), ctypes.c_void_p(stream)))
+
+
+def fma_rate(precision: int, iters: int | None = None, blocks_per_sm: int = 4):
+    """(flop/s, ms) of the device's fused multiply-add throughput in FP32 or
+    FP64 (mrt_debug_fma_rate); iters defaults to about 0.1 s of work."""
+    if iters is None:
+        iters = 3000 if precision == FP64 else 200000
+    rate, ms = ctypes.c_double(), ctypes.c_double()
+    check(load().mrt_debug_fma_rate(int(precision), int(iters), int(blocks_per_sm), ctypes.byref(rate),
+                                    ctypes.byref(ms)))
+    return rate.value, ms.value
 
 
 class Grid:

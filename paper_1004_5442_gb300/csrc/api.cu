@@ -353,18 +353,39 @@ __global__ void __launch_bounds__(FINAL_THREADS, 16) totals_pass_kernel(const do
 
 __global__ void __launch_bounds__(FINAL_THREADS, 16) totals_final_kernel(const double* block_sums, int nblocks,
                                                                          double scale, const unsigned* flag,
+                                                                         const unsigned long long* stamp,
                                                                          double* out) {
     __shared__ double red[FINAL_THREADS][4];
     double acc[4] = {0, 0, 0, 0};
     for (int p = threadIdx.x; p < nblocks; p += FINAL_THREADS)
         for (int k = 0; k < 4; ++k) acc[k] += block_sums[4 * p + k];
     tree_sum4(acc, red, out, scale);
-    if (threadIdx.x == 0) out[4] = (double)*flag;
+    if (threadIdx.x == 0) {
+        out[4] = (double)*flag;
+        out[5] = (double)*stamp;
+    }
 }
 
-// Both passes on the grid's side stream: partials buffer b into totals
-// buffer b (block_sums is used by one reduction at a time, in the side
-// stream's order).
+// Sequence stamp of the partials a step is about to write: the grid's
+// counter, advanced on the grid's stream, so stamps follow step order.
+__global__ void totals_stamp_kernel(unsigned long long* seq, int slot) {
+    seq[1 + slot] = ++seq[0];
+}
+
+// Copy the totals slot with the newer stamp (the side stream's latest or
+// the captured graph's) into the pick slot a reader copies out.
+__global__ void totals_pick_kernel(double* totals, int side_slot, int cap_slot, int pick_slot) {
+    const double* a = totals + mrt_grid::kTotalsSlot * side_slot;
+    const double* c = totals + mrt_grid::kTotalsSlot * cap_slot;
+    const double* src = c[5] > a[5] ? c : a;
+    double* dst = totals + mrt_grid::kTotalsSlot * pick_slot;
+    for (int k = 0; k < mrt_grid::kTotalsSlot; ++k) dst[k] = src[k];
+}
+
+// Both passes of one reduction: the partials of slot b (0, 1: the side
+// stream's double buffer; kCapSlot: a captured graph's) into totals slot b.
+// The side-stream slots share block_sums, used by one reduction at a time
+// in the side stream's order; the captured slot has its own.
 static cudaError_t reduce_totals_on(mrt_grid* g, int b, int nparts, cudaStream_t st) {
     int chunk = FINAL_PER_BLOCK;
     int blocks = (nparts + chunk - 1) / chunk;
@@ -373,10 +394,12 @@ static cudaError_t reduce_totals_on(mrt_grid* g, int b, int nparts, cudaStream_t
         chunk = (nparts + blocks - 1) / blocks;
     }
     if (blocks < 1) blocks = 1;
-    totals_pass_kernel<<<blocks, FINAL_THREADS, 0, st>>>(g->partials + (size_t)b * 4 * g->max_parts, nparts, chunk,
-                                                         g->block_sums);
-    totals_final_kernel<<<1, FINAL_THREADS, 0, st>>>(g->block_sums, blocks, g->p.dx * g->p.dx, g->flag,
-                                                     g->totals_dev + 5 * b);
+    const bool cap = b == mrt_grid::kCapSlot;
+    const double* parts = cap ? g->cap_partials : g->partials + (size_t)b * 4 * g->max_parts;
+    double* sums = cap ? g->cap_block_sums : g->block_sums;
+    totals_pass_kernel<<<blocks, FINAL_THREADS, 0, st>>>(parts, nparts, chunk, sums);
+    totals_final_kernel<<<1, FINAL_THREADS, 0, st>>>(sums, blocks, g->p.dx * g->p.dx, g->flag, g->seq + 1 + b,
+                                                     g->totals_dev + mrt_grid::kTotalsSlot * b);
     return cudaGetLastError();
 }
 
@@ -389,16 +412,29 @@ static cudaError_t tail_to_side(mrt_grid* g) {
     return cudaStreamWaitEvent(g->tstream, g->ev_tail, 0);
 }
 
-// Partials buffer for the next totals reduction: the grid's stream first
-// waits until the side stream has finished reading it (inside a capture as
-// an external wait, as the event was recorded outside it).
+// Partials buffer for the next totals reduction.  Outside a capture: the
+// side stream's next buffer, after the grid's stream has waited until the
+// side stream finished reading it.  Inside a capture: the captured slot's
+// own buffer, which only the grid's stream touches.  Once the grid has been
+// captured, a stamp of the step order precedes the partials.
 static cudaError_t begin_totals(mrt_grid* g, double** partials, bool capturing) {
-    const int b = g->tnext;
-    if (g->red_pending[b]) {
-        cudaError_t e = cudaStreamWaitEvent(g->stream, g->ev_red[b], capturing ? cudaEventWaitExternal : 0);
-        if (e != cudaSuccess) return e;
+    int slot;
+    if (capturing) {
+        g->cap_used = true;
+        slot = mrt_grid::kCapSlot;
+        *partials = g->cap_partials;
+    } else {
+        slot = g->tnext;
+        if (g->red_pending[slot]) {
+            cudaError_t e = cudaStreamWaitEvent(g->stream, g->ev_red[slot], 0);
+            if (e != cudaSuccess) return e;
+        }
+        *partials = g->partials + (size_t)slot * 4 * g->max_parts;
     }
-    *partials = g->partials + (size_t)b * 4 * g->max_parts;
+    if (g->cap_used) {
+        totals_stamp_kernel<<<1, 1, 0, g->stream>>>(g->seq, slot);
+        return cudaGetLastError();
+    }
     return cudaSuccess;
 }
 
@@ -411,13 +447,9 @@ static cudaError_t end_totals(mrt_grid* g, int nparts, bool capturing) {
     const int b = g->tnext;
     cudaError_t e;
     if (capturing) {
-        // no event: later work on buffer b is ordered behind it on the
-        // grid's stream, where the caller launches the graph
-        if ((e = reduce_totals_on(g, b, nparts, g->stream)) != cudaSuccess) return e;
-        g->red_pending[b] = false;
-        g->tlast = b;
-        g->tnext = b ^ 1;
-        return cudaSuccess;
+        // no event: every later use of the captured slot is ordered behind
+        // it on the grid's stream, where the caller launches the graph
+        return reduce_totals_on(g, mrt_grid::kCapSlot, nparts, g->stream);
     }
     if ((e = cudaEventRecord(g->ev_step[b], g->stream)) != cudaSuccess) return e;
     if ((e = cudaStreamWaitEvent(g->tstream, g->ev_step[b], 0)) != cudaSuccess) return e;
@@ -519,6 +551,9 @@ static void release(mrt_grid* g) {
     cudaFree(g->partials);
     cudaFree(g->totals_dev);
     cudaFree(g->block_sums);
+    cudaFree(g->cap_block_sums);
+    cudaFree(g->cap_partials);
+    cudaFree(g->seq);
     cudaFree(g->qnext);
     cudaFreeHost(g->host_stage);
     for (int k = 0; k < mrt_grid::kTotalsEvents; ++k)
@@ -630,8 +665,13 @@ extern "C" mrt_status mrt_create(const mrt_params* params, const double* rho, co
         return bail(fail(MRT_ECUDA, "memset: %s", cudaGetErrorString(e)));
     if ((e = cudaMalloc(&g->flag, sizeof(unsigned))) != cudaSuccess ||
         (e = cudaMemsetAsync(g->flag, 0, sizeof(unsigned), g->stream)) != cudaSuccess ||
-        (e = cudaMalloc(&g->totals_dev, 2 * 5 * sizeof(double))) != cudaSuccess ||
+        (e = cudaMalloc(&g->totals_dev, 4 * mrt_grid::kTotalsSlot * sizeof(double))) != cudaSuccess ||
+        (e = cudaMemsetAsync(g->totals_dev, 0, 4 * mrt_grid::kTotalsSlot * sizeof(double), g->stream)) !=
+            cudaSuccess ||
+        (e = cudaMalloc(&g->seq, 4 * sizeof(unsigned long long))) != cudaSuccess ||
+        (e = cudaMemsetAsync(g->seq, 0, 4 * sizeof(unsigned long long), g->stream)) != cudaSuccess ||
         (e = cudaMalloc(&g->block_sums, 4 * sizeof(double) * FINAL_MAX_BLOCKS)) != cudaSuccess ||
+        (e = cudaMalloc(&g->cap_block_sums, 4 * sizeof(double) * FINAL_MAX_BLOCKS)) != cudaSuccess ||
         (e = cudaMallocHost(&g->host_stage, 8 * sizeof(double))) != cudaSuccess)
         return bail(fail(MRT_ENOMEM, "cudaMalloc: %s", cudaGetErrorString(e)));
     for (int k = 0; k < mrt_grid::kTotalsEvents; ++k)
@@ -706,7 +746,8 @@ extern "C" mrt_status mrt_create(const mrt_params* params, const double* rho, co
     g->parts = parts;
     const int red_parts = grid_for((long)params->nx * params->ny, RED_THREADS, 1024);
     g->max_parts = parts > red_parts ? parts : red_parts;
-    if ((e = cudaMalloc(&g->partials, 2 * 4 * sizeof(double) * (size_t)g->max_parts)) != cudaSuccess)
+    if ((e = cudaMalloc(&g->partials, 2 * 4 * sizeof(double) * (size_t)g->max_parts)) != cudaSuccess ||
+        (e = cudaMalloc(&g->cap_partials, 4 * sizeof(double) * (size_t)g->max_parts)) != cudaSuccess)
         return bail(fail(MRT_ENOMEM, "cudaMalloc partials: %s", cudaGetErrorString(e)));
 
     if (kernel == MRT_KERNEL_TMA) {
@@ -950,6 +991,22 @@ static mrt_status totals_impl(mrt_grid* g) {
     return MRT_OK;
 }
 
+// Totals slot a reader copies, on the side stream after everything enqueued
+// on the grid's stream: the side stream's latest, or, once the grid has been
+// captured, whichever of that and the captured slot has the newer stamp
+// (a replay and direct steps may alternate in any order).
+static mrt_status reader_slot(mrt_grid* g, int* slot) {
+    CUDA_TRY(tail_to_side(g));
+    *slot = g->tlast;
+    if (g->cap_used) {
+        totals_pick_kernel<<<1, 1, 0, g->tstream>>>(g->totals_dev, g->tlast, mrt_grid::kCapSlot,
+                                                    mrt_grid::kPickSlot);
+        CUDA_TRY(cudaGetLastError());
+        *slot = mrt_grid::kPickSlot;
+    }
+    return MRT_OK;
+}
+
 // The totals readers copy on the side stream, which a capture of the grid's
 // stream cannot take in: they refuse to run inside one.
 static mrt_status refuse_in_capture(mrt_grid* g) {
@@ -966,8 +1023,9 @@ extern "C" mrt_status mrt_conserved_totals(mrt_grid* g, double out[4]) {
         mrt_status st = g->fp64 ? totals_impl<double>(g) : totals_impl<float>(g);
         if (st != MRT_OK) return st;
     }
-    CUDA_TRY(tail_to_side(g));
-    CUDA_TRY(cudaMemcpyAsync(g->host_stage, g->totals_dev + 5 * g->tlast, 5 * sizeof(double),
+    int slot = 0;
+    if (mrt_status st = reader_slot(g, &slot); st != MRT_OK) return st;
+    CUDA_TRY(cudaMemcpyAsync(g->host_stage, g->totals_dev + mrt_grid::kTotalsSlot * slot, 5 * sizeof(double),
                              cudaMemcpyDeviceToHost, g->tstream));
     CUDA_TRY(cudaStreamSynchronize(g->tstream));
     CUDA_TRY(cudaStreamSynchronize(g->stream));
@@ -987,11 +1045,15 @@ extern "C" mrt_status mrt_conserved_totals_async(mrt_grid* g, double* dst, long*
     }
     // on the side stream, after the reduction of the latest totals; the
     // grid's stream runs on meanwhile
-    CUDA_TRY(tail_to_side(g));
-    CUDA_TRY(cudaMemcpyAsync(dst, g->totals_dev + 5 * g->tlast, 5 * sizeof(double), cudaMemcpyDeviceToHost,
-                             g->tstream));
+    int slot = 0;
+    if (mrt_status st = reader_slot(g, &slot); st != MRT_OK) return st;
+    CUDA_TRY(cudaMemcpyAsync(dst, g->totals_dev + mrt_grid::kTotalsSlot * slot, 5 * sizeof(double),
+                             cudaMemcpyDeviceToHost, g->tstream));
     const long t = g->tickets;
     CUDA_TRY(cudaEventRecord(g->tev[t % mrt_grid::kTotalsEvents], g->tstream));
+    // a replay of a captured graph writes its totals slot on the grid's
+    // stream: later work there waits until this copy has read it
+    if (g->cap_used) CUDA_TRY(cudaStreamWaitEvent(g->stream, g->tev[t % mrt_grid::kTotalsEvents], 0));
     g->tickets = t + 1;
     *ticket = t;
     return MRT_OK;

@@ -11,6 +11,9 @@
 //    its 2 s limit) and sets the timeout flag, which mrt_health reports as
 //    MRT_ETIMEOUT.  It exercises the failure path of every TMA kernel without
 //    a fault, a trap or an unbounded wait.
+//  * mrt_debug_fma_rate: the device's fused multiply-add throughput in FP32
+//    or FP64, the arithmetic roof against which the FP64 step (bound by the
+//    FP64 pipe on this part) is measured.
 #include "host_state.h"
 #include "tma.cuh"
 
@@ -46,7 +49,76 @@ __global__ void wait_timeout_kernel(unsigned* flag) {
     }
 }
 
+// Independent multiply-add chains a <- a * b + c per thread (b = c = 1/2:
+// every chain converges to 1 and stays a normal number, so no denormal or
+// overflow path is timed).  kChains chains give each warp enough
+// independent instructions to cover the pipe latency; the sum is stored only
+// if it equals a value it cannot reach, which keeps every chain live.
+constexpr int kFmaThreads = 256;
+constexpr int kFmaChains = 8;
+constexpr int kFmaUnroll = 16;
+template <class T>
+__global__ void __launch_bounds__(kFmaThreads) fma_kernel(long iters, T b, T c, T* out) {
+    T a[kFmaChains];
+#pragma unroll
+    for (int k = 0; k < kFmaChains; ++k) a[k] = (T)(threadIdx.x + 1) * (T)(k + 1) * (T)1e-3;
+    for (long it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int u = 0; u < kFmaUnroll; ++u) {
+#pragma unroll
+            for (int k = 0; k < kFmaChains; ++k) a[k] = fma(a[k], b, c);
+        }
+    }
+    T s = 0;
+#pragma unroll
+    for (int k = 0; k < kFmaChains; ++k) s += a[k];
+    if (s == (T)-1) out[blockIdx.x * kFmaThreads + threadIdx.x] = s;
+}
+
 }  // namespace
+
+extern "C" mrt_status mrt_debug_fma_rate(int precision, long iters, int blocks_per_sm, double* flops_per_s,
+                                         double* ms) {
+    if (!flops_per_s || iters < 1 || blocks_per_sm < 1 || blocks_per_sm > 8 ||
+        (precision != MRT_FP32 && precision != MRT_FP64))
+        return mrt_fail(MRT_EINVAL, "need precision MRT_FP32 or MRT_FP64, iters >= 1, 1 <= blocks_per_sm <= 8, "
+                                    "flops_per_s");
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int blocks = sms * blocks_per_sm;
+    cudaStream_t st = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    void* out = nullptr;
+    cudaError_t e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    if (e == cudaSuccess) e = cudaMallocAsync(&out, (size_t)blocks * kFmaThreads * 8, st);
+    float el = 0.f;
+    if (e == cudaSuccess) {
+        for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {  // the first launch warms up
+            e = cudaEventRecord(e0, st);
+            if (precision == MRT_FP64)
+                fma_kernel<double><<<blocks, kFmaThreads, 0, st>>>(iters, 0.5, 0.5, static_cast<double*>(out));
+            else
+                fma_kernel<float><<<blocks, kFmaThreads, 0, st>>>(iters, 0.5f, 0.5f, static_cast<float*>(out));
+            if (e == cudaSuccess) e = cudaGetLastError();
+            if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+        }
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&el, e0, e1);
+        cudaFreeAsync(out, st);
+        cudaStreamSynchronize(st);
+    }
+    if (e1) cudaEventDestroy(e1);
+    if (e0) cudaEventDestroy(e0);
+    if (st) cudaStreamDestroy(st);
+    if (e != cudaSuccess) return mrt_fail(MRT_ECUDA, "fma rate: %s", cudaGetErrorString(e));
+    const double flops = 2.0 * kFmaChains * kFmaUnroll * (double)iters * kFmaThreads * blocks;
+    *flops_per_s = flops / (el * 1e-3);
+    if (ms) *ms = el;
+    return MRT_OK;
+}
 
 extern "C" mrt_status mrt_debug_padding(mrt_grid* g, long* nonzero) {
     if (!g || !nonzero) return mrt_fail(MRT_EINVAL, "null argument");

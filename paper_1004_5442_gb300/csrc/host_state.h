@@ -48,7 +48,13 @@ struct mrt_grid {
     unsigned* flag = nullptr;        // device flag word
     double* partials = nullptr;      // 2 buffers of max_parts x 4 doubles (block / warp partials)
     int max_parts = 0;
-    double* totals_dev = nullptr;    // 2 buffers of 4 totals + a copy of the flag word, as doubles
+    // Totals slots of kTotalsSlot doubles: 4 totals, a copy of the flag word
+    // and the sequence stamp of the step they belong to.  Slots 0 and 1: the
+    // side-stream reductions; slot 2: reductions inside a caller's captured
+    // graph; slot 3: the newer of slot tlast and slot 2, picked for a reader.
+    static constexpr int kTotalsSlot = 6;
+    static constexpr int kCapSlot = 2, kPickSlot = 3;
+    double* totals_dev = nullptr;
     // The totals reduction and its read-back run on a side stream: a step
     // that reduces totals writes its partials into buffer tnext and goes on;
     // the side stream waits for it (ev_step), sums the partials into
@@ -64,6 +70,16 @@ struct mrt_grid {
     cudaGraphExec_t pair_exec[2][2] = {};
     int tlast = 0;                   // buffer holding the latest totals
     double* block_sums = nullptr;    // first-pass sums of the totals reduction
+    // A reduction captured into a caller's graph has partials, first-pass
+    // sums and totals slot of its own, so a replay never shares scratch with
+    // a side-stream reduction still in flight.  Once a grid has been
+    // captured, every totals-producing step first writes a sequence stamp
+    // (seq[0] counts, seq[1 + slot] holds the stamp of that slot's partials)
+    // on the grid's stream, and the readers take the slot with the newer one.
+    double* cap_partials = nullptr;
+    double* cap_block_sums = nullptr;
+    unsigned long long* seq = nullptr;  // device: counter + 3 stamps
+    bool cap_used = false;
     double* host_stage = nullptr;    // pinned host copy of totals_dev (one small DMA per read)
     static constexpr int kTotalsEvents = 8;
     cudaEvent_t tev[kTotalsEvents] = {};  // completion markers of asynchronous totals copies

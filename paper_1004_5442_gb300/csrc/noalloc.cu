@@ -87,7 +87,8 @@ __global__ void __launch_bounds__(kThreads) partial_kernel(const T* __restrict__
         }
 }
 
-// Fixed-order sum of the first nparts partials, times dx*dy, into out[4].
+// Fixed-order sum of the first nparts partials, times scale = dx*dx (square
+// cells: the entry point takes one cell size), into out[4].
 __global__ void __launch_bounds__(kThreads) final_kernel(const double* __restrict__ scratch, int nparts,
                                                          double scale, double* __restrict__ out) {
     __shared__ double red[kThreads][4];

@@ -41,3 +41,46 @@ def assert_parity(got, want, linf=None, l1=None, label=""):
         if l1 is not None:
             assert e1 <= l1, f"{label} {name}: L1 {e1:.3e} > {l1:.1e} ({errs})"
     return errs
+
+
+def oracle_macro_job(w, nsteps, threads):
+    """(rho, ux, uy, T) of an oracle run of workload w after nsteps steps,
+    with `threads` OpenMP threads; the job of one worker process."""
+    oracle.set_threads(int(threads))
+    return oracle.macro(run_oracle(w, nsteps))
+
+
+def oracle_totals_job(w, nsteps, threads):
+    """(macro fields, totals) of an oracle run of w after nsteps steps."""
+    oracle.set_threads(int(threads))
+    g = run_oracle(w, nsteps)
+    return oracle.macro(g), oracle.totals(g)
+
+
+def _cone(a, y0, x0, size, r):
+    n0, n1 = a.shape
+    ys = np.arange(y0 - r, y0 + size + r) % n0
+    xs = np.arange(x0 - r, x0 + size + r) % n1
+    return np.ascontiguousarray(a[np.ix_(ys, xs)])
+
+
+def oracle_window_job(w, y0, x0, size, r):
+    """(rho, ux, uy, T) on the size x size window at (y0, x0) of a periodic
+    workload after r oracle steps, from a run on the window's dependency
+    cone (the window widened by r cells on every side, wrapped, periodic on
+    the cone itself): with a radius-1 stencil the cone's wrong edges spoil
+    only the r - 1 cells next to them by step r."""
+    oracle.set_threads(1)
+    fields = [_cone(a, y0, x0, size, r) for a in (w.rho, w.ux, w.uy, w.T)]
+    m = size + 2 * r
+    g = oracle.create(m, m, w.dx, w.dt, w.b, w.s, *fields)
+    oracle.run(g, r)
+    return tuple(np.ascontiguousarray(q[r:r + size, r:r + size]) for q in oracle.macro(g))
+
+
+def spawn_pool(workers):
+    """Process pool for oracle jobs.  Workers are started with spawn, never
+    forked from a process that has touched the GPU."""
+    import multiprocessing as mp
+    from concurrent.futures import ProcessPoolExecutor
+    return ProcessPoolExecutor(max_workers=int(workers), mp_context=mp.get_context("spawn"))

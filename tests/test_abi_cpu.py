@@ -99,6 +99,11 @@ def test_null_handles_of_later_entry_points_rejected(lib):
     assert lib.mrt_load(None, b"/nonexistent/x") == Bd.MRT_EINVAL
     assert lib.mrt_debug_padding(None, ctypes.byref(n)) == Bd.MRT_EINVAL
     assert lib.mrt_debug_wait_timeout(None) == Bd.MRT_EINVAL
+    r = ctypes.c_double()
+    assert lib.mrt_debug_fma_rate(Bd.FP64, 100, 4, None, None) == Bd.MRT_EINVAL
+    assert lib.mrt_debug_fma_rate(7, 100, 4, ctypes.byref(r), None) == Bd.MRT_EINVAL
+    assert lib.mrt_debug_fma_rate(Bd.FP32, 0, 4, ctypes.byref(r), None) == Bd.MRT_EINVAL
+    assert lib.mrt_debug_fma_rate(Bd.FP32, 10, 9, ctypes.byref(r), None) == Bd.MRT_EINVAL
 
 
 def test_status_strings(lib):

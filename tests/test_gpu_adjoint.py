@@ -171,3 +171,32 @@ def test_autograd_function_matches_adjoint():
     for t, r in zip((rho0, ux0, uy0, T0), ref[:4]):
         np.testing.assert_allclose(t.grad.cpu().numpy(), r, rtol=1e-12, atol=1e-14 * np.max(np.abs(r)))
     np.testing.assert_allclose(s.grad.cpu().numpy(), ref[4], rtol=1e-12, atol=0)
+
+
+def test_autograd_second_backward():
+    """retain_graph=True keeps the recorded run: a second backward gives the
+    same gradients bit for bit (accumulated twice in .grad); without it a
+    second backward raises PyTorch's error.  Run on a side stream, so the
+    reverse sweep must wait for the caller's stream by event."""
+    import torch
+
+    from paper_1004_5442_gb300.autograd import mrt_run
+    w = W.smooth_vortex(n=48, nsteps=20, r0=0.15)
+    side = torch.cuda.Stream()
+    with torch.cuda.stream(side):
+        target = torch.tensor(W.vortex_target(w), device="cuda")
+        dev = lambda a: torch.tensor(np.ascontiguousarray(a), device="cuda", requires_grad=True)
+        rho0, ux0, uy0, T0 = dev(w.rho), dev(w.ux), dev(w.uy), dev(w.T)
+        s = torch.tensor(w.s, device="cuda", requires_grad=True)
+        params = dict(nx=w.nx, ny=w.ny, dx=w.dx, dt=w.dt, gamma=w.gamma, precision=Bd.FP64)
+        rhoN = mrt_run(rho0, ux0, uy0, T0, s, params, w.nsteps, 5)
+        L = 0.5 * torch.sum((rhoN - target) ** 2) * w.dx ** 2
+        L.backward(retain_graph=True)
+        first = [t.grad.clone() for t in (rho0, ux0, uy0, T0, s)]
+        L.backward(retain_graph=True)
+        for t, g1 in zip((rho0, ux0, uy0, T0, s), first):
+            assert torch.equal(t.grad, 2 * g1)
+        L.backward()
+        with pytest.raises(RuntimeError):
+            L.backward()
+    side.synchronize()

@@ -1,11 +1,12 @@
 """mrt_step inside a caller's CUDA graph capture of the grid's stream.
 
 Inside a capture the library launches every step directly and reduces the
-totals on the grid's stream (its own two-step graphs and the side-stream
-reduction stay out of the caller's graph).  Replays of an even step count on
-the grid's stream advance the state bit for bit as direct calls do, and the
-totals read after a replay are that replay's.  A side-stream reduction
-pending when the capture starts enters the graph as an external event wait.
+totals on the grid's stream into a totals slot of the graph's own (its own
+two-step graphs and the side-stream reduction stay out of the caller's
+graph).  Replays of an even step count on the grid's stream advance the state
+bit for bit as direct calls do; replays and direct calls of even step counts
+may alternate, and the totals read afterwards are those of the latest step,
+whichever of the two produced it (a stamp of the stream order decides).
 """
 import numpy as np
 import pytest
@@ -58,3 +59,43 @@ def test_captured_steps_replay_like_direct_calls(kernel, tile, prec):
             np.testing.assert_array_equal(a.totals(), b.totals())
         assert a.health() == Bd.MRT_OK and b.health() == Bd.MRT_OK
         assert a.info()["steps"] == 13 and b.info()["steps"] == 21
+
+
+@pytest.mark.parametrize("prec", [Bd.FP32, Bd.FP64])
+def test_direct_steps_between_capture_and_replay(prec):
+    """Capture, then a direct even step, then replays and direct steps in
+    turn: the state and both totals readers follow the latest step (the
+    replay's totals are not hidden by the earlier direct step's, nor the
+    other way round)."""
+    import torch
+    w = W.random_smooth(300, 70, seed=17, amp=0.1)
+    s = torch.cuda.Stream()
+    stage = torch.empty(5, dtype=torch.float64).pin_memory()
+    with Bd.Grid.from_workload(w, precision=prec, kernel=Bd.KERNEL_TMA, tile=6, stream=s.cuda_stream) as a, \
+            Bd.Grid.from_workload(w, precision=prec, kernel=Bd.KERNEL_TMA, tile=6) as b:
+        a.step(2)
+        b.step(2)
+        cg = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(cg, stream=s):
+            a.step(2)
+        with torch.cuda.stream(s):
+            a.step(2)                 # direct, after the capture
+            b.step(2)
+            np.testing.assert_array_equal(a.totals(), b.totals())
+            for direct_after in (False, True, True, False):
+                cg.replay()
+                b.step(2)
+                if direct_after:
+                    a.step(4)
+                    b.step(4)
+                np.testing.assert_array_equal(a.get_f(), b.get_f())
+                want = b.totals()
+                np.testing.assert_array_equal(a.totals(), want)
+                t = a.totals_async(stage)
+                cg.replay()           # enqueued while the copy may still be pending
+                b.step(2)
+                a.totals_wait(t)
+                np.testing.assert_array_equal(stage.numpy()[:4], want)
+                assert stage.numpy()[4] == 0.0
+                np.testing.assert_array_equal(a.totals(), b.totals())
+        assert a.health() == Bd.MRT_OK

@@ -67,3 +67,15 @@ def test_bounded_wait_runs_out_and_is_reported():
     with Bd.Grid.from_workload(w, precision=Bd.FP32) as g:
         g.step(3)
         assert g.health() == Bd.MRT_OK
+
+
+def test_fma_rate_is_plausible():
+    """The multiply-add throughput probe: positive, FP32 well above FP64 on
+    this part, and both below the SM count times the widest issue a clock
+    allows (128 FP32 lanes per SM, 2 flops each, at 3 GHz)."""
+    import torch
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    r64, ms64 = Bd.fma_rate(Bd.FP64, iters=200)
+    r32, ms32 = Bd.fma_rate(Bd.FP32, iters=2000)
+    assert 0 < r64 < r32 <= sms * 128 * 2 * 3e9
+    assert ms64 > 0 and ms32 > 0

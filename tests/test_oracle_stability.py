@@ -27,12 +27,12 @@ def _sigma(s57, s89, others):
     return x
 
 
-def _radius(orc, state, gamma, sigma, dtdx):
+def _radius(orc, state, gamma, sigma, dtdx, advection=0):
     rho, ux, uy, T = state
     b = 2.0 / (gamma - 1.0)
     dx = 1.0 / N
     dt = dtdx * dx
-    g = orc.create(N, N, dx, dt, b, np.asarray(sigma) / dt, rho, ux, uy, T)
+    g = orc.create(N, N, dx, dt, b, np.asarray(sigma) / dt, rho, ux, uy, T, advection=advection)
     f0 = g.f.copy()
     X, Y = np.meshgrid(np.arange(N) + 0.5, np.arange(N) + 0.5)
     h = 1e-7 * np.max(np.abs(f0))
