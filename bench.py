@@ -43,13 +43,11 @@ KERNEL_SOURCES = ["paper_1004_5442_gb300/csrc/step_kernels.cu", "paper_1004_5442
 PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "step_tma_f32_kh4096.md")
 # FP64 step, per cell-update (ncu instruction counters of a plain
 # step_tma<double> launch, tile 6, profiles/step_tma_f64_kh2048.md):
-# FP64-pipe thread instructions and flops (DADD + DMUL + 2 DFMA).  The FP64
-# pipe issues 2 thread instructions per clock per SM (152 SMs; 2 x 2 flops x
-# 152 x 2.07 GHz = 1.26 TFLOP/s, the part's FP64 rate).
-FP64_PIPE_INST_PER_CELL = 286.0
-FP64_FLOPS_PER_CELL = 386.0
-FP64_LANES_PER_SM = 2
-N_SMS = 152
+# FP64-pipe thread instructions and flops (DADD 86 + DMUL 28 + 2 x DFMA 118).
+# Their roof is the device's FP64 multiply-add rate, measured in the same
+# run by mrt_debug_fma_rate (one DFMA = 2 flops = 1 pipe instruction).
+FP64_PIPE_INST_PER_CELL = 234.0
+FP64_FLOPS_PER_CELL = 350.0
 EXACT_PROFILES = os.path.join(ROOT, "tests", "golden", "riemann_exact_profiles.json")
 
 
@@ -74,6 +72,8 @@ def parse():
     ap.add_argument("--batch-count", type=int, default=256, help="instances of the sweep (first n screened draws)")
     ap.add_argument("--tile", type=int, default=0, help="TMA kernel variant (0 = library default)")
     ap.add_argument("--sweep-tiles", action="store_true", help="time every TMA variant, print one line each")
+    ap.add_argument("--fma-only", action="store_true",
+                    help="print the device's FP64 and FP32 multiply-add throughput (mrt_debug_fma_rate) and exit")
     return ap.parse_args()
 
 
@@ -467,16 +467,17 @@ def run_ours(args):
         g64.close()
         per64 = ms64 * 1e-3 / k64
         rate64 = cells / per64
-        clk = (line["clocks"].get("sm_max_mhz") or 2070.0) * 1e6
-        pipe_peak = N_SMS * FP64_LANES_PER_SM * clk                    # thread instructions / s
+        fma64, fma_ms = Bd.fma_rate(Bd.FP64)                          # flop/s, 2 per DFMA
+        pipe_peak = fma64 / 2                                          # DFMA instructions / s
         line["fp64"] = {"value": rate64, "unit": "cell-updates/s", "steps": k64,
                         "hbm_achieved_gbs": BYTES_PER_CELL_F64 * cells / per64 / 1e9,
                         "hbm_frac": BYTES_PER_CELL_F64 * cells / per64 / 1e9 / peak,
                         "roofline": {"bound": "alu", "achieved": rate64 * FP64_FLOPS_PER_CELL / 1e12,
-                                     "peak": 2 * pipe_peak / 1e12, "unit": "TFLOP/s",
-                                     "frac": rate64 * FP64_FLOPS_PER_CELL / (2 * pipe_peak),
+                                     "peak": fma64 / 1e12, "unit": "TFLOP/s",
+                                     "frac": rate64 * FP64_FLOPS_PER_CELL / fma64,
                                      "pipe_frac": rate64 * FP64_PIPE_INST_PER_CELL / pipe_peak,
-                                     "peak_source": "derived: 152 SMs x 2 FP64 lanes x 2 flops x max SM clock",
+                                     "peak_source": "measured: mrt_debug_fma_rate FP64 in this run "
+                                                    f"(independent DFMA chains, {fma_ms:.1f} ms launch)",
                                      "per_cell": {"fp64_pipe_inst": FP64_PIPE_INST_PER_CELL,
                                                   "flops": FP64_FLOPS_PER_CELL}}}
 
@@ -754,10 +755,28 @@ def sweep_tiles(args):
             g.close()
 
 
+def fma_only(args):
+    """The device's multiply-add throughput, FP64 and FP32, at 2, 4 and 8
+    blocks of 256 threads per SM, three launches each (CUDA events inside
+    mrt_debug_fma_rate)."""
+    from paper_1004_5442_gb300 import build as B
+    B.build()
+    from paper_1004_5442_gb300 import binding as Bd
+    out = {}
+    for name, prec in (("fp64", Bd.FP64), ("fp32", Bd.FP32)):
+        for bps in (2, 4, 8):
+            runs = [Bd.fma_rate(prec, blocks_per_sm=bps) for _ in range(3)]
+            out[f"{name}_blocks_per_sm_{bps}"] = {"tflops": [r / 1e12 for r, _ in runs], "ms": [m for _, m in runs]}
+    print(json.dumps(out), flush=True)
+
+
 def main():
     args = parse()
     if args.sweep_tiles:
         sweep_tiles(args)
+        return
+    if args.fma_only:
+        fma_only(args)
         return
     if args.impl == "reference":
         run_reference(args)

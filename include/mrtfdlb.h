@@ -103,8 +103,9 @@ typedef struct mrt_params {
                            1..5 = ring depth / store path / CTAs-per-SM choices
                            with one static chunk of rows per CTA; 6, 7 = the
                            variants of 5 and 4 whose CTAs take 8- or 32-row
-                           work items from an atomic counter; other values
-                           give MRT_EINVAL.  Results do not depend on it. */
+                           work items (10-row on tile 6 with MRT_ADV_LW2D)
+                           from an atomic counter; other values give
+                           MRT_EINVAL.  Results do not depend on it. */
     int advection;      /* mrt_advection; 0 (MRT_ADV_LW) for the method's
                            axis-by-axis Lax-Wendroff operator */
 } mrt_params;

@@ -128,6 +128,25 @@ int mrt_model_build(double dx, double dt, double b, const double s[16], Coef<dou
             k->kX[g][j] = -0.25 * ic.C2inv[g][j];
         }
     for (int kk = 0; kk < 12; ++kk) k->sig[kk] = s[4 + kk] * dt;
+    // FP64 kernels: sigma_k folded into the inverse-block constants, and the
+    // Lax-Wendroff centre weights (p + q = c^2 per axis)
+    const double* sg = k->sig;  // sigma_5 .. sigma_16 at 0 .. 11
+    for (int g = 0; g < 4; ++g) {
+        k->kSs[g][0] = k->kS[g][0] * sg[0];
+        k->kSs[g][1] = k->kS[g][1] * sg[9];
+        for (int j = 0; j < 3; ++j) {
+            k->kDx[g][j] = k->kD[g][j] * sg[3 + 2 * j];   // sigma_8, sigma_10, sigma_12
+            k->kDy[g][j] = k->kD[g][j] * sg[4 + 2 * j];   // sigma_9, sigma_11, sigma_13
+        }
+        const double c = kU(g) * dt / dx;
+        k->lw0[g] = g < 2 ? 1.0 - c * c : 1.0 - 2.0 * c * c;
+    }
+    for (int g = 0; g < 2; ++g) {
+        k->kQs[g][0] = k->kQ[g][0] * sg[1];    // sigma_6
+        k->kQs[g][1] = k->kQ[g][1] * sg[11];   // sigma_16
+        k->kXs[g][0] = k->kX[g][0] * sg[2];    // sigma_7
+        k->kXs[g][1] = k->kX[g][1] * sg[10];   // sigma_15
+    }
     k->inv_b = 1.0 / b;
     k->c14a = 2.0 * (b + 2.0);
     k->c14b = 6.0 + b;
@@ -704,7 +723,7 @@ extern "C" mrt_status mrt_create(const mrt_params* params, const double* rho, co
         if (g->tile == 0) {
             // the work-queue tile when the grid gives every resident CTA at
             // least two items, else one static chunk of rows per CTA
-            const int qt = g->xt ? kQueueTileXT : kQueueTile, qr = tile_cfg(qt).queue_rows;
+            const int qt = g->xt ? kQueueTileXT : kQueueTile, qr = queue_rows(qt, g->xt);
             if ((e = occupancy(qt, &occ)) != cudaSuccess)
                 return bail(fail(MRT_ECUDA, "occupancy query: %s", cudaGetErrorString(e)));
             const long items = (long)strips * ((params->ny + qr - 1) / qr);
@@ -714,7 +733,7 @@ extern "C" mrt_status mrt_create(const mrt_params* params, const double* rho, co
         if (e != cudaSuccess) return bail(fail(MRT_ECUDA, "occupancy query: %s", cudaGetErrorString(e)));
         if (occ < 1) occ = 1;
         const long resident = (long)sms * occ;
-        const int qrows = tile_cfg(g->tile).queue_rows;
+        const int qrows = queue_rows(g->tile, g->xt);
         g->strips = strips;
         if (qrows > 0) {
             // one wave of resident CTAs taking (row band, strip) items

@@ -25,7 +25,8 @@ using namespace mrt;
 namespace {
 
 constexpr int kCoefSlots = 256;                     // instances across all live batches (per device)
-__constant__ Coef<float> c_batch_coef[kCoefSlots];  // 52 floats each: 53 KB
+__constant__ Coef<float> c_batch_coef[kCoefSlots];  // 54 floats each: 55 KB
+static_assert(sizeof(Coef<float>) == 54 * sizeof(float), "the FP32 step constants fill the constant table");
 
 std::mutex g_slot_mu;
 bool g_slot_used[kCoefSlots] = {};

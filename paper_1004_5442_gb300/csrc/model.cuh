@@ -45,9 +45,30 @@ __host__ __device__ constexpr int mirror_plane(int i, int axis) {
     return 4 * g + (axis == 0 ? (k ^ 1) : (3 - k));
 }
 
+// FP64 only: the inverse-block constants with each moment's sigma_k folded
+// in (so the relaxation costs one subtraction per moment instead of two
+// operations), and the centre weights of the Lax-Wendroff update written as
+// a0 f + p f_up + q f_down (+ the diagonal groups' second axis), so that
+// one multiply-add takes each neighbour.  FP64 runs on a pipe that retires
+// two lanes per clock per SM, which bounds the FP64 step; the FP32 step is
+// bound by HBM and keeps the difference form, which leaves a uniform state
+// exactly unchanged.  Empty for FP32, so the per-instance constant table of
+// the batched kernel keeps its size.
+template <class T>
+struct CoefFold {};
+template <>
+struct CoefFold<double> {
+    double kSs[4][2];  // kS[g][j] * (sigma_5, sigma_14)
+    double kDx[4][3];  // kD[g][j] * (sigma_8, sigma_10, sigma_12)
+    double kDy[4][3];  // kD[g][j] * (sigma_9, sigma_11, sigma_13)
+    double kQs[2][2];  // kQ[g][j] * (sigma_6, sigma_16)
+    double kXs[2][2];  // kX[g][j] * (sigma_7, sigma_15)
+    double lw0[4];     // centre weight: 1 - c^2 (axis groups), 1 - 2 c^2 (diagonal groups)
+};
+
 // Everything a step kernel needs besides the state.
 template <class T>
-struct Coef {
+struct Coef : CoefFold<T> {
     // Collision increment dt*Omega in the combined basis, already scaled by
     // the inverse butterflies' 1/4 or 1/2 and by -1:
     T kS[4][2];   // S_g    <- (Delta_5, Delta_14)
@@ -212,22 +233,81 @@ __device__ __forceinline__ void cell_update(const Fetch& F, const Coef<T>& k, T 
     P_in = P;
 
     // ---- relaxation Delta_k = sigma_k (m_k - m^eq_k), k = 5..16 ---------
-    const T d5 = k.sig[0] * (m5 - q5), d6 = k.sig[1] * (m6 - q6), d7 = k.sig[2] * (m7 - q7);
-    const T d8 = k.sig[3] * (m8 - q8), d9 = k.sig[4] * (m9 - q9);
-    const T d10 = k.sig[5] * (m10 - q10), d11 = k.sig[6] * (m11 - q11);
-    const T d12 = k.sig[7] * (m12 - q12), nd13 = k.sig[8] * (n13 - nq13);   // -Delta_13
-    const T d14 = k.sig[9] * (m14 - q14), d15 = k.sig[10] * (m15 - q15);
-    const T d16 = k.sig[11] * (m16 - q16);
+    // (FP64: the residuals m_k - m^eq_k alone; sigma_k is in the constants)
+    constexpr bool kFold = sizeof(T) == 8;
+    auto relax = [&](int j, T r) -> T {
+        if constexpr (kFold) return r; else return k.sig[j] * r;
+    };
+    const T d5 = relax(0, m5 - q5), d6 = relax(1, m6 - q6), d7 = relax(2, m7 - q7);
+    const T d8 = relax(3, m8 - q8), d9 = relax(4, m9 - q9);
+    const T d10 = relax(5, m10 - q10), d11 = relax(6, m11 - q11);
+    const T d12 = relax(7, m12 - q12), nd13 = relax(8, n13 - nq13);   // -Delta_13
+    const T d14 = relax(9, m14 - q14), d15 = relax(10, m15 - q15);
+    const T d16 = relax(11, m16 - q16);
 
     // ---- inverse blocks (scaled), inverse butterflies, then advection ----
 #pragma unroll
     for (int g = 0; g < 4; ++g) {
-        const T cS = k.kS[g][0] * d5 + k.kS[g][1] * d14;
-        const T cX = k.kD[g][0] * d8 + k.kD[g][1] * d10 + k.kD[g][2] * d12;
-        const T cY = k.kD[g][0] * d9 + k.kD[g][1] * d11 + k.kD[g][2] * nd13;
+        T cS, cX, cY;
+        if constexpr (kFold) {
+            cS = k.kSs[g][0] * d5 + k.kSs[g][1] * d14;
+            cX = k.kDx[g][0] * d8 + k.kDx[g][1] * d10 + k.kDx[g][2] * d12;
+            cY = k.kDy[g][0] * d9 + k.kDy[g][1] * d11 + k.kDy[g][2] * nd13;
+        } else {
+            cS = k.kS[g][0] * d5 + k.kS[g][1] * d14;
+            cX = k.kD[g][0] * d8 + k.kD[g][1] * d10 + k.kD[g][2] * d12;
+            cY = k.kD[g][0] * d9 + k.kD[g][1] * d11 + k.kD[g][2] * nd13;
+        }
         const T p = k.lwp[g], qq = k.lwq[g];
         const int i0 = 4 * g;
-        if (g < 2) {
+        if constexpr (kFold) {
+          if (g < 2) {
+            // FP64: out = a0 f + p f_up + q f_down + collision, one
+            // multiply-add per neighbour (+x: p on x-1, q on x+1; -x mirrored;
+            // +y / -y likewise along y)
+            const T cQ = k.kQs[g][0] * d6 + k.kQs[g][1] * d16;
+            const T sp = cS + cQ, sm = cS - cQ;
+            const T a0 = k.lw0[g];
+            out[i0 + 0] = a0 * f[i0 + 0] + (p * F(i0 + 0, XM) + (qq * F(i0 + 0, XP) + (sp + cX)));
+            out[i0 + 2] = a0 * f[i0 + 2] + (p * F(i0 + 2, XP) + (qq * F(i0 + 2, XM) + (sp - cX)));
+            out[i0 + 1] = a0 * f[i0 + 1] + (p * F(i0 + 1, YM) + (qq * F(i0 + 1, YP) + (sm + cY)));
+            out[i0 + 3] = a0 * f[i0 + 3] + (p * F(i0 + 3, YP) + (qq * F(i0 + 3, YM) + (sm - cY)));
+          } else {
+            // FP64 diagonal groups: a0 = 1 - 2 c^2; the mixed term of the
+            // unsplit operator enters as four more multiply-adds
+            const T cXY = k.kXs[g - 2][0] * d7 + k.kXs[g - 2][1] * d15;
+            const T t1 = cS + cXY, t2 = cS - cXY, s1 = cX + cY, s2 = cX - cY;
+            const T a0 = k.lw0[g];
+            auto mixed = [&](int i, T w, T acc) -> T {
+                if constexpr (XT)
+                    return w * F(i, XPYP) + (-w * F(i, XPYM) + (-w * F(i, XMYP) + (w * F(i, XMYM) + acc)));
+                else
+                    return acc;
+            };
+            const T w = XT ? k.kxy[g - 2] : (T)0;
+            {   // (+,+): p on x-1, y-1; q on x+1, y+1
+                const T c0 = mixed(i0 + 0, w, t1 + s1);
+                out[i0 + 0] = a0 * f[i0 + 0] + (p * (F(i0 + 0, XM) + F(i0 + 0, YM)) +
+                                                 (qq * (F(i0 + 0, XP) + F(i0 + 0, YP)) + c0));
+            }
+            {   // (-,+): p on x+1, y-1; q on x-1, y+1
+                const T c1 = mixed(i0 + 1, -w, t2 - s2);
+                out[i0 + 1] = a0 * f[i0 + 1] + (p * (F(i0 + 1, XP) + F(i0 + 1, YM)) +
+                                                 (qq * (F(i0 + 1, XM) + F(i0 + 1, YP)) + c1));
+            }
+            {   // (-,-): p on x+1, y+1; q on x-1, y-1
+                const T c2 = mixed(i0 + 2, w, t1 - s1);
+                out[i0 + 2] = a0 * f[i0 + 2] + (p * (F(i0 + 2, XP) + F(i0 + 2, YP)) +
+                                                 (qq * (F(i0 + 2, XM) + F(i0 + 2, YM)) + c2));
+            }
+            {   // (+,-): p on x-1, y+1; q on x+1, y-1
+                const T c3 = mixed(i0 + 3, -w, t2 + s2);
+                out[i0 + 3] = a0 * f[i0 + 3] + (p * (F(i0 + 3, XM) + F(i0 + 3, YP)) +
+                                                 (qq * (F(i0 + 3, XP) + F(i0 + 3, YM)) + c3));
+            }
+          }
+        } else {
+          if (g < 2) {
             const T cQ = k.kQ[g][0] * d6 + k.kQ[g][1] * d16;
             const T sp = cS + cQ, sm = cS - cQ;
             // +x: p on x-1, q on x+1; -x mirrored; +y / -y likewise along y
@@ -294,6 +374,7 @@ __device__ __forceinline__ void cell_update(const Fetch& F, const Coef<T>& k, T 
                 const T b = (F(i0 + 3, XP) + F(i0 + 3, YM)) - (fc + fc);
                 out[i0 + 3] = fc + (p * a + (qq * b + with_mixed((t2 + s2), e3)));
             }
+          }
         }
     }
 }

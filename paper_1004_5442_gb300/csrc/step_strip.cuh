@@ -282,7 +282,7 @@ __device__ __forceinline__ bool strip_chunk(StripRing<T>& R, const CUtensorMap* 
         for (int i = 0; i < NV; ++i) fs[i] = (T)0;
     }
 
-#pragma unroll 1
+#pragma unroll 2
     for (int r = 1; r <= nrows; ++r) {
         const int y = y0 + r - 1;
         // Out slots alternate on the global row count (base + r), not on r:

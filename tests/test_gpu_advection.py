@@ -87,9 +87,10 @@ def test_many_steps_parity(kernel, tile, bcx, bcy):
 
 
 def test_queue_tile_on_a_large_grid_and_totals():
-    """2048 x 2048 gives every resident CTA at least two 8-row items, so the
-    automatic choice is the queue tile 6 in both precisions; one FP64 step
-    and its totals match the oracle."""
+    """2048 x 2048 gives every resident CTA at least two work items (10 rows
+    each for this operator, the last band ragged), so the automatic choice
+    is the queue tile 6 in both precisions; one FP64 step and its totals
+    match the oracle."""
     w = W.random_smooth(2048, 2048, seed=3, amp=0.05)
     g = _oracle(w, 1)
     with _gpu(w, Bd.FP32, Bd.KERNEL_AUTO, 0) as grid:
