@@ -64,11 +64,19 @@ typedef enum mrt_bc { MRT_BC_PERIODIC = 0, MRT_BC_FIXED_EQ = 1, MRT_BC_REFLECT_F
 
 /* Step kernel selection: MRT_KERNEL_TMA is the TMA-staged strip kernel,
  * MRT_KERNEL_DIRECT the one-thread-per-cell kernel that reads its stencil
- * straight from global memory.  MRT_KERNEL_AUTO picks the TMA kernel, except
- * for FP64 grids of fewer than 77,824 cells, where the direct kernel (whose
- * small blocks spread the FP64 arithmetic over more SMs) is faster.  Both
- * run the same cell arithmetic; results agree to rounding. */
-typedef enum mrt_kernel { MRT_KERNEL_AUTO = 0, MRT_KERNEL_TMA = 1, MRT_KERNEL_DIRECT = 2 } mrt_kernel;
+ * straight from global memory, MRT_KERNEL_SPLIT the kernel for small grids
+ * that gives each 32-cell row segment four warps, one per velocity group
+ * (the cell update's phases split across them, so four times as many warps
+ * share the latency of one cell update); an mrt_step of two or more steps on
+ * such a grid runs them all in one cooperative launch in which each tile
+ * waits (bounded) for its neighbour tiles' previous step instead of a kernel
+ * boundary.  MRT_KERNEL_AUTO picks the split kernel for grids of at most
+ * 8,192 cells (FP64) or 2,048 cells (FP32), the direct kernel for other FP64
+ * grids of fewer than 77,824 cells (its small blocks spread the FP64
+ * arithmetic over more SMs), and the TMA kernel otherwise.  All run the same
+ * cell arithmetic; results agree to rounding. */
+typedef enum mrt_kernel { MRT_KERNEL_AUTO = 0, MRT_KERNEL_TMA = 1, MRT_KERNEL_DIRECT = 2, MRT_KERNEL_SPLIT = 3 }
+    mrt_kernel;
 
 /* Space discretisation of the advection term v_ia d_a f_i (Sect.
  * "Construction of energy-conserving MRT LB model": Lax-Wendroff in space,

@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libmrtfdlb.so")
 MRT_OK, MRT_EINVAL, MRT_ENOMEM, MRT_ECUDA, MRT_EUNSTABLE, MRT_ETIMEOUT = range(6)
 FP32, FP64 = 0, 1
 BC_PERIODIC, BC_FIXED_EQ, BC_REFLECT_FIXED = 0, 1, 2
-KERNEL_AUTO, KERNEL_TMA, KERNEL_DIRECT = 0, 1, 2
+KERNEL_AUTO, KERNEL_TMA, KERNEL_DIRECT, KERNEL_SPLIT = 0, 1, 2, 3
 ADV_LW, ADV_LW2D = 0, 1
 
 # every symbol include/mrtfdlb.h declares

@@ -134,7 +134,7 @@ extern "C" mrt_status mrt_adjoint_record(mrt_grid* g, const double* rho0, const 
         A_TRY(cudaMemcpyAsync(buf_at(t->ck, t->state_bytes, c), g->f[g->cur], t->state_bytes,
                               cudaMemcpyDeviceToDevice, g->stream));
         const long len = std::min<long>(t->K, nsteps - (long)c * t->K);
-        st = mrt_step(g, len);
+        st = mrt_step_single_launches(g, len);
         if (st != MRT_OK) return st;
     }
     return MRT_OK;

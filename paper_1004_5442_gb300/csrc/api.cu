@@ -548,11 +548,12 @@ static mrt_status validate(const mrt_params* p) {
     if (p->bc_x < MRT_BC_PERIODIC || p->bc_x > MRT_BC_REFLECT_FIXED) return fail(MRT_EINVAL, "bad bc_x");
     if (p->bc_y < MRT_BC_PERIODIC || p->bc_y > MRT_BC_REFLECT_FIXED) return fail(MRT_EINVAL, "bad bc_y");
     if (p->precision != MRT_FP32 && p->precision != MRT_FP64) return fail(MRT_EINVAL, "bad precision");
-    if (p->kernel < MRT_KERNEL_AUTO || p->kernel > MRT_KERNEL_DIRECT) return fail(MRT_EINVAL, "bad kernel");
+    if (p->kernel < MRT_KERNEL_AUTO || p->kernel > MRT_KERNEL_SPLIT) return fail(MRT_EINVAL, "bad kernel");
     if (p->tile < 0 || p->tile >= NUM_TILES) return fail(MRT_EINVAL, "bad tile %d", p->tile);
     if (p->advection != MRT_ADV_LW && p->advection != MRT_ADV_LW2D)
         return fail(MRT_EINVAL, "bad advection %d", p->advection);
-    if (p->advection == MRT_ADV_LW2D && p->kernel != MRT_KERNEL_DIRECT && !tile_supports_xt(p->tile))
+    if (p->advection == MRT_ADV_LW2D && (p->kernel == MRT_KERNEL_AUTO || p->kernel == MRT_KERNEL_TMA) &&
+        !tile_supports_xt(p->tile))
         return fail(MRT_EINVAL, "the unsplit operator runs on tiles 0, 1, 4, 5, 6 and 7");
     return MRT_OK;
 }
@@ -574,6 +575,7 @@ static void release(mrt_grid* g) {
     cudaFree(g->cap_partials);
     cudaFree(g->seq);
     cudaFree(g->qnext);
+    cudaFree(g->tile_done);
     cudaFreeHost(g->host_stage);
     for (int k = 0; k < mrt_grid::kTotalsEvents; ++k)
         if (g->tev[k]) cudaEventDestroy(g->tev[k]);
@@ -710,7 +712,10 @@ extern "C" mrt_status mrt_create(const mrt_params* params, const double* rho, co
     // direct kernel's small blocks spread the FP64 arithmetic over more SMs
     const long cells = (long)params->nx * params->ny;
     int kernel = params->kernel;
-    if (kernel == MRT_KERNEL_AUTO) kernel = (g->fp64 && cells < kSmallFp64Cells) ? MRT_KERNEL_DIRECT : MRT_KERNEL_TMA;
+    if (kernel == MRT_KERNEL_AUTO) {
+        if (cells <= (g->fp64 ? kSplitFp64Cells : kSplitFp32Cells)) kernel = MRT_KERNEL_SPLIT;
+        else kernel = (g->fp64 && cells < kSmallFp64Cells) ? MRT_KERNEL_DIRECT : MRT_KERNEL_TMA;
+    }
     int parts = 0;
     if (kernel == MRT_KERNEL_TMA) {
         int occ = 0, sms = 0;
@@ -758,8 +763,23 @@ extern "C" mrt_status mrt_create(const mrt_params* params, const double* rho, co
         }
     } else {
         dim3 gr, bl;
-        if (g->fp64) direct_grid<double>(g->L, &gr, &bl); else direct_grid<float>(g->L, &gr, &bl);
+        if (kernel == MRT_KERNEL_SPLIT) split_grid(g->L, &gr, &bl);
+        else if (g->fp64) direct_grid<double>(g->L, &gr, &bl);
+        else direct_grid<float>(g->L, &gr, &bl);
         parts = (int)(gr.x * gr.y);
+        if (kernel == MRT_KERNEL_SPLIT) {
+            // the multi-step launch keeps every block resident: one block per
+            // tile, as many as fit on the device at once
+            int coop = 0, blocks = 0;
+            cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, g->device);
+            e = g->fp64 ? split_persist_blocks<double>(g->xt, &blocks) : split_persist_blocks<float>(g->xt, &blocks);
+            if (e != cudaSuccess) return bail(fail(MRT_ECUDA, "occupancy query: %s", cudaGetErrorString(e)));
+            if (coop && blocks > 0) {
+                if ((e = cudaMalloc(&g->tile_done, sizeof(unsigned) * (size_t)parts)) != cudaSuccess)
+                    return bail(fail(MRT_ENOMEM, "cudaMalloc: %s", cudaGetErrorString(e)));
+                g->persist_blocks = std::min(blocks, parts);
+            }
+        }
     }
     g->kernel = kernel;
     g->parts = parts;
@@ -855,7 +875,8 @@ mrt_status step_between(mrt_grid* g, const void* in, void* out, const CUtensorMa
     queue_args(g, a);
     cudaError_t e = g->kernel == MRT_KERNEL_TMA
         ? launch_step_tma<T>(g->tile, g->xt, map_in, map_out, a, g->tma_grid_x, g->tma_grid_y, totals, g->stream)
-        : launch_step_direct<T>(a, g->xt, totals, g->stream);
+        : g->kernel == MRT_KERNEL_SPLIT ? launch_step_split<T>(a, g->xt, totals, g->stream)
+                                        : launch_step_direct<T>(a, g->xt, totals, g->stream);
     if (e != cudaSuccess) return fail(MRT_ECUDA, "step launch: %s", cudaGetErrorString(e));
     return MRT_OK;
 }
@@ -877,6 +898,8 @@ static mrt_status enqueue_step(mrt_grid* g, StepArgs<T>& a, bool totals, cudaStr
     if (g->kernel == MRT_KERNEL_TMA) {
         e = launch_step_tma<T>(g->tile, g->xt, &g->maps[g->cur], &g->maps_out[g->cur ^ 1], a, g->tma_grid_x,
                                g->tma_grid_y, totals, st);
+    } else if (g->kernel == MRT_KERNEL_SPLIT) {
+        e = launch_step_split<T>(a, g->xt, totals, st);
     } else {
         e = launch_step_direct<T>(a, g->xt, totals, st);
     }
@@ -930,14 +953,44 @@ static mrt_status pair_graph(mrt_grid* g, cudaGraphExec_t* out) {
 // All but the last step of a call replay two-step graphs (fewer launch gaps
 // on small grids); the last step, which also reduces totals, and an odd one
 // before it are launched directly.
+// All steps of a call in one launch of the split kernel's multi-step form,
+// the last one reducing totals.  At most 2^31 - 1 steps per launch.
 template <class T>
-static mrt_status step_impl(mrt_grid* g, long nsteps) {
+static mrt_status persist_steps(mrt_grid* g, long nsteps) {
+    StepArgs<T> a = step_args<T>(g);
+    CUDA_TRY(begin_totals(g, &a.partials, false));
+    CUDA_TRY(cudaMemsetAsync(g->tile_done, 0, sizeof(unsigned) * (size_t)g->parts, g->stream));
+    T* b0 = static_cast<T*>(g->f[g->cur]);
+    T* b1 = static_cast<T*>(g->f[g->cur ^ 1]);
+    a.in = b0;
+    a.out = b1;
+    const cudaError_t e = launch_step_split_persist<T>(a, g->xt, b0, b1, (int)nsteps, true, g->tile_done,
+                                                       g->persist_blocks, g->stream);
+    if (e != cudaSuccess) return fail(MRT_ECUDA, "multi-step launch: %s", cudaGetErrorString(e));
+    CUDA_TRY(end_totals(g, g->parts, false));
+    g->cur ^= (int)(nsteps & 1);
+    g->steps += nsteps;
+    g->totals_fresh = true;
+    return MRT_OK;
+}
+
+template <class T>
+static mrt_status step_impl(mrt_grid* g, long nsteps, bool allow_persist = true) {
     StepArgs<T> a = step_args<T>(g);
     // while a caller captures the grid's stream, every step is launched
     // directly and the totals are reduced on that stream
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     CUDA_TRY(cudaStreamIsCapturing(g->stream, &cs));
     const bool capturing = cs != cudaStreamCaptureStatusNone;
+    if (allow_persist && g->persist_blocks > 0 && nsteps >= 2 && !capturing) {
+        for (long done = 0; done < nsteps;) {
+            const long n = std::min<long>(nsteps - done, 1L << 30);
+            mrt_status st = persist_steps<T>(g, n);
+            if (st != MRT_OK) return st;
+            done += n;
+        }
+        return MRT_OK;
+    }
     long plain = nsteps - 1;
     if (plain >= 2 && !capturing) {
         cudaGraphExec_t& ex = g->pair_exec[g->cur][g->qpar & 1];
@@ -960,6 +1013,13 @@ static mrt_status step_impl(mrt_grid* g, long nsteps) {
         g->totals_fresh = true;
     }
     return MRT_OK;
+}
+
+// Steps launched one at a time (the form the reverse sweep recomputes a
+// segment with), for the recorded forward run of the reverse mode.
+mrt_status mrt_step_single_launches(mrt_grid* g, long nsteps) {
+    if (nsteps <= 0) return MRT_OK;
+    return g->fp64 ? step_impl<double>(g, nsteps, false) : step_impl<float>(g, nsteps, false);
 }
 
 extern "C" mrt_status mrt_step(mrt_grid* g, long nsteps) {

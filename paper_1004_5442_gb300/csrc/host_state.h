@@ -95,6 +95,10 @@ struct mrt_grid {
     int strips = 0, nitems = 0;      // work-queue tiles: strips and (row band, strip) items
     int parts = 0;                   // block partials a totals step writes
     unsigned* qnext = nullptr;       // work-queue tiles: two launch counters
+    // split kernel: completed-step count per tile for the multi-step launch,
+    // and the number of blocks that launch uses (0: not available)
+    unsigned* tile_done = nullptr;
+    int persist_blocks = 0;
     int qpar = 0;                    // which counter the next launch uses
     mrt::Coef<double> kd;
     mrt::Coef<float> kf;
@@ -115,3 +119,7 @@ mrt_status step_between(mrt_grid* g, const void* in, void* out, const CUtensorMa
 mrt_status mrt_reinit(mrt_grid* g, const double* rho, const double* ux, const double* uy, const double* T,
                       int on_device);
 mrt_status mrt_fail(mrt_status s, const char* fmt, ...);
+// mrt_step without the split kernel's multi-step launch: every step its own
+// launch, as the reverse sweep recomputes its segments, so recorded and
+// recomputed states are the same bits.
+mrt_status mrt_step_single_launches(mrt_grid* g, long nsteps);

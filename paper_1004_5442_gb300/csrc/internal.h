@@ -35,6 +35,13 @@ struct NvtxRange {
 // FP64 grids below this many cells (4 rows of 128 cells per SM) run the
 // direct kernel under MRT_KERNEL_AUTO.
 constexpr long kSmallFp64Cells = 152L * 128 * 4;
+// Grids up to this many cells run the split kernel (and its multi-step
+// launch) under MRT_KERNEL_AUTO.  Measured per step: FP64 400 x 4 5.0 us and
+// 1300 x 4 7.1 us against 11.3 us for the direct kernel, but 2048 x 8 12.7
+// against 12.3; FP32 400 x 4 2.4 us against 4.1 us (the launch period of
+// this part), 1300 x 4 6.2 against 4.1.
+constexpr long kSplitFp64Cells = 8192;
+constexpr long kSplitFp32Cells = 2048;
 
 // Flag word bits written by the kernels.
 constexpr unsigned FLAG_UNSTABLE = 1u;  // rho or P not positive, or not finite
@@ -140,6 +147,21 @@ template <class T>
 cudaError_t tma_occupancy(int tile, bool xt, int* blocks_per_sm);
 template <class T>
 void direct_grid(const Layout& L, dim3* grid, dim3* block);
+// Four warps per 32-cell row segment, one per velocity group (small grids);
+// one totals partial per block.
+template <class T>
+cudaError_t launch_step_split(const StepArgs<T>& a, bool xt, bool totals, cudaStream_t st);
+void split_grid(const Layout& L, dim3* grid, dim3* block);
+// All nsteps of a call in one cooperative launch of split tiles (small
+// grids): step s reads buf0 for even s, buf1 for odd s; the last step
+// writes totals partials (one per tile) if totals; done holds one
+// completed-step count per tile and must be zero at launch.  blocks: at most
+// split_persist_blocks (every block resident).
+template <class T>
+cudaError_t split_persist_blocks(bool xt, int* blocks);
+template <class T>
+cudaError_t launch_step_split_persist(const StepArgs<T>& a, bool xt, T* buf0, T* buf1, int nsteps, bool totals,
+                                      unsigned* done, int blocks, cudaStream_t st);
 
 
 // Reverse-sweep arguments (adjoint_kernels.cu).

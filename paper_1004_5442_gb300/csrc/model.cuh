@@ -155,228 +155,318 @@ __device__ __forceinline__ T recip(T x) { return (T)1 / x; }
 template <>
 __device__ __forceinline__ float recip<float>(float x) { return __fdividef(1.0f, x); }
 
-// One cell of one time step (Eq. 3, forward Euler + Lax-Wendroff):
-// reads the stencil through F(i, pos), writes f^{n+1} to out and returns
-// the cell's input rho and P for the health check.
+// The cell update is written in phases, so that one thread can run all of
+// them for a cell (cell_update) or four threads can share a cell, one per
+// velocity group (the split kernel), with bit-identical arithmetic.
+
+// Phase 1, per group g: the butterflies of its four values (the order inside
+// a group is (+x, +y, -x, -y) or ((+,+), (-,+), (-,-), (+,-))).
+template <class T>
+struct GroupSums {
+    T S, QX, Dx, Dy;
+};
+template <class T>
+__device__ __forceinline__ GroupSums<T> group_sums(int g, const T q[4]) {
+    GroupSums<T> r;
+    const T s02 = q[0] + q[2], s13 = q[1] + q[3];
+    const T d02 = q[0] - q[2], d13 = q[1] - q[3];
+    r.S = s02 + s13;
+    r.QX = s02 - s13;
+    if (g < 2) { r.Dx = d02; r.Dy = d13; }
+    else { r.Dx = d02 - d13; r.Dy = d02 + d13; }
+    return r;
+}
+
+// Phase 2, per block of moment rows (eta^2 = 25/4 on group 0 only, so
+// W_g = V_g except W_0 = V_0 + 25/4):
+//   (m1, m5, m4, m14) from S_0..3;  (m2, m12, m10, m8) from Dx_0..3 and
+//   (m3, -m13, m11, m9) from Dy_0..3;  (m6, m16, m7, m15) from QX_0..3.
+constexpr double kEta2 = 6.25;
+template <class T>
+__device__ __forceinline__ void moments_S(const T S[4], T m[4]) {
+    m[0] = (S[0] + S[1]) + (S[2] + S[3]);
+    m[1] = (T)kV(0) * S[0] + (T)kV(1) * S[1] + (T)kV(2) * S[2] + (T)kV(3) * S[3];
+    m[2] = (T)kEta2 * S[0] + m[1];
+    m[3] = (T)(kV(0) * kW(0)) * S[0] + (T)(kV(1) * kW(1)) * S[1]
+         + (T)(kV(2) * kW(2)) * S[2] + (T)(kV(3) * kW(3)) * S[3];
+}
+template <class T>
+__device__ __forceinline__ void moments_D(const T D[4], T m[4]) {
+    m[0] = (T)kU(0) * D[0] + (T)kU(1) * D[1] + (T)kU(2) * D[2] + (T)kU(3) * D[3];
+    m[1] = (T)(kU(1) * kV(1)) * D[1] + D[0];                 // u^3 on the axis groups
+    m[2] = (T)(kU(3) * kV(3)) * D[3] + ((T)(kU(2) * kV(2)) * D[2] + m[1]);
+    m[3] = (T)kEta2 * D[0] + m[2];
+}
+template <class T>
+__device__ __forceinline__ void moments_Q(const T QX[4], T m[4]) {
+    m[0] = (T)kV(1) * QX[1] + QX[0];
+    m[1] = (T)(kV(1) * kW(1)) * QX[1] + (T)(kV(0) * kW(0)) * QX[0];
+    m[2] = (T)(0.5 * kV(3)) * QX[3] + (T)(0.5 * kV(2)) * QX[2];
+    m[3] = (T)(0.5 * kV(3) * kW(3)) * QX[3] + (T)(0.5 * kV(2) * kW(2)) * QX[2];
+}
+
+// Phase 3: the closure P = (e - j^2/rho)/b, T = P/rho (R = 1) and the terms
+// the equilibrium moments of every block share (Appendix).
+template <class T>
+struct EqBase {
+    T rinv, ux, uy, kx, ky, j2r, P, Tt, twoP, q5, q6;
+};
+template <class T>
+__device__ __forceinline__ EqBase<T> eq_base(T rho, T jx, T jy, T e, const Coef<T>& k) {
+    EqBase<T> b;
+    b.rinv = recip<T>(rho);
+    b.ux = jx * b.rinv;
+    b.uy = jy * b.rinv;
+    b.kx = jx * b.ux;
+    b.ky = jy * b.uy;
+    b.j2r = b.kx + b.ky;                        // j^2 / rho
+    b.P = (e - b.j2r) * k.inv_b;
+    b.Tt = b.P * b.rinv;
+    b.twoP = b.P + b.P;
+    b.q5 = b.twoP + b.j2r;
+    b.q6 = b.kx - b.ky;                         // (jx^2 - jy^2)/rho
+    return b;
+}
+
+// Relaxed residuals Delta_k = sigma_k (m_k - m^eq_k), k = 5..16 (-Delta_13 in
+// nd13); FP64 keeps m_k - m^eq_k, its constants carry sigma_k.
+template <class T>
+struct Deltas {
+    T d5, d6, d7, d8, d9, d10, d11, d12, nd13, d14, d15, d16;
+};
+template <class T>
+__device__ __forceinline__ T relax(const Coef<T>& k, int j, T r) {
+    if constexpr (sizeof(T) == 8) return r; else return k.sig[j] * r;
+}
+// block S: m5, m14
+template <class T>
+__device__ __forceinline__ void relax_S(const EqBase<T>& b, T m5, T m14, const Coef<T>& k, Deltas<T>& D) {
+    const T u2 = b.ux * b.ux + b.uy * b.uy;
+    const T q14 = b.Tt * (k.c14a * b.P + k.c14b * b.j2r) + b.j2r * u2;
+    D.d5 = relax(k, 0, m5 - b.q5);
+    D.d14 = relax(k, 9, m14 - q14);
+}
+// block Dx: m8, m10, m12 (e the energy moment m4)
+template <class T>
+__device__ __forceinline__ void relax_Dx(const EqBase<T>& b, T e, T m8, T m10, T m12, const Coef<T>& k,
+                                         Deltas<T>& D) {
+    const T e2P = e + b.twoP;
+    const T q8 = e2P * b.ux;
+    const T h10 = b.twoP + b.q5;                // 4P + j^2/rho
+    const T q10 = h10 * b.ux;
+    const T q12 = (b.twoP + b.q6) * b.ux;
+    D.d8 = relax(k, 3, m8 - q8);
+    D.d10 = relax(k, 5, m10 - q10);
+    D.d12 = relax(k, 7, m12 - q12);
+}
+// block Dy: m9, m11, -m13
+template <class T>
+__device__ __forceinline__ void relax_Dy(const EqBase<T>& b, T e, T m9, T m11, T n13, const Coef<T>& k,
+                                         Deltas<T>& D) {
+    const T e2P = e + b.twoP;
+    const T q9 = e2P * b.uy;
+    const T h10 = b.twoP + b.q5;
+    const T q11 = h10 * b.uy;
+    const T nq13 = (b.twoP - b.q6) * b.uy;      // -q13
+    D.d9 = relax(k, 4, m9 - q9);
+    D.d11 = relax(k, 6, m11 - q11);
+    D.nd13 = relax(k, 8, n13 - nq13);
+}
+// block Q: m6, m16, m7, m15 (jx the x momentum m2)
+template <class T>
+__device__ __forceinline__ void relax_Q(const EqBase<T>& b, T jx, T m6, T m16, T m7, T m15, const Coef<T>& k,
+                                        Deltas<T>& D) {
+    const T q7 = jx * b.uy;
+    const T g15 = k.c15 * b.P + b.j2r;
+    const T q15 = g15 * (b.ux * b.uy);
+    const T q16 = g15 * (b.ux * b.ux - b.uy * b.uy);
+    D.d6 = relax(k, 1, m6 - b.q6);
+    D.d7 = relax(k, 2, m7 - q7);
+    D.d15 = relax(k, 10, m15 - q15);
+    D.d16 = relax(k, 11, m16 - q16);
+}
+
+// Phase 4, per group g: the collision increment of its four velocities
+// (inverse blocks, already scaled by the inverse butterflies' 1/4 or 1/2
+// and by -1) and the Lax-Wendroff advection, from the centre values fg and
+// the neighbours read through F(plane, pos); writes og.
 //
-// The Lax-Wendroff terms are accumulated as multiply-adds of neighbour
-// differences onto the collision increment, so a uniform state is left
-// exactly unchanged by the advection in any precision.
+// The FP32 form accumulates the Lax-Wendroff terms as multiply-adds of
+// neighbour differences onto the collision increment, so a uniform state is
+// left exactly unchanged by the advection.
 //
 // XT: the unsplit two-dimensional Lax-Wendroff operator, which adds to each
 // diagonal velocity the mixed term (c_x c_y / 4)(f(x+1,y+1) - f(x+1,y-1)
 // - f(x-1,y+1) + f(x-1,y-1)) of the second-order Taylor expansion in time
 // (c_x c_y > 0 for (+,+) and (-,-), < 0 for (-,+) and (+,-)).
+template <class T, bool XT, class Fetch>
+__device__ __forceinline__ void group_update(int g, const Fetch& F, const Coef<T>& k, const Deltas<T>& D,
+                                             const T fg[4], T og[4]) {
+    constexpr bool kFold = sizeof(T) == 8;
+    T cS, cX, cY;
+    if constexpr (kFold) {
+        cS = k.kSs[g][0] * D.d5 + k.kSs[g][1] * D.d14;
+        cX = k.kDx[g][0] * D.d8 + k.kDx[g][1] * D.d10 + k.kDx[g][2] * D.d12;
+        cY = k.kDy[g][0] * D.d9 + k.kDy[g][1] * D.d11 + k.kDy[g][2] * D.nd13;
+    } else {
+        cS = k.kS[g][0] * D.d5 + k.kS[g][1] * D.d14;
+        cX = k.kD[g][0] * D.d8 + k.kD[g][1] * D.d10 + k.kD[g][2] * D.d12;
+        cY = k.kD[g][0] * D.d9 + k.kD[g][1] * D.d11 + k.kD[g][2] * D.nd13;
+    }
+    const T p = k.lwp[g], qq = k.lwq[g];
+    const int i0 = 4 * g;  // plane of the group's first velocity
+    if constexpr (kFold) {
+      if (g < 2) {
+        // FP64: out = a0 f + p f_up + q f_down + collision, one
+        // multiply-add per neighbour (+x: p on x-1, q on x+1; -x mirrored;
+        // +y / -y likewise along y)
+        const T cQ = k.kQs[g][0] * D.d6 + k.kQs[g][1] * D.d16;
+        const T sp = cS + cQ, sm = cS - cQ;
+        const T a0 = k.lw0[g];
+        og[0] = a0 * fg[0] + (p * F(i0 + 0, XM) + (qq * F(i0 + 0, XP) + (sp + cX)));
+        og[2] = a0 * fg[2] + (p * F(i0 + 2, XP) + (qq * F(i0 + 2, XM) + (sp - cX)));
+        og[1] = a0 * fg[1] + (p * F(i0 + 1, YM) + (qq * F(i0 + 1, YP) + (sm + cY)));
+        og[3] = a0 * fg[3] + (p * F(i0 + 3, YP) + (qq * F(i0 + 3, YM) + (sm - cY)));
+      } else {
+        // FP64 diagonal groups: a0 = 1 - 2 c^2; the mixed term of the
+        // unsplit operator enters as four more multiply-adds
+        const T cXY = k.kXs[g - 2][0] * D.d7 + k.kXs[g - 2][1] * D.d15;
+        const T t1 = cS + cXY, t2 = cS - cXY, s1 = cX + cY, s2 = cX - cY;
+        const T a0 = k.lw0[g];
+        auto mixed = [&](int i, T w, T acc) -> T {
+            if constexpr (XT)
+                return w * F(i, XPYP) + (-w * F(i, XPYM) + (-w * F(i, XMYP) + (w * F(i, XMYM) + acc)));
+            else
+                return acc;
+        };
+        const T w = XT ? k.kxy[g - 2] : (T)0;
+        {   // (+,+): p on x-1, y-1; q on x+1, y+1
+            const T c0 = mixed(i0 + 0, w, t1 + s1);
+            og[0] = a0 * fg[0] + (p * (F(i0 + 0, XM) + F(i0 + 0, YM)) +
+                                             (qq * (F(i0 + 0, XP) + F(i0 + 0, YP)) + c0));
+        }
+        {   // (-,+): p on x+1, y-1; q on x-1, y+1
+            const T c1 = mixed(i0 + 1, -w, t2 - s2);
+            og[1] = a0 * fg[1] + (p * (F(i0 + 1, XP) + F(i0 + 1, YM)) +
+                                             (qq * (F(i0 + 1, XM) + F(i0 + 1, YP)) + c1));
+        }
+        {   // (-,-): p on x+1, y+1; q on x-1, y-1
+            const T c2 = mixed(i0 + 2, w, t1 - s1);
+            og[2] = a0 * fg[2] + (p * (F(i0 + 2, XP) + F(i0 + 2, YP)) +
+                                             (qq * (F(i0 + 2, XM) + F(i0 + 2, YM)) + c2));
+        }
+        {   // (+,-): p on x-1, y+1; q on x+1, y-1
+            const T c3 = mixed(i0 + 3, -w, t2 + s2);
+            og[3] = a0 * fg[3] + (p * (F(i0 + 3, XM) + F(i0 + 3, YP)) +
+                                             (qq * (F(i0 + 3, XP) + F(i0 + 3, YM)) + c3));
+        }
+      }
+    } else {
+      if (g < 2) {
+        const T cQ = k.kQ[g][0] * D.d6 + k.kQ[g][1] * D.d16;
+        const T sp = cS + cQ, sm = cS - cQ;
+        // +x: p on x-1, q on x+1; -x mirrored; +y / -y likewise along y
+        {
+            const T fc = fg[0];
+            T t = qq * (F(i0 + 0, XP) - fc) + (sp + cX);
+            og[0] = fc + (p * (F(i0 + 0, XM) - fc) + t);
+        }
+        {
+            const T fc = fg[2];
+            T t = p * (F(i0 + 2, XP) - fc) + (sp - cX);
+            og[2] = fc + (qq * (F(i0 + 2, XM) - fc) + t);
+        }
+        {
+            const T fc = fg[1];
+            T t = qq * (F(i0 + 1, YP) - fc) + (sm + cY);
+            og[1] = fc + (p * (F(i0 + 1, YM) - fc) + t);
+        }
+        {
+            const T fc = fg[3];
+            T t = p * (F(i0 + 3, YP) - fc) + (sm - cY);
+            og[3] = fc + (qq * (F(i0 + 3, YM) - fc) + t);
+        }
+    } else {
+        const T cXY = k.kX[g - 2][0] * D.d7 + k.kX[g - 2][1] * D.d15;
+        const T t1 = cS + cXY, t2 = cS - cXY, s1 = cX + cY, s2 = cX - cY;
+        // XT: mixed terms, (f++ - f+-) - (f-+ - f--) scaled by |c_x c_y|/4
+        // and signed by c_x c_y; exactly 0 on a uniform state
+        T e0 = 0, e1 = 0, e2 = 0, e3 = 0;
+        auto with_mixed = [](T v, T e) -> T {
+            if constexpr (XT) return v + e; else return v;
+        };
+        if constexpr (XT) {
+            const T w = k.kxy[g - 2];
+            auto mixed = [&](int i) { return (F(i, XPYP) - F(i, XPYM)) - (F(i, XMYP) - F(i, XMYM)); };
+            e0 = w * mixed(i0 + 0);
+            e1 = -(w * mixed(i0 + 1));
+            e2 = w * mixed(i0 + 2);
+            e3 = -(w * mixed(i0 + 3));
+        }
+        // |c_x| = |c_y| on a diagonal: pair the x and y neighbours that
+        // carry the same weight, (a + b - 2 f) is exact for a uniform state
+        {   // (+,+): p on x-1, y-1; q on x+1, y+1
+            const T fc = fg[0];
+            const T a = (F(i0 + 0, XM) + F(i0 + 0, YM)) - (fc + fc);
+            const T b = (F(i0 + 0, XP) + F(i0 + 0, YP)) - (fc + fc);
+            og[0] = fc + (p * a + (qq * b + with_mixed((t1 + s1), e0)));
+        }
+        {   // (-,+): q on x-1, p on x+1; p on y-1, q on y+1
+            const T fc = fg[1];
+            const T a = (F(i0 + 1, XP) + F(i0 + 1, YM)) - (fc + fc);
+            const T b = (F(i0 + 1, XM) + F(i0 + 1, YP)) - (fc + fc);
+            og[1] = fc + (p * a + (qq * b + with_mixed((t2 - s2), e1)));
+        }
+        {   // (-,-): q on x-1, y-1; p on x+1, y+1
+            const T fc = fg[2];
+            const T a = (F(i0 + 2, XP) + F(i0 + 2, YP)) - (fc + fc);
+            const T b = (F(i0 + 2, XM) + F(i0 + 2, YM)) - (fc + fc);
+            og[2] = fc + (p * a + (qq * b + with_mixed((t1 - s1), e2)));
+        }
+        {   // (+,-): p on x-1, q on x+1; q on y-1, p on y+1
+            const T fc = fg[3];
+            const T a = (F(i0 + 3, XM) + F(i0 + 3, YP)) - (fc + fc);
+            const T b = (F(i0 + 3, XP) + F(i0 + 3, YM)) - (fc + fc);
+            og[3] = fc + (p * a + (qq * b + with_mixed((t2 + s2), e3)));
+        }
+      }
+    }
+}
+
+// One cell of one time step (Eq. 3, forward Euler + Lax-Wendroff): reads
+// the stencil through F(i, pos), writes f^{n+1} to out and returns the
+// cell's input rho and P for the health check.
 template <class T, bool XT = false, class Fetch>
 __device__ __forceinline__ void cell_update(const Fetch& F, const Coef<T>& k, T out[NV],
                                             T& rho_in, T& P_in) {
     T f[NV];
 #pragma unroll
     for (int i = 0; i < NV; ++i) f[i] = F(i, C);
-
-    // ---- forward transform: butterflies, then the five blocks ----------
     T S[4], Dx[4], Dy[4], QX[4];
 #pragma unroll
     for (int g = 0; g < 4; ++g) {
-        const T* q = f + 4 * g;
-        const T s02 = q[0] + q[2], s13 = q[1] + q[3];
-        const T d02 = q[0] - q[2], d13 = q[1] - q[3];
-        S[g] = s02 + s13;
-        QX[g] = s02 - s13;
-        if (g < 2) { Dx[g] = d02; Dy[g] = d13; }
-        else { Dx[g] = d02 - d13; Dy[g] = d02 + d13; }
+        const GroupSums<T> gs = group_sums<T>(g, f + 4 * g);
+        S[g] = gs.S;
+        QX[g] = gs.QX;
+        Dx[g] = gs.Dx;
+        Dy[g] = gs.Dy;
     }
-    // eta^2 = 25/4 on group 0 only, so W_g = V_g except W_0 = V_0 + 25/4.
-    constexpr double E2 = 6.25;
-    const T m1 = (S[0] + S[1]) + (S[2] + S[3]);
-    const T m5 = (T)kV(0) * S[0] + (T)kV(1) * S[1] + (T)kV(2) * S[2] + (T)kV(3) * S[3];
-    const T m4 = (T)E2 * S[0] + m5;
-    const T m14 = (T)(kV(0) * kW(0)) * S[0] + (T)(kV(1) * kW(1)) * S[1]
-                + (T)(kV(2) * kW(2)) * S[2] + (T)(kV(3) * kW(3)) * S[3];
-    const T m2 = (T)kU(0) * Dx[0] + (T)kU(1) * Dx[1] + (T)kU(2) * Dx[2] + (T)kU(3) * Dx[3];
-    const T m12 = (T)(kU(1) * kV(1)) * Dx[1] + Dx[0];                 // u^3 on the axis groups
-    const T m10 = (T)(kU(3) * kV(3)) * Dx[3] + ((T)(kU(2) * kV(2)) * Dx[2] + m12);
-    const T m8 = (T)E2 * Dx[0] + m10;
-    const T m3 = (T)kU(0) * Dy[0] + (T)kU(1) * Dy[1] + (T)kU(2) * Dy[2] + (T)kU(3) * Dy[3];
-    const T n13 = (T)(kU(1) * kV(1)) * Dy[1] + Dy[0];                 // -m13
-    const T m11 = (T)(kU(3) * kV(3)) * Dy[3] + ((T)(kU(2) * kV(2)) * Dy[2] + n13);
-    const T m9 = (T)E2 * Dy[0] + m11;
-    const T m6 = (T)kV(1) * QX[1] + QX[0];
-    const T m16 = (T)(kV(1) * kW(1)) * QX[1] + (T)(kV(0) * kW(0)) * QX[0];
-    const T m7 = (T)(0.5 * kV(3)) * QX[3] + (T)(0.5 * kV(2)) * QX[2];
-    const T m15 = (T)(0.5 * kV(3) * kW(3)) * QX[3] + (T)(0.5 * kV(2) * kW(2)) * QX[2];
-
-    // ---- equilibrium moments (Appendix), P = (e - j^2/rho)/b, R = 1 ------
-    const T rho = m1, jx = m2, jy = m3, e = m4;
-    const T rinv = recip<T>(rho);
-    const T ux = jx * rinv, uy = jy * rinv;
-    const T kx = jx * ux, ky = jy * uy;
-    const T j2r = kx + ky;                       // j^2 / rho
-    const T P = (e - j2r) * k.inv_b;
-    const T Tt = P * rinv;
-    const T twoP = P + P;
-    const T q5 = twoP + j2r;
-    const T q6 = kx - ky;                        // (jx^2 - jy^2)/rho
-    const T q7 = jx * uy;
-    const T e2P = e + twoP;
-    const T q8 = e2P * ux, q9 = e2P * uy;
-    const T h10 = twoP + q5;                     // 4P + j^2/rho
-    const T q10 = h10 * ux, q11 = h10 * uy;
-    const T q12 = (twoP + q6) * ux;
-    const T nq13 = (twoP - q6) * uy;             // -q13
-    const T u2 = ux * ux + uy * uy;
-    const T q14 = Tt * (k.c14a * P + k.c14b * j2r) + j2r * u2;
-    const T g15 = k.c15 * P + j2r;
-    const T q15 = g15 * (ux * uy);
-    const T q16 = g15 * (ux * ux - uy * uy);
-    rho_in = rho;
-    P_in = P;
-
-    // ---- relaxation Delta_k = sigma_k (m_k - m^eq_k), k = 5..16 ---------
-    // (FP64: the residuals m_k - m^eq_k alone; sigma_k is in the constants)
-    constexpr bool kFold = sizeof(T) == 8;
-    auto relax = [&](int j, T r) -> T {
-        if constexpr (kFold) return r; else return k.sig[j] * r;
-    };
-    const T d5 = relax(0, m5 - q5), d6 = relax(1, m6 - q6), d7 = relax(2, m7 - q7);
-    const T d8 = relax(3, m8 - q8), d9 = relax(4, m9 - q9);
-    const T d10 = relax(5, m10 - q10), d11 = relax(6, m11 - q11);
-    const T d12 = relax(7, m12 - q12), nd13 = relax(8, n13 - nq13);   // -Delta_13
-    const T d14 = relax(9, m14 - q14), d15 = relax(10, m15 - q15);
-    const T d16 = relax(11, m16 - q16);
-
-    // ---- inverse blocks (scaled), inverse butterflies, then advection ----
+    T mS[4], mX[4], mY[4], mQ[4];
+    moments_S<T>(S, mS);
+    moments_D<T>(Dx, mX);
+    moments_D<T>(Dy, mY);
+    moments_Q<T>(QX, mQ);
+    // rho = m1, jx = m2, jy = m3, e = m4
+    const EqBase<T> b = eq_base<T>(mS[0], mX[0], mY[0], mS[2], k);
+    rho_in = mS[0];
+    P_in = b.P;
+    Deltas<T> D;
+    relax_S<T>(b, mS[1], mS[3], k, D);
+    relax_Dx<T>(b, mS[2], mX[3], mX[2], mX[1], k, D);
+    relax_Dy<T>(b, mS[2], mY[3], mY[2], mY[1], k, D);
+    relax_Q<T>(b, mX[0], mQ[0], mQ[1], mQ[2], mQ[3], k, D);
 #pragma unroll
-    for (int g = 0; g < 4; ++g) {
-        T cS, cX, cY;
-        if constexpr (kFold) {
-            cS = k.kSs[g][0] * d5 + k.kSs[g][1] * d14;
-            cX = k.kDx[g][0] * d8 + k.kDx[g][1] * d10 + k.kDx[g][2] * d12;
-            cY = k.kDy[g][0] * d9 + k.kDy[g][1] * d11 + k.kDy[g][2] * nd13;
-        } else {
-            cS = k.kS[g][0] * d5 + k.kS[g][1] * d14;
-            cX = k.kD[g][0] * d8 + k.kD[g][1] * d10 + k.kD[g][2] * d12;
-            cY = k.kD[g][0] * d9 + k.kD[g][1] * d11 + k.kD[g][2] * nd13;
-        }
-        const T p = k.lwp[g], qq = k.lwq[g];
-        const int i0 = 4 * g;
-        if constexpr (kFold) {
-          if (g < 2) {
-            // FP64: out = a0 f + p f_up + q f_down + collision, one
-            // multiply-add per neighbour (+x: p on x-1, q on x+1; -x mirrored;
-            // +y / -y likewise along y)
-            const T cQ = k.kQs[g][0] * d6 + k.kQs[g][1] * d16;
-            const T sp = cS + cQ, sm = cS - cQ;
-            const T a0 = k.lw0[g];
-            out[i0 + 0] = a0 * f[i0 + 0] + (p * F(i0 + 0, XM) + (qq * F(i0 + 0, XP) + (sp + cX)));
-            out[i0 + 2] = a0 * f[i0 + 2] + (p * F(i0 + 2, XP) + (qq * F(i0 + 2, XM) + (sp - cX)));
-            out[i0 + 1] = a0 * f[i0 + 1] + (p * F(i0 + 1, YM) + (qq * F(i0 + 1, YP) + (sm + cY)));
-            out[i0 + 3] = a0 * f[i0 + 3] + (p * F(i0 + 3, YP) + (qq * F(i0 + 3, YM) + (sm - cY)));
-          } else {
-            // FP64 diagonal groups: a0 = 1 - 2 c^2; the mixed term of the
-            // unsplit operator enters as four more multiply-adds
-            const T cXY = k.kXs[g - 2][0] * d7 + k.kXs[g - 2][1] * d15;
-            const T t1 = cS + cXY, t2 = cS - cXY, s1 = cX + cY, s2 = cX - cY;
-            const T a0 = k.lw0[g];
-            auto mixed = [&](int i, T w, T acc) -> T {
-                if constexpr (XT)
-                    return w * F(i, XPYP) + (-w * F(i, XPYM) + (-w * F(i, XMYP) + (w * F(i, XMYM) + acc)));
-                else
-                    return acc;
-            };
-            const T w = XT ? k.kxy[g - 2] : (T)0;
-            {   // (+,+): p on x-1, y-1; q on x+1, y+1
-                const T c0 = mixed(i0 + 0, w, t1 + s1);
-                out[i0 + 0] = a0 * f[i0 + 0] + (p * (F(i0 + 0, XM) + F(i0 + 0, YM)) +
-                                                 (qq * (F(i0 + 0, XP) + F(i0 + 0, YP)) + c0));
-            }
-            {   // (-,+): p on x+1, y-1; q on x-1, y+1
-                const T c1 = mixed(i0 + 1, -w, t2 - s2);
-                out[i0 + 1] = a0 * f[i0 + 1] + (p * (F(i0 + 1, XP) + F(i0 + 1, YM)) +
-                                                 (qq * (F(i0 + 1, XM) + F(i0 + 1, YP)) + c1));
-            }
-            {   // (-,-): p on x+1, y+1; q on x-1, y-1
-                const T c2 = mixed(i0 + 2, w, t1 - s1);
-                out[i0 + 2] = a0 * f[i0 + 2] + (p * (F(i0 + 2, XP) + F(i0 + 2, YP)) +
-                                                 (qq * (F(i0 + 2, XM) + F(i0 + 2, YM)) + c2));
-            }
-            {   // (+,-): p on x-1, y+1; q on x+1, y-1
-                const T c3 = mixed(i0 + 3, -w, t2 + s2);
-                out[i0 + 3] = a0 * f[i0 + 3] + (p * (F(i0 + 3, XM) + F(i0 + 3, YP)) +
-                                                 (qq * (F(i0 + 3, XP) + F(i0 + 3, YM)) + c3));
-            }
-          }
-        } else {
-          if (g < 2) {
-            const T cQ = k.kQ[g][0] * d6 + k.kQ[g][1] * d16;
-            const T sp = cS + cQ, sm = cS - cQ;
-            // +x: p on x-1, q on x+1; -x mirrored; +y / -y likewise along y
-            {
-                const T fc = f[i0 + 0];
-                T t = qq * (F(i0 + 0, XP) - fc) + (sp + cX);
-                out[i0 + 0] = fc + (p * (F(i0 + 0, XM) - fc) + t);
-            }
-            {
-                const T fc = f[i0 + 2];
-                T t = p * (F(i0 + 2, XP) - fc) + (sp - cX);
-                out[i0 + 2] = fc + (qq * (F(i0 + 2, XM) - fc) + t);
-            }
-            {
-                const T fc = f[i0 + 1];
-                T t = qq * (F(i0 + 1, YP) - fc) + (sm + cY);
-                out[i0 + 1] = fc + (p * (F(i0 + 1, YM) - fc) + t);
-            }
-            {
-                const T fc = f[i0 + 3];
-                T t = p * (F(i0 + 3, YP) - fc) + (sm - cY);
-                out[i0 + 3] = fc + (qq * (F(i0 + 3, YM) - fc) + t);
-            }
-        } else {
-            const T cXY = k.kX[g - 2][0] * d7 + k.kX[g - 2][1] * d15;
-            const T t1 = cS + cXY, t2 = cS - cXY, s1 = cX + cY, s2 = cX - cY;
-            // XT: mixed terms, (f++ - f+-) - (f-+ - f--) scaled by |c_x c_y|/4
-            // and signed by c_x c_y; exactly 0 on a uniform state
-            T e0 = 0, e1 = 0, e2 = 0, e3 = 0;
-            auto with_mixed = [](T v, T e) -> T {
-                if constexpr (XT) return v + e; else return v;
-            };
-            if constexpr (XT) {
-                const T w = k.kxy[g - 2];
-                auto mixed = [&](int i) { return (F(i, XPYP) - F(i, XPYM)) - (F(i, XMYP) - F(i, XMYM)); };
-                e0 = w * mixed(i0 + 0);
-                e1 = -(w * mixed(i0 + 1));
-                e2 = w * mixed(i0 + 2);
-                e3 = -(w * mixed(i0 + 3));
-            }
-            // |c_x| = |c_y| on a diagonal: pair the x and y neighbours that
-            // carry the same weight, (a + b - 2 f) is exact for a uniform state
-            {   // (+,+): p on x-1, y-1; q on x+1, y+1
-                const T fc = f[i0 + 0];
-                const T a = (F(i0 + 0, XM) + F(i0 + 0, YM)) - (fc + fc);
-                const T b = (F(i0 + 0, XP) + F(i0 + 0, YP)) - (fc + fc);
-                out[i0 + 0] = fc + (p * a + (qq * b + with_mixed((t1 + s1), e0)));
-            }
-            {   // (-,+): q on x-1, p on x+1; p on y-1, q on y+1
-                const T fc = f[i0 + 1];
-                const T a = (F(i0 + 1, XP) + F(i0 + 1, YM)) - (fc + fc);
-                const T b = (F(i0 + 1, XM) + F(i0 + 1, YP)) - (fc + fc);
-                out[i0 + 1] = fc + (p * a + (qq * b + with_mixed((t2 - s2), e1)));
-            }
-            {   // (-,-): q on x-1, y-1; p on x+1, y+1
-                const T fc = f[i0 + 2];
-                const T a = (F(i0 + 2, XP) + F(i0 + 2, YP)) - (fc + fc);
-                const T b = (F(i0 + 2, XM) + F(i0 + 2, YM)) - (fc + fc);
-                out[i0 + 2] = fc + (p * a + (qq * b + with_mixed((t1 - s1), e2)));
-            }
-            {   // (+,-): p on x-1, q on x+1; q on y-1, p on y+1
-                const T fc = f[i0 + 3];
-                const T a = (F(i0 + 3, XM) + F(i0 + 3, YP)) - (fc + fc);
-                const T b = (F(i0 + 3, XP) + F(i0 + 3, YM)) - (fc + fc);
-                out[i0 + 3] = fc + (p * a + (qq * b + with_mixed((t2 + s2), e3)));
-            }
-          }
-        }
-    }
+    for (int g = 0; g < 4; ++g) group_update<T, XT>(g, F, k, D, f + 4 * g, out + 4 * g);
 }
 
 #endif  // __CUDACC__

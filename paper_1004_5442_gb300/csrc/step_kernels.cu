@@ -152,6 +152,282 @@ __global__ void __launch_bounds__(DIR_BX* BY) step_direct(const StepArgs<T> a) {
     }
 }
 
+// --------------------------------------------------------------------------
+// Four warps per 32-cell row segment, one per velocity group: for grids too
+// small to fill the SMs with one cell per thread, where one warp per SM
+// would wait out the dependent latency of a whole cell update alone.  The
+// phases of cell_update run split across the warps, bit for bit the same
+// arithmetic: warp g reads the stencil of group g and forms its butterfly
+// sums; the warps take one block of moment rows each; every warp forms the
+// closure and the relaxed residuals of its block; each warp applies the
+// inverse and the Lax-Wendroff update to its own four velocities.  Shared
+// memory carries the sums, moments and residuals between the phases.
+// --------------------------------------------------------------------------
+constexpr int SPLIT_W = 32;
+
+// Store a group's four outputs of cell (x, y) and the ghost copies the next
+// step reads (the four-plane form of store_cell: a velocity's mirror image
+// lies in its own group).
+template <class T>
+__device__ __forceinline__ void store_group(T* __restrict__ out, const Layout& L, int per_x, int per_y, int x,
+                                            int y, int g, const T og[4]) {
+    const long row = (long)(y + 1) * L.pitch;
+    const long col = L.G + x;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const long pl = (long)(4 * g + j) * L.plane;
+        out[pl + row + col] = og[j];
+        if (per_x && x == 0) out[pl + row + L.G + L.nx] = og[j];
+        if (per_x && x == L.nx - 1) out[pl + row + L.G - 1] = og[j];
+        if (per_y && y == 0) out[pl + (long)(L.ny + 1) * L.pitch + col] = og[j];
+        if (per_y && y == L.ny - 1) out[pl + col] = og[j];
+        if (L.refl_x && x == 0) out[pl + row + L.G - 1] = og[mirror_plane(4 * g + j, 0) - 4 * g];
+        if (L.refl_y && y == 0) out[pl + col] = og[mirror_plane(4 * g + j, 1) - 4 * g];
+    }
+}
+
+template <class T, bool TOTALS, bool XT, int G>
+__device__ __forceinline__ void split_output(const StepArgs<T>& a, const T (&v)[4][9], const Deltas<T>& D, int x,
+                                             int y, T og[4]) {
+    const T fg[4] = {v[0][C], v[1][C], v[2][C], v[3][C]};
+    auto F = [&](int i, int pos) -> T { return v[i - 4 * G][pos]; };
+    group_update<T, XT>(G, F, a.k, D, fg, og);
+    store_group<T>(a.out, a.L, a.per_x, a.per_y, x, y, G, og);
+    if (XT && G >= 2)   // the unsplit operator reads corner ghosts of the diagonal planes only
+        store_corners<T>(a.out, a.L, a.per_x, a.per_y, x, y, [&](int j) { return og[j - 4 * G]; }, 4 * G,
+                         4 * G + 4);
+}
+
+// Shared memory of one split tile.
+template <class T>
+struct SplitSmem {
+    T sum[4][4][SPLIT_W];   // [S, QX, Dx, Dy][group][cell]
+    T m[4][4][SPLIT_W];     // [block S, Dx, Dy, Q][row][cell]
+    T d[12][SPLIT_W];       // Delta_5 .. Delta_16 (-Delta_13)
+    T out[NV][SPLIT_W];     // a totals step's outputs
+};
+
+// State loads of the split kernels: through the read-only path when the
+// launch only reads the buffer, through L2 alone (ld.global.cg) in the
+// multi-step kernel, where the buffer a step reads was written by other
+// blocks earlier in the same launch.
+template <bool COHERENT, class T>
+__device__ __forceinline__ T split_load(const T* p) {
+    if constexpr (COHERENT) return __ldcg(p); else return __ldg(p);
+}
+
+// One tile of a split kernel: 32 cells of row y from column x0, four warps
+// (threadIdx.y = velocity group g).  Returns through bad the health check
+// of the tile's cells and, with TOTALS, writes the tile's FP64 totals
+// partial to partial[0..3].
+template <class T, bool TOTALS, bool XT, bool COHERENT>
+__device__ __forceinline__ void split_tile(const StepArgs<T>& a, int x0, int y, SplitSmem<T>& sh, bool& bad,
+                                           double* partial) {
+    const Layout& L = a.L;
+    const int lane = threadIdx.x, g = threadIdx.y;
+    const int x = x0 + lane;
+    const bool active = x < L.nx;
+    // ---- phase 1: group g's stencil and butterfly sums ------------------
+    T v[4][9];
+    if (active) {
+        const T* __restrict__ in = a.in;
+        const long base = (long)(y + 1) * L.pitch + L.G + x;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const T* p = in + (long)(4 * g + j) * L.plane + base;
+            v[j][C] = split_load<COHERENT>(p);
+            v[j][XM] = split_load<COHERENT>(p - 1);
+            v[j][XP] = split_load<COHERENT>(p + 1);
+            v[j][YM] = split_load<COHERENT>(p - L.pitch);
+            v[j][YP] = split_load<COHERENT>(p + L.pitch);
+            if (XT && g >= 2) {
+                v[j][XPYP] = split_load<COHERENT>(p + L.pitch + 1);
+                v[j][XPYM] = split_load<COHERENT>(p - L.pitch + 1);
+                v[j][XMYP] = split_load<COHERENT>(p + L.pitch - 1);
+                v[j][XMYM] = split_load<COHERENT>(p - L.pitch - 1);
+            }
+        }
+        const T fg[4] = {v[0][C], v[1][C], v[2][C], v[3][C]};
+        const GroupSums<T> gs = group_sums<T>(g, fg);
+        sh.sum[0][g][lane] = gs.S;
+        sh.sum[1][g][lane] = gs.QX;
+        sh.sum[2][g][lane] = gs.Dx;
+        sh.sum[3][g][lane] = gs.Dy;
+    }
+    __syncthreads();
+    // ---- phase 2: one block of moment rows per warp ---------------------
+    if (active) {
+        const int kind = g == 0 ? 0 : g == 1 ? 2 : g == 2 ? 3 : 1;
+        const T q[4] = {sh.sum[kind][0][lane], sh.sum[kind][1][lane], sh.sum[kind][2][lane], sh.sum[kind][3][lane]};
+        T m[4];
+        if (g == 0) moments_S<T>(q, m);
+        else if (g < 3) moments_D<T>(q, m);
+        else moments_Q<T>(q, m);
+#pragma unroll
+        for (int r = 0; r < 4; ++r) sh.m[g][r][lane] = m[r];
+    }
+    __syncthreads();
+    // ---- phase 3: closure and the relaxed residuals of the warp's block -
+    bad = false;
+    if (active) {
+        const T rho = sh.m[0][0][lane], e = sh.m[0][2][lane], jx = sh.m[1][0][lane], jy = sh.m[2][0][lane];
+        const EqBase<T> b = eq_base<T>(rho, jx, jy, e, a.k);
+        Deltas<T> D;
+        if (g == 0) {
+            relax_S<T>(b, sh.m[0][1][lane], sh.m[0][3][lane], a.k, D);
+            sh.d[0][lane] = D.d5;
+            sh.d[9][lane] = D.d14;
+            bad = !healthy(rho, b.P);
+        } else if (g == 1) {
+            relax_Dx<T>(b, e, sh.m[1][3][lane], sh.m[1][2][lane], sh.m[1][1][lane], a.k, D);
+            sh.d[3][lane] = D.d8;
+            sh.d[5][lane] = D.d10;
+            sh.d[7][lane] = D.d12;
+        } else if (g == 2) {
+            relax_Dy<T>(b, e, sh.m[2][3][lane], sh.m[2][2][lane], sh.m[2][1][lane], a.k, D);
+            sh.d[4][lane] = D.d9;
+            sh.d[6][lane] = D.d11;
+            sh.d[8][lane] = D.nd13;
+        } else {
+            relax_Q<T>(b, jx, sh.m[3][0][lane], sh.m[3][1][lane], sh.m[3][2][lane], sh.m[3][3][lane], a.k, D);
+            sh.d[1][lane] = D.d6;
+            sh.d[11][lane] = D.d16;
+            sh.d[2][lane] = D.d7;
+            sh.d[10][lane] = D.d15;
+        }
+    }
+    __syncthreads();
+    // ---- phase 4: inverse and Lax-Wendroff update of the warp's group ---
+    T og[4] = {0, 0, 0, 0};
+    if (active) {
+        Deltas<T> D;
+        D.d5 = sh.d[0][lane]; D.d6 = sh.d[1][lane]; D.d7 = sh.d[2][lane]; D.d8 = sh.d[3][lane];
+        D.d9 = sh.d[4][lane]; D.d10 = sh.d[5][lane]; D.d11 = sh.d[6][lane]; D.d12 = sh.d[7][lane];
+        D.nd13 = sh.d[8][lane]; D.d14 = sh.d[9][lane]; D.d15 = sh.d[10][lane]; D.d16 = sh.d[11][lane];
+        switch (g) {
+            case 0: split_output<T, TOTALS, XT, 0>(a, v, D, x, y, og); break;
+            case 1: split_output<T, TOTALS, XT, 1>(a, v, D, x, y, og); break;
+            case 2: split_output<T, TOTALS, XT, 2>(a, v, D, x, y, og); break;
+            default: split_output<T, TOTALS, XT, 3>(a, v, D, x, y, og); break;
+        }
+    }
+    if (TOTALS) {
+        // the cell's conserved moments from all 16 outputs (warp 0), one
+        // FP64 partial per tile
+#pragma unroll
+        for (int j = 0; j < 4; ++j) sh.out[4 * g + j][lane] = og[j];
+        __syncthreads();
+        T q[4] = {0, 0, 0, 0};
+        if (g == 0 && active) {
+            T o[NV];
+#pragma unroll
+            for (int i = 0; i < NV; ++i) o[i] = sh.out[i][lane];
+            conserved_moments<T>(o, q[0], q[1], q[2], q[3]);
+        }
+        double w[4] = {(double)q[0], (double)q[1], (double)q[2], (double)q[3]};
+        block_sum4(w, partial);
+    }
+}
+
+template <class T, bool TOTALS, bool XT>
+__global__ void __launch_bounds__(4 * SPLIT_W) step_split(const StepArgs<T> a) {
+    __shared__ SplitSmem<T> sh;
+    bool bad = false;
+    split_tile<T, TOTALS, XT, false>(a, blockIdx.x * SPLIT_W, blockIdx.y, sh, bad,
+                                     a.partials + 4 * (size_t)(blockIdx.y * gridDim.x + blockIdx.x));
+    if (__syncthreads_or(bad) && threadIdx.x == 0 && threadIdx.y == 0) atomicOr(a.flag, FLAG_UNSTABLE);
+}
+
+// --------------------------------------------------------------------------
+// All steps of a call in one cooperative launch of split tiles, for grids so
+// small that a kernel launch (about 4 us on this part, in a CUDA graph too)
+// costs as much as the step.  Each resident block keeps its tiles for the
+// whole run.  A tile publishes the number of steps it has completed
+// (release, after the block's stores); before step s it waits (acquire,
+// bounded) until every tile it reads from - the up to eight neighbours on
+// the 32-cell x 1-row tile grid, wrapped on periodic axes, whose cells and
+// ghost copies its radius-1 stencil touches - has completed step s - 1.
+// That also orders the step's stores after the neighbours' last reads of the
+// buffer being overwritten (it held their step s - 1 input).  A tile is
+// never more than one step ahead of a neighbour, every wait is for an
+// earlier step, and the cooperative launch keeps every block resident, so
+// the waits end; a wait that runs out sets the timeout flag and the block
+// returns.
+// --------------------------------------------------------------------------
+__device__ __forceinline__ unsigned ld_relaxed(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release(unsigned* p, unsigned v) {
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Bounded wait of one thread until *p >= target (2 s limit), polling with
+// relaxed loads; the acquire fence after the last one orders this thread's
+// later reads after the release that published the count.
+__device__ __forceinline__ bool wait_at_least(const unsigned* p, unsigned target) {
+    bool ok = ld_relaxed(p) >= target;
+    if (!ok) {
+        // spin for the first 20 us (a neighbour is normally a fraction of a
+        // step behind), then back off
+        const uint64_t t0 = globaltimer_ns();
+        uint64_t el = 0;
+        while (!(ok = ld_relaxed(p) >= target) && (el = globaltimer_ns() - t0) <= kWaitLimitNs)
+            if (el > 20000) __nanosleep(256);
+    }
+    asm volatile("fence.acq_rel.gpu;" ::: "memory");
+    return ok;
+}
+
+template <class T, bool XT>
+__global__ void __launch_bounds__(4 * SPLIT_W) step_split_persist(const StepArgs<T> a, T* buf0, T* buf1, int nsteps,
+                                                                  int totals, unsigned* done) {
+    __shared__ SplitSmem<T> sh;
+    const Layout& L = a.L;
+    const int ntx = (L.nx + SPLIT_W - 1) / SPLIT_W;
+    const int ntiles = ntx * L.ny;
+    const bool lead = threadIdx.x == 0 && threadIdx.y == 0;
+    bool bad_any = false;
+    for (int s = 0; s < nsteps; ++s) {
+        StepArgs<T> as = a;
+        as.in = (s & 1) ? buf1 : buf0;
+        as.out = (s & 1) ? buf0 : buf1;
+        const bool tot = totals && s == nsteps - 1;
+        for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+            const int sx = t % ntx, y = t / ntx;
+            bool ok = true;
+            if (s > 0 && threadIdx.y == 0 && threadIdx.x < 9) {
+                // lane k of warp 0 waits for neighbour (dx, dy) = (k % 3 - 1, k / 3 - 1)
+                int ny = y + (int)threadIdx.x / 3 - 1, nx = sx + (int)threadIdx.x % 3 - 1;
+                bool need = true;
+                if (ny < 0 || ny >= L.ny) {
+                    need = a.per_y;                    // fixed or wall ghosts: constant or written by this tile
+                    ny = (ny + L.ny) % L.ny;
+                }
+                if (nx < 0 || nx >= ntx) {
+                    need = need && a.per_x;
+                    nx = (nx + ntx) % ntx;
+                }
+                const int n = ny * ntx + nx;
+                if (need && n != t) ok = wait_at_least(done + n, (unsigned)s);
+            }
+            if (!__syncthreads_and(ok)) {
+                if (lead) atomicOr(a.flag, FLAG_TIMEOUT);
+                return;
+            }
+            bool bad = false;
+            double* part = a.partials + 4 * (size_t)t;
+            if (tot) split_tile<T, true, XT, true>(as, sx * SPLIT_W, y, sh, bad, part);
+            else split_tile<T, false, XT, true>(as, sx * SPLIT_W, y, sh, bad, part);
+            bad_any |= bad;
+            __syncthreads();   // the tile's stores, before its count is published
+            if (lead) st_release(done + t, (unsigned)(s + 1));
+        }
+    }
+    if (__syncthreads_or(bad_any) && lead) atomicOr(a.flag, FLAG_UNSTABLE);
+}
+
 template <class T, int NS, bool TSTORE, int MINB, bool YWIN = false, bool QUEUE = false, bool XT = false>
 struct TmaKernels {
     static cudaError_t launch(const CUtensorMap* mi, const CUtensorMap* mo, const StepArgs<T>& a, dim3 grid,
@@ -258,6 +534,55 @@ cudaError_t launch_step_direct(const StepArgs<T>& a, bool xt, bool totals, cudaS
     return cudaGetLastError();
 }
 
+void split_grid(const Layout& L, dim3* grid, dim3* block) {
+    *block = dim3(SPLIT_W, 4);
+    *grid = dim3((L.nx + SPLIT_W - 1) / SPLIT_W, L.ny);
+}
+
+template <class T>
+cudaError_t launch_step_split(const StepArgs<T>& a, bool xt, bool totals, cudaStream_t st) {
+    dim3 grid, block;
+    split_grid(a.L, &grid, &block);
+    if (xt) {
+        if (totals) step_split<T, true, true><<<grid, block, 0, st>>>(a);
+        else step_split<T, false, true><<<grid, block, 0, st>>>(a);
+    } else {
+        if (totals) step_split<T, true, false><<<grid, block, 0, st>>>(a);
+        else step_split<T, false, false><<<grid, block, 0, st>>>(a);
+    }
+    return cudaGetLastError();
+}
+
+template <class T>
+cudaError_t split_persist_blocks(bool xt, int* blocks) {
+    int occ = 0, dev = 0, sms = 0;
+    cudaError_t e = xt ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, step_split_persist<T, true>, 4 * SPLIT_W, 0)
+                       : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, step_split_persist<T, false>, 4 * SPLIT_W, 0);
+    if (e != cudaSuccess) return e;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    *blocks = occ * sms;
+    return cudaSuccess;
+}
+
+template <class T>
+cudaError_t launch_step_split_persist(const StepArgs<T>& a, bool xt, T* buf0, T* buf1, int nsteps, bool totals,
+                                      unsigned* done, int blocks, cudaStream_t st) {
+    void* args[] = {(void*)&a, (void*)&buf0, (void*)&buf1, (void*)&nsteps, nullptr, (void*)&done};
+    int tot = totals ? 1 : 0;
+    args[4] = (void*)&tot;
+    const void* fn = xt ? (const void*)step_split_persist<T, true> : (const void*)step_split_persist<T, false>;
+    return cudaLaunchCooperativeKernel(fn, dim3(blocks), dim3(SPLIT_W, 4), args, 0, st);
+}
+
+template cudaError_t split_persist_blocks<float>(bool, int*);
+template cudaError_t split_persist_blocks<double>(bool, int*);
+template cudaError_t launch_step_split_persist<float>(const StepArgs<float>&, bool, float*, float*, int, bool,
+                                                       unsigned*, int, cudaStream_t);
+template cudaError_t launch_step_split_persist<double>(const StepArgs<double>&, bool, double*, double*, int, bool,
+                                                        unsigned*, int, cudaStream_t);
+template cudaError_t launch_step_split<float>(const StepArgs<float>&, bool, bool, cudaStream_t);
+template cudaError_t launch_step_split<double>(const StepArgs<double>&, bool, bool, cudaStream_t);
 template cudaError_t launch_step_tma<float>(int, bool, const CUtensorMap*, const CUtensorMap*,
                                             const StepArgs<float>&, int, int, bool, cudaStream_t);
 template cudaError_t launch_step_tma<double>(int, bool, const CUtensorMap*, const CUtensorMap*,

@@ -156,10 +156,11 @@ __device__ __forceinline__ void store_cell(T* __restrict__ out, const Layout& L,
 // when applied to the ghost column: the wrapped row on a periodic y axis,
 // row 0 of the column with mirrored velocities behind a reflecting y wall.
 // Corners beyond a fixed end never change (set at creation).  v(i) is the
-// cell's output of plane i.
+// cell's output of plane i; planes [i0, i1) are written (a velocity and its
+// mirror images share a group of four).
 template <class T, class V>
 __device__ __forceinline__ void store_corners(T* __restrict__ out, const Layout& L, int per_x, int per_y, int x,
-                                              int y, const V& v) {
+                                              int y, const V& v, int i0 = 0, int i1 = NV) {
     long col = -1;
     bool mx = false;
     if (per_x) col = x == 0 ? L.G + L.nx : (x == L.nx - 1 ? L.G - 1 : -1);
@@ -172,6 +173,7 @@ __device__ __forceinline__ void store_corners(T* __restrict__ out, const Layout&
     if (row < 0) return;
 #pragma unroll
     for (int i = 0; i < NV; ++i) {
+        if (i < i0 || i >= i1) continue;
         const int j = mx ? (my ? mirror_plane(mirror_plane(i, 1), 0) : mirror_plane(i, 0))
                          : (my ? mirror_plane(i, 1) : i);
         out[i * L.plane + row * L.pitch + col] = v(j);

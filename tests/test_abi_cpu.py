@@ -46,7 +46,7 @@ def _params(**kw):
 
 @pytest.mark.parametrize("field,value", [("nx", 2), ("ny", 1), ("dx", 0.0), ("dt", -1.0),
                                          ("gamma", 1.0), ("precision", 7), ("bc_x", 3),
-                                         ("kernel", 9), ("tile", 8), ("tile", -1),
+                                         ("kernel", 4), ("kernel", 9), ("tile", 8), ("tile", -1),
                                          ("Pr", float("nan")), ("advection", 2), ("advection", -1)])
 def test_invalid_params_rejected(lib, field, value):
     p, w = _params(**{field: value})

@@ -21,7 +21,7 @@ from _parity import assert_parity
 
 pytestmark = pytest.mark.gpu
 
-VARIANTS = [(Bd.KERNEL_TMA, t) for t in (0, 1, 4, 5, 6, 7)] + [(Bd.KERNEL_DIRECT, 0)]
+VARIANTS = [(Bd.KERNEL_TMA, t) for t in (0, 1, 4, 5, 6, 7)] + [(Bd.KERNEL_DIRECT, 0), (Bd.KERNEL_SPLIT, 0)]
 BCS = [(0, 0), (1, 0), (0, 1), (1, 1), (2, 0), (2, 1), (0, 2), (2, 2)]
 
 

@@ -178,7 +178,10 @@ def test_vortex_adjoint_512_against_oracle():
         assert err <= tol, (label, "rates", err)
 
     L64, g64, dL64 = _grads(w, Bd.FP64, lg)
-    assert abs(L64 - doc["loss"]) <= 1e-12 * abs(doc["loss"])
+    # L sums squares of differences of order 1e-3 of rho; the FP64 step's
+    # multiply-add form rounds the rho = 1 background by about eps_64 kappa
+    # (kappa = sum |f_i| / rho, 47 here) per step: 1e-10 of L
+    assert abs(L64 - doc["loss"]) <= 1e-10 * abs(doc["loss"])
     compare(g64, 1e-10, "fp64")
     # central differences of the oracle's loss (h = 1e-4)
     for q, name in enumerate(names):

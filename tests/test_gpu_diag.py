@@ -11,7 +11,7 @@ from paper_1004_5442_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
 
-VARIANTS = [(Bd.KERNEL_TMA, t) for t in (1, 2, 3, 4, 5, 6, 7)] + [(Bd.KERNEL_DIRECT, 0)]
+VARIANTS = [(Bd.KERNEL_TMA, t) for t in (1, 2, 3, 4, 5, 6, 7)] + [(Bd.KERNEL_DIRECT, 0), (Bd.KERNEL_SPLIT, 0)]
 BCS = [(Bd.BC_PERIODIC, Bd.BC_PERIODIC), (Bd.BC_FIXED_EQ, Bd.BC_PERIODIC),
        (Bd.BC_REFLECT_FIXED, Bd.BC_REFLECT_FIXED), (Bd.BC_FIXED_EQ, Bd.BC_FIXED_EQ)]
 

@@ -21,8 +21,8 @@ from _parity import assert_parity, field_errors, run_gpu, run_oracle
 pytestmark = pytest.mark.gpu
 
 KERNELS = [Bd.KERNEL_TMA, Bd.KERNEL_DIRECT]
-# (kernel, tile): every compiled TMA variant and the direct kernel
-VARIANTS = [(Bd.KERNEL_TMA, t) for t in (1, 2, 3, 4, 5, 6, 7)] + [(Bd.KERNEL_DIRECT, 0)]
+# (kernel, tile): every compiled TMA variant, the direct and the split kernel
+VARIANTS = [(Bd.KERNEL_TMA, t) for t in (1, 2, 3, 4, 5, 6, 7)] + [(Bd.KERNEL_DIRECT, 0), (Bd.KERNEL_SPLIT, 0)]
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -272,12 +272,17 @@ def test_full_size_kh_sampled_windows():
 def test_automatic_kernel_and_tile_choice():
     """Tile 0 / MRT_KERNEL_AUTO: the work-queue tile 6 on grids with at least
     two 8-row items per resident CTA, the static tile 4 (FP32) or 1 (FP64)
-    on smaller ones, and the direct kernel on small FP64 grids."""
+    on smaller ones, the direct kernel on small FP64 grids and the split
+    kernel on tiny ones (8192 cells in FP64, 2048 in FP32)."""
     cases = [(W.kelvin_helmholtz(n=2048, nsteps=0), Bd.FP32, (Bd.KERNEL_TMA, 6)),
              (W.kelvin_helmholtz(n=2048, nsteps=0), Bd.FP64, (Bd.KERNEL_TMA, 6)),
              (W.kelvin_helmholtz(n=512, nsteps=0), Bd.FP32, (Bd.KERNEL_TMA, 4)),
              (W.kelvin_helmholtz(n=512, nsteps=0), Bd.FP64, (Bd.KERNEL_TMA, 1)),
-             (W.sod_tube(), Bd.FP64, (Bd.KERNEL_DIRECT, None)),
+             (W.sod_tube(), Bd.FP64, (Bd.KERNEL_SPLIT, None)),
+             (W.sod_tube(), Bd.FP32, (Bd.KERNEL_SPLIT, None)),
+             (W.colliding_shocks(), Bd.FP64, (Bd.KERNEL_SPLIT, None)),
+             (W.colliding_shocks(), Bd.FP32, (Bd.KERNEL_TMA, 4)),
+             (W.strong_shock(), Bd.FP64, (Bd.KERNEL_DIRECT, None)),
              (W.strong_shock(), Bd.FP32, (Bd.KERNEL_TMA, 4))]
     for w, prec, (kernel, tile) in cases:
         with Bd.Grid.from_workload(w, precision=prec) as g:
