@@ -759,6 +759,7 @@ def fma_only(args):
     """The device's multiply-add throughput, FP64 and FP32, at 2, 4 and 8
     blocks of 256 threads per SM, three launches each (CUDA events inside
     mrt_debug_fma_rate)."""
+    import torch
     from paper_1004_5442_gb300 import build as B
     B.build()
     from paper_1004_5442_gb300 import binding as Bd
@@ -767,6 +768,19 @@ def fma_only(args):
         for bps in (2, 4, 8):
             runs = [Bd.fma_rate(prec, blocks_per_sm=bps) for _ in range(3)]
             out[f"{name}_blocks_per_sm_{bps}"] = {"tflops": [r / 1e12 for r, _ in runs], "ms": [m for _, m in runs]}
+    # FP64 with few warps: one block per SM of 1 or 4 warps, 32 down to 1
+    # active lanes; clocks per warp multiply-add per SM at the observed rate
+    clk = 2.07e9
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    for warps in (1, 4):
+        for lanes in (32, 8, 1):
+            r, ms = Bd.fma_rate(Bd.FP64, iters=1250, blocks_per_sm=1, threads_per_block=32 * warps, active_lanes=lanes)
+            warp_fma = r / 2 / lanes                     # warp multiply-adds per second
+            out[f"fp64_warps_per_sm_{warps}_lanes_{lanes}"] = {"tflops": r / 1e12, "ms": ms,
+                                                               "clocks_per_warp_fma_per_sm": clk * sms / warp_fma}
+    for blocks in (1, 152, 608):
+        a, b = Bd.launch_period(2000, blocks, 128)
+        out[f"launch_period_{blocks}_blocks_of_128"] = {"us_stream": a, "us_graph_of_two": b}
     print(json.dumps(out), flush=True)
 
 

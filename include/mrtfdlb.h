@@ -355,15 +355,26 @@ mrt_status mrt_debug_wait_timeout(mrt_grid *g);
 /* mrt_debug_fma_rate: fused multiply-add throughput of the current device in
  * FP32 or FP64 (precision = mrt_precision), the arithmetic roof of the
  * steps that are bound by the FP64 pipe.  One launch of blocks_per_sm (1..8)
- * blocks of 256 threads per SM, each thread running 8 independent chains
- * a <- a * 1/2 + 1/2 for 16 * iters multiply-adds each, is timed with CUDA
+ * blocks of threads_per_block threads (a multiple of 32, at most 1024, at
+ * most 2048 per SM) per SM, in which the first active_lanes (1..32) lanes of
+ * every warp run 8 independent chains a <- a * 1/2 + 1/2 of 16 * iters
+ * multiply-adds each (the other lanes return at once), is timed with CUDA
  * events after one untimed launch of the same shape; *flops_per_s =
  * 2 * multiply-adds / time, *ms (may be NULL) the timed launch's duration.
  * Allocates a small output buffer (stream-ordered) and synchronises.
- * Errors: MRT_EINVAL (precision, iters < 1, blocks_per_sm out of range,
- * NULL flops_per_s), MRT_ECUDA. */
-mrt_status mrt_debug_fma_rate(int precision, long iters, int blocks_per_sm, double *flops_per_s,
-                              double *ms);
+ * Errors: MRT_EINVAL (an argument out of range, NULL flops_per_s),
+ * MRT_ECUDA.
+ *
+ * mrt_debug_launch_period: the time per launch of a kernel that does
+ * nothing, with blocks x threads threads, over nlaunches (even, >= 2)
+ * launches in a row on one stream (*us_stream) and as nlaunches/2 replays
+ * of a two-launch CUDA graph (*us_graph), CUDA events after one untimed
+ * launch; the floor under any step of a small grid.  Synchronises.
+ * Errors: MRT_EINVAL, MRT_ECUDA. */
+mrt_status mrt_debug_fma_rate(int precision, long iters, int blocks_per_sm, int threads_per_block,
+                              int active_lanes, double *flops_per_s, double *ms);
+mrt_status mrt_debug_launch_period(int nlaunches, int blocks, int threads, double *us_stream,
+                                   double *us_graph);
 
 /* Release every device resource of the grid (synchronises its streams). */
 void mrt_destroy(mrt_grid *g);

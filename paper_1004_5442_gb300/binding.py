@@ -29,7 +29,7 @@ EXPORTED = ["mrt_create", "mrt_step", "mrt_get_macro", "mrt_conserved_totals", "
             "mrt_adjoint_backward", "mrt_adjoint_step", "mrt_batch_create", "mrt_batch_step",
             "mrt_batch_tune", "mrt_batch_grid", "mrt_batch_info", "mrt_batch_sync", "mrt_batch_stream",
             "mrt_batch_destroy", "mrt_debug_padding", "mrt_debug_wait_timeout", "mrt_conserved_totals_async",
-            "mrt_totals_wait", "mrt_save", "mrt_load", "mrt_debug_fma_rate"]
+            "mrt_totals_wait", "mrt_save", "mrt_load", "mrt_debug_fma_rate", "mrt_debug_launch_period"]
 
 
 class MrtError(RuntimeError):
@@ -96,7 +96,8 @@ def load(path: str = LIB_PATH):
     L.mrt_totals_wait.argtypes = [vp, ctypes.c_long]
     L.mrt_save.argtypes = [vp, ctypes.c_char_p]
     L.mrt_load.argtypes = [vp, ctypes.c_char_p]
-    L.mrt_debug_fma_rate.argtypes = [ip, ctypes.c_long, ip, dp, dp]
+    L.mrt_debug_fma_rate.argtypes = [ip, ctypes.c_long, ip, ip, ip, dp, dp]
+    L.mrt_debug_launch_period.argtypes = [ip, ip, ip, dp, dp]
     L.mrt_batch_destroy.argtypes = [vp]
     L.mrt_batch_destroy.restype = None
     for name in ("mrt_create", "mrt_step", "mrt_get_macro", "mrt_conserved_totals", "mrt_get_f",
@@ -104,7 +105,7 @@ def load(path: str = LIB_PATH):
                  "mrt_adjoint_record", "mrt_adjoint_backward", "mrt_adjoint_step", "mrt_batch_create",
                  "mrt_batch_step", "mrt_batch_tune", "mrt_batch_grid", "mrt_batch_info", "mrt_batch_sync",
                  "mrt_batch_stream", "mrt_debug_padding", "mrt_debug_wait_timeout", "mrt_conserved_totals_async",
-                 "mrt_totals_wait", "mrt_save", "mrt_load", "mrt_debug_fma_rate"):
+                 "mrt_totals_wait", "mrt_save", "mrt_load", "mrt_debug_fma_rate", "mrt_debug_launch_period"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -154,15 +155,26 @@ def conserved_totals_static(f, precision: int, nx: int, ny: int, dx: float, out,
                                              float(dx), ctypes.c_void_p(_ptr(out)), ctypes.c_void_p(stream)))
 
 
-def fma_rate(precision: int, iters: int | None = None, blocks_per_sm: int = 4):
+def fma_rate(precision: int, iters: int | None = None, blocks_per_sm: int = 4, threads_per_block: int = 256,
+             active_lanes: int = 32):
     """(flop/s, ms) of the device's fused multiply-add throughput in FP32 or
-    FP64 (mrt_debug_fma_rate); iters defaults to about 0.1 s of work."""
+    FP64 (mrt_debug_fma_rate); iters defaults to about 0.1 s of work at
+    full occupancy."""
     if iters is None:
         iters = 3000 if precision == FP64 else 200000
     rate, ms = ctypes.c_double(), ctypes.c_double()
-    check(load().mrt_debug_fma_rate(int(precision), int(iters), int(blocks_per_sm), ctypes.byref(rate),
-                                    ctypes.byref(ms)))
+    check(load().mrt_debug_fma_rate(int(precision), int(iters), int(blocks_per_sm), int(threads_per_block),
+                                    int(active_lanes), ctypes.byref(rate), ctypes.byref(ms)))
     return rate.value, ms.value
+
+
+def launch_period(nlaunches: int = 2000, blocks: int = 1, threads: int = 128):
+    """(us per launch on a stream, us per launch in two-launch CUDA graphs)
+    of a kernel that does nothing (mrt_debug_launch_period)."""
+    a, b = ctypes.c_double(), ctypes.c_double()
+    check(load().mrt_debug_launch_period(int(nlaunches), int(blocks), int(threads), ctypes.byref(a),
+                                         ctypes.byref(b)))
+    return a.value, b.value
 
 
 class Grid:

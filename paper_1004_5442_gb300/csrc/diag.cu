@@ -54,11 +54,12 @@ __global__ void wait_timeout_kernel(unsigned* flag) {
 // overflow path is timed).  kChains chains give each warp enough
 // independent instructions to cover the pipe latency; the sum is stored only
 // if it equals a value it cannot reach, which keeps every chain live.
-constexpr int kFmaThreads = 256;
+constexpr int kFmaMaxThreads = 1024;
 constexpr int kFmaChains = 8;
 constexpr int kFmaUnroll = 16;
 template <class T>
-__global__ void __launch_bounds__(kFmaThreads) fma_kernel(long iters, T b, T c, T* out) {
+__global__ void __launch_bounds__(kFmaMaxThreads) fma_kernel(long iters, int active_lanes, T b, T c, T* out) {
+    if ((int)(threadIdx.x & 31) >= active_lanes) return;
     T a[kFmaChains];
 #pragma unroll
     for (int k = 0; k < kFmaChains; ++k) a[k] = (T)(threadIdx.x + 1) * (T)(k + 1) * (T)1e-3;
@@ -72,17 +73,24 @@ __global__ void __launch_bounds__(kFmaThreads) fma_kernel(long iters, T b, T c, 
     T s = 0;
 #pragma unroll
     for (int k = 0; k < kFmaChains; ++k) s += a[k];
-    if (s == (T)-1) out[blockIdx.x * kFmaThreads + threadIdx.x] = s;
+    if (s == (T)-1) out[blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
+// A kernel that does nothing but exist, for the launch period.
+__global__ void empty_kernel(int* sink) {
+    if (sink && threadIdx.x == 1u << 30) *sink = 0;
 }
 
 }  // namespace
 
-extern "C" mrt_status mrt_debug_fma_rate(int precision, long iters, int blocks_per_sm, double* flops_per_s,
-                                         double* ms) {
-    if (!flops_per_s || iters < 1 || blocks_per_sm < 1 || blocks_per_sm > 8 ||
-        (precision != MRT_FP32 && precision != MRT_FP64))
+extern "C" mrt_status mrt_debug_fma_rate(int precision, long iters, int blocks_per_sm, int threads_per_block,
+                                         int active_lanes, double* flops_per_s, double* ms) {
+    if (!flops_per_s || iters < 1 || blocks_per_sm < 1 || blocks_per_sm > 8 || threads_per_block < 32 ||
+        threads_per_block > kFmaMaxThreads || threads_per_block % 32 || blocks_per_sm * threads_per_block > 2048 ||
+        active_lanes < 1 || active_lanes > 32 || (precision != MRT_FP32 && precision != MRT_FP64))
         return mrt_fail(MRT_EINVAL, "need precision MRT_FP32 or MRT_FP64, iters >= 1, 1 <= blocks_per_sm <= 8, "
-                                    "flops_per_s");
+                                    "threads_per_block a multiple of 32 in 32..1024 with at most 2048 threads per "
+                                    "SM, 1 <= active_lanes <= 32, flops_per_s");
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -93,15 +101,17 @@ extern "C" mrt_status mrt_debug_fma_rate(int precision, long iters, int blocks_p
     cudaError_t e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreate(&e0);
     if (e == cudaSuccess) e = cudaEventCreate(&e1);
-    if (e == cudaSuccess) e = cudaMallocAsync(&out, (size_t)blocks * kFmaThreads * 8, st);
+    if (e == cudaSuccess) e = cudaMallocAsync(&out, (size_t)blocks * threads_per_block * 8, st);
     float el = 0.f;
     if (e == cudaSuccess) {
         for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {  // the first launch warms up
             e = cudaEventRecord(e0, st);
             if (precision == MRT_FP64)
-                fma_kernel<double><<<blocks, kFmaThreads, 0, st>>>(iters, 0.5, 0.5, static_cast<double*>(out));
+                fma_kernel<double><<<blocks, threads_per_block, 0, st>>>(iters, active_lanes, 0.5, 0.5,
+                                                                         static_cast<double*>(out));
             else
-                fma_kernel<float><<<blocks, kFmaThreads, 0, st>>>(iters, 0.5f, 0.5f, static_cast<float*>(out));
+                fma_kernel<float><<<blocks, threads_per_block, 0, st>>>(iters, active_lanes, 0.5f, 0.5f,
+                                                                        static_cast<float*>(out));
             if (e == cudaSuccess) e = cudaGetLastError();
             if (e == cudaSuccess) e = cudaEventRecord(e1, st);
         }
@@ -114,9 +124,60 @@ extern "C" mrt_status mrt_debug_fma_rate(int precision, long iters, int blocks_p
     if (e0) cudaEventDestroy(e0);
     if (st) cudaStreamDestroy(st);
     if (e != cudaSuccess) return mrt_fail(MRT_ECUDA, "fma rate: %s", cudaGetErrorString(e));
-    const double flops = 2.0 * kFmaChains * kFmaUnroll * (double)iters * kFmaThreads * blocks;
+    const double warps = (double)blocks * (threads_per_block / 32);
+    const double flops = 2.0 * kFmaChains * kFmaUnroll * (double)iters * warps * active_lanes;
     *flops_per_s = flops / (el * 1e-3);
     if (ms) *ms = el;
+    return MRT_OK;
+}
+
+extern "C" mrt_status mrt_debug_launch_period(int nlaunches, int blocks, int threads, double* us_stream,
+                                              double* us_graph) {
+    if (nlaunches < 2 || nlaunches % 2 || blocks < 1 || threads < 1 || threads > 1024 || !us_stream || !us_graph)
+        return mrt_fail(MRT_EINVAL, "need an even nlaunches >= 2, blocks >= 1, 1 <= threads <= 1024, outputs");
+    cudaStream_t st = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    float a = 0.f, b = 0.f;
+    cudaError_t e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    if (e == cudaSuccess) {
+        empty_kernel<<<blocks, threads, 0, st>>>(nullptr);
+        e = cudaEventRecord(e0, st);
+        for (int i = 0; i < nlaunches && e == cudaSuccess; ++i) {
+            empty_kernel<<<blocks, threads, 0, st>>>(nullptr);
+            e = cudaGetLastError();
+        }
+        if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&a, e0, e1);
+    }
+    if (e == cudaSuccess) e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        empty_kernel<<<blocks, threads, 0, st>>>(nullptr);
+        empty_kernel<<<blocks, threads, 0, st>>>(nullptr);
+        const cudaError_t ec = cudaStreamEndCapture(st, &graph);
+        e = cudaGetLastError();
+        if (e == cudaSuccess) e = ec;
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+    if (e == cudaSuccess) e = cudaGraphLaunch(exec, st);
+    if (e == cudaSuccess) e = cudaEventRecord(e0, st);
+    for (int i = 0; i < nlaunches / 2 && e == cudaSuccess; ++i) e = cudaGraphLaunch(exec, st);
+    if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&b, e0, e1);
+    if (st) cudaStreamSynchronize(st);
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    if (e1) cudaEventDestroy(e1);
+    if (e0) cudaEventDestroy(e0);
+    if (st) cudaStreamDestroy(st);
+    if (e != cudaSuccess) return mrt_fail(MRT_ECUDA, "launch period: %s", cudaGetErrorString(e));
+    *us_stream = 1e3 * a / nlaunches;
+    *us_graph = 1e3 * b / nlaunches;
     return MRT_OK;
 }
 

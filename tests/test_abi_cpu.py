@@ -99,11 +99,17 @@ def test_null_handles_of_later_entry_points_rejected(lib):
     assert lib.mrt_load(None, b"/nonexistent/x") == Bd.MRT_EINVAL
     assert lib.mrt_debug_padding(None, ctypes.byref(n)) == Bd.MRT_EINVAL
     assert lib.mrt_debug_wait_timeout(None) == Bd.MRT_EINVAL
-    r = ctypes.c_double()
-    assert lib.mrt_debug_fma_rate(Bd.FP64, 100, 4, None, None) == Bd.MRT_EINVAL
-    assert lib.mrt_debug_fma_rate(7, 100, 4, ctypes.byref(r), None) == Bd.MRT_EINVAL
-    assert lib.mrt_debug_fma_rate(Bd.FP32, 0, 4, ctypes.byref(r), None) == Bd.MRT_EINVAL
-    assert lib.mrt_debug_fma_rate(Bd.FP32, 10, 9, ctypes.byref(r), None) == Bd.MRT_EINVAL
+    r, r2 = ctypes.c_double(), ctypes.c_double()
+    assert lib.mrt_debug_fma_rate(Bd.FP64, 100, 4, 256, 32, None, None) == Bd.MRT_EINVAL
+    assert lib.mrt_debug_fma_rate(7, 100, 4, 256, 32, ctypes.byref(r), None) == Bd.MRT_EINVAL
+    assert lib.mrt_debug_fma_rate(Bd.FP32, 0, 4, 256, 32, ctypes.byref(r), None) == Bd.MRT_EINVAL
+    assert lib.mrt_debug_fma_rate(Bd.FP32, 10, 9, 256, 32, ctypes.byref(r), None) == Bd.MRT_EINVAL
+    assert lib.mrt_debug_fma_rate(Bd.FP32, 10, 4, 100, 32, ctypes.byref(r), None) == Bd.MRT_EINVAL
+    assert lib.mrt_debug_fma_rate(Bd.FP32, 10, 4, 1024, 32, ctypes.byref(r), None) == Bd.MRT_EINVAL
+    assert lib.mrt_debug_fma_rate(Bd.FP32, 10, 4, 256, 0, ctypes.byref(r), None) == Bd.MRT_EINVAL
+    assert lib.mrt_debug_launch_period(3, 1, 128, ctypes.byref(r), ctypes.byref(r2)) == Bd.MRT_EINVAL
+    assert lib.mrt_debug_launch_period(10, 1, 2000, ctypes.byref(r), ctypes.byref(r2)) == Bd.MRT_EINVAL
+    assert lib.mrt_debug_launch_period(10, 1, 128, None, ctypes.byref(r2)) == Bd.MRT_EINVAL
 
 
 def test_status_strings(lib):

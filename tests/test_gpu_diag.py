@@ -79,3 +79,8 @@ def test_fma_rate_is_plausible():
     r32, ms32 = Bd.fma_rate(Bd.FP32, iters=2000)
     assert 0 < r64 < r32 <= sms * 128 * 2 * 3e9
     assert ms64 > 0 and ms32 > 0
+    # a warp with one active lane counts one lane's flops
+    r1, _ = Bd.fma_rate(Bd.FP32, iters=200, blocks_per_sm=1, threads_per_block=32, active_lanes=1)
+    assert 0 < r1 < r32
+    us_stream, us_graph = Bd.launch_period(200)
+    assert 0 < us_stream < 1000 and 0 < us_graph < 1000
