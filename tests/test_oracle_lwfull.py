@@ -93,3 +93,44 @@ def test_growth_at_the_unstable_states_remains(orc):
         assert r_full > 1.0 + 1e-4, (state, r_full)
         assert r_euler > 1.0 + 1e-4, (state, r_euler)
         assert abs(r_full - r_euler) < 0.2 * (r_euler - 1.0), (state, r_full, r_euler)
+
+
+def test_kinetic_equation_itself_grows_at_the_unstable_states(orc):
+    """Eq. 3 linearised about a uniform equilibrium, exact in space and time:
+    a Fourier mode exp(i k.x) evolves by d/dt = -i k.v + J, with J =
+    -Minv S (I - JE) M the collision Jacobian (JE = d fhat^eq / d fhat, the
+    oracle's complex-step Jacobian in its first four columns).  At the
+    four-quadrant problem's quadrants 2 and 3 it has eigenvalues with
+    positive real part at resolved wavenumbers (k dx <= 1, at the paper's
+    dt = 0.005 dx, rates per dt), where quadrant 1 has none: the growth is a
+    property of the kinetic equation at those states, which no consistent
+    time scheme removes.  Their equilibria also have negative members."""
+    vx, vy, _, M, Minv = orc.model()
+    gamma = 1.4
+    b = 2.0 / (gamma - 1.0)
+    sig = np.full(16, 0.03)
+    sig[7] = sig[8] = 0.2
+    dx_over_dt = 200.0
+
+    def max_growth(state):
+        rho, ux, uy, T = state
+        J4 = orc.feq_jacobian(rho, rho * ux, rho * uy, b * rho * T + rho * (ux * ux + uy * uy), b)
+        JE = np.zeros((16, 16))
+        JE[:, :4] = J4
+        L = -Minv @ np.diag(sig) @ (np.eye(16) - JE) @ M
+        worst = -np.inf
+        for kdx in (0.4, 0.8, 1.0):
+            k = kdx / dx_over_dt
+            for ang in np.linspace(0, 2 * np.pi, 49):
+                A = -1j * k * (np.cos(ang) * np.diag(vx) + np.sin(ang) * np.diag(vy)) + L
+                worst = max(worst, float(np.max(np.linalg.eigvals(A).real)))
+        return worst
+
+    q1 = (1.5, 0.0, 0.0, 1.0)
+    q2 = (0.5323, 1.206, 0.0, 0.3 / 0.5323)
+    q3 = (0.138, 1.206, 1.206, 0.029 / 0.138)
+    assert max_growth(q1) <= 1e-12
+    assert max_growth(q2) > 1e-6
+    assert max_growth(q3) > 1e-4
+    for state in (q2, q3):
+        assert np.min(orc.feq(*state, b)) < 0
