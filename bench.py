@@ -68,6 +68,9 @@ def parse():
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-problems", action="store_true", help="skip the tube / 2-D Riemann problem runs")
+    ap.add_argument("--problem-steps", type=int, default=0,
+                    help="run each tube / 2-D Riemann problem for at most this many steps and report timings only "
+                         "(for profiler captures; 0 = the problems' full runs with their error checks)")
     ap.add_argument("--batch-steps", type=int, default=1000, help="timed steps of the 256-instance sweep")
     ap.add_argument("--batch-count", type=int, default=256, help="instances of the sweep (first n screened draws)")
     ap.add_argument("--tile", type=int, default=0, help="TMA kernel variant (0 = library default)")
@@ -501,7 +504,7 @@ def run_ours(args):
 
     # the paper's tube and 2-D problems: throughput next to error vs exact
     if not args.no_problems:
-        line["paper_problems"] = paper_problems(Bd, W, torch, stream, peak)
+        line["paper_problems"] = paper_problems(Bd, W, torch, stream, peak, args.problem_steps)
 
     # 256 independent tube/ripple instances of uneven size, one launch per step
     if not args.no_batch:
@@ -609,15 +612,37 @@ def _shock_x(rho, dx, behind, ahead):
     return x
 
 
-def paper_problems(Bd, W, torch, stream, peak):
+def paper_problems(Bd, W, torch, stream, peak, cap=0):
     """Sod (400 x 4, FP64), strong shock (2048 x 8, FP32 and FP64), colliding
     shocks (1300 x 4, gamma 7/5, MRT and SRT rates, FP64, t = 0.13), the
     Richtmyer-Meshkov run (360 x 100, reflecting wall, t = 0.104) and the
     four-quadrant 2-D Riemann problem (500^2): cell-updates/s with the error
-    against the stored exact solutions where one exists."""
+    against the stored exact solutions where one exists.  cap > 0: at most
+    cap steps per problem, timings only."""
     with open(EXACT_PROFILES) as fh:
         exact = json.load(fh)
     out = {}
+    if cap > 0:
+        cases = [("sod_400x4", W.sod_tube(), (Bd.FP64,)), ("strong_shock_2048x8", W.strong_shock(), (Bd.FP32, Bd.FP64)),
+                 ("colliding_shocks_gamma1.4", W.colliding_shocks(gamma=1.4), (Bd.FP64,)),
+                 ("richtmyer_meshkov_360x100", W.richtmyer_meshkov(), (Bd.FP32, Bd.FP64)),
+                 ("four_quadrant_500x500", W.four_quadrant_riemann(n=500), (Bd.FP32,))]
+        for name, w, precs in cases:
+            n = min(cap, w.nsteps)
+            for prec in precs:
+                g = Bd.Grid.from_workload(w, precision=prec, stream=stream.cuda_stream)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                torch.cuda.synchronize()
+                e0.record(stream)
+                g.step(n)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                ms = e0.elapsed_time(e1)
+                out[f"{name}_{'fp64' if prec == Bd.FP64 else 'fp32'}"] = {
+                    "steps": n, "ms": ms, "us_per_step": 1e3 * ms / n, "kernel": g.info()["kernel"],
+                    "healthy": g.health() == Bd.MRT_OK}
+                g.close()
+        return out
 
     def timed(w, prec, nsteps):
         g = Bd.Grid.from_workload(w, precision=prec, stream=stream.cuda_stream)
