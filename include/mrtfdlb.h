@@ -345,9 +345,12 @@ void mrt_batch_destroy(mrt_batch *b);
  * left ghost column, right of the right one; zero from creation on): a guard
  * band that counts out-of-bounds writes.  Synchronises the grid's stream.
  * mrt_debug_wait_timeout: launches one thread that waits, with the bounded
- * wait of the TMA kernels, on a barrier nothing completes; after the wait's
- * 2 s limit the grid's timeout flag is set, so the next mrt_health returns
- * MRT_ETIMEOUT (the grid stays flagged).  Asynchronous on the grid's stream.
+ * wait of the TMA kernels, on a barrier nothing completes, and one that
+ * waits, with the bounded wait of the split kernel's multi-step launch, on
+ * a tile counter nothing raises; after the waits' 2 s limit the grid's
+ * timeout flag is set, so the next mrt_health returns MRT_ETIMEOUT (the
+ * grid stays flagged).  Allocates the counter (stream-ordered).
+ * Asynchronous on the grid's stream.
  * Errors: MRT_EINVAL (null pointers), MRT_ENOMEM, MRT_ECUDA. */
 mrt_status mrt_debug_padding(mrt_grid *g, long *nonzero);
 mrt_status mrt_debug_wait_timeout(mrt_grid *g);

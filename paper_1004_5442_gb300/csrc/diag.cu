@@ -7,10 +7,12 @@
 //    nonzero word there is an out-of-bounds write: a guard band, in place of
 //    a memory checker.
 //  * mrt_debug_wait_timeout: one thread runs the kernels' bounded mbarrier
-//    wait on a barrier that nothing completes, so the wait runs out (after
-//    its 2 s limit) and sets the timeout flag, which mrt_health reports as
-//    MRT_ETIMEOUT.  It exercises the failure path of every TMA kernel without
-//    a fault, a trap or an unbounded wait.
+//    wait on a barrier that nothing completes, another the multi-step
+//    launch's bounded wait on a tile counter that nothing raises, so both
+//    waits run out (after their 2 s limit) and set the timeout flag, which
+//    mrt_health reports as MRT_ETIMEOUT.  It exercises the failure path of
+//    every TMA kernel and of the multi-step launch without a fault, a trap
+//    or an unbounded wait.
 //  * mrt_debug_fma_rate: the device's fused multiply-add throughput in FP32
 //    or FP64, the arithmetic roof against which the FP64 step (bound by the
 //    FP64 pipe on this part) is measured.
@@ -39,13 +41,18 @@ __global__ void padding_kernel(Layout L, const T* __restrict__ f, unsigned long 
     if (c) atomicAdd(count, c);
 }
 
-__global__ void wait_timeout_kernel(unsigned* flag) {
+__global__ void wait_timeout_kernel(unsigned* flag, const unsigned* never) {
     __shared__ __align__(8) uint64_t bar;
     if (threadIdx.x == 0) {
         tma::mbar_init(&bar, 1);
         tma::fence_barrier_init();
         // nothing arrives on the barrier: the bounded wait gives up
         if (!tma::mbar_wait_bounded(&bar, 0u)) atomicOr(flag, FLAG_TIMEOUT);
+    }
+    if (threadIdx.x == 32) {
+        // nothing raises the counter: the multi-step launch's bounded wait
+        // on a neighbour tile gives up
+        if (!tma::wait_at_least(never, 1u)) atomicOr(flag, FLAG_TIMEOUT);
     }
 }
 
@@ -205,8 +212,16 @@ extern "C" mrt_status mrt_debug_padding(mrt_grid* g, long* nonzero) {
 
 extern "C" mrt_status mrt_debug_wait_timeout(mrt_grid* g) {
     if (!g) return mrt_fail(MRT_EINVAL, "grid is NULL");
-    wait_timeout_kernel<<<1, 32, 0, g->stream>>>(g->flag);
-    cudaError_t e = cudaGetLastError();
+    // a zero counter that nothing raises, freed in stream order after the probe
+    unsigned* never = nullptr;
+    cudaError_t e = cudaMallocAsync(&never, sizeof(unsigned), g->stream);
+    if (e != cudaSuccess) return mrt_fail(MRT_ENOMEM, "timeout probe: %s", cudaGetErrorString(e));
+    e = cudaMemsetAsync(never, 0, sizeof(unsigned), g->stream);
+    if (e == cudaSuccess) {
+        wait_timeout_kernel<<<1, 64, 0, g->stream>>>(g->flag, never);
+        e = cudaGetLastError();
+    }
+    cudaFreeAsync(never, g->stream);
     if (e != cudaSuccess) return mrt_fail(MRT_ECUDA, "timeout probe: %s", cudaGetErrorString(e));
     return MRT_OK;
 }

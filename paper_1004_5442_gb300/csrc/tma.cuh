@@ -88,6 +88,34 @@ __device__ __forceinline__ void fence_async_shared() {
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 
+// Flags between the blocks of one launch (the split kernel's multi-step
+// form): a relaxed load of a counter, a release store of one, and a bounded
+// wait of one thread until a counter reaches a target.
+__device__ __forceinline__ unsigned ld_relaxed(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release(unsigned* p, unsigned v) {
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Bounded wait of one thread until *p >= target (2 s limit), polling with
+// relaxed loads; the acquire fence after the last one orders this thread's
+// later reads after the release that published the count.
+__device__ __forceinline__ bool wait_at_least(const unsigned* p, unsigned target) {
+    bool ok = ld_relaxed(p) >= target;
+    if (!ok) {
+        // spin for the first 20 us (a neighbour is normally a fraction of a
+        // step behind), then back off
+        const uint64_t t0 = globaltimer_ns();
+        uint64_t el = 0;
+        while (!(ok = ld_relaxed(p) >= target) && (el = globaltimer_ns() - t0) <= kWaitLimitNs)
+            if (el > 20000) __nanosleep(256);
+    }
+    asm volatile("fence.acq_rel.gpu;" ::: "memory");
+    return ok;
+}
 
 }  // namespace tma
 }  // namespace mrt
