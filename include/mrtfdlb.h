@@ -121,9 +121,11 @@ typedef struct mrt_params {
 typedef struct mrt_grid mrt_grid;
 
 /* Create a grid and set f = f^eq(rho, u, T) in every cell (Sect. (b):
- * f^eq = M^-1 fhat^eq).  rho, ux, uy, T are [ny][nx] doubles, on the device
- * if fields_on_device, else on the host.  stream is a cudaStream_t (NULL =
- * legacy default stream).  Errors: MRT_EINVAL for nx or ny < 3, dx, dt <= 0,
+ * f^eq = M^-1 fhat^eq, formed in FP64 and stored in the grid's precision).
+ * rho, ux, uy, T are [ny][nx] doubles, on the device if fields_on_device,
+ * else on the host; host fields are uploaded through a device buffer of
+ * 4 nx ny doubles that the grid keeps for mrt_get_macro's host readout.
+ * stream is a cudaStream_t (NULL = legacy default stream).  Errors: MRT_EINVAL for nx or ny < 3, dx, dt <= 0,
  * gamma <= 1, a negative or non-finite rate, a null pointer, and for an
  * initial state with rho <= 0, T <= 0 or a non-finite value (checked on the
  * device); MRT_ENOMEM; MRT_ECUDA.  Synchronises the stream once. */
@@ -157,7 +159,9 @@ mrt_status mrt_step(mrt_grid *g, long nsteps);
  * e = fhat_4 = b rho R T + j^2/rho, R = 1 as in Sect. "Numerical Simulation
  * and Analysis"): T = (e - j^2/rho)/(b rho).  Outputs are [ny][nx] doubles, on the
  * device if dst_on_device (asynchronous on the grid's stream), else on the
- * host (synchronises).  Any output pointer may be NULL to skip it. */
+ * host (synchronises; through the grid's device buffer of 4 nx ny doubles,
+ * allocated by the first host readout unless host fields created the grid).
+ * Any output pointer may be NULL to skip it. */
 mrt_status mrt_get_macro(mrt_grid *g, double *rho, double *ux, double *uy, double *T,
                          int dst_on_device);
 

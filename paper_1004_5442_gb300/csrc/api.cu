@@ -161,68 +161,108 @@ int mrt_model_build(double dx, double dt, double b, const double s[16], Coef<dou
 // ---------------------------------------------------------------------------
 namespace {
 
-// f = M^-1 fhat^eq(rho, u, T) per cell, in FP64, stored as T.
-template <class T>
-__global__ void init_kernel(Layout L, InitCoef ic, const double* __restrict__ rho,
-                            const double* __restrict__ ux, const double* __restrict__ uy,
-                            const double* __restrict__ Tf, T* __restrict__ f, unsigned* flag) {
-    const long n = (long)L.nx * L.ny;
-    for (long c = blockIdx.x * (long)blockDim.x + threadIdx.x; c < n; c += (long)gridDim.x * blockDim.x) {
-        const int x = (int)(c % L.nx), y = (int)(c / L.nx);
-        const double r = rho[c], u = ux[c], v = uy[c], t = Tf[c];
-        if (!(r > 0.0) || !(t > 0.0) || !isfinite(r) || !isfinite(t) || !isfinite(u) || !isfinite(v))
-            atomicOr(flag, FLAG_UNSTABLE);
-        const double b = ic.b;
-        const double jx = r * u, jy = r * v;
-        const double P = r * t;
-        const double j2r = jx * u + jy * v;
-        const double e = b * P + j2r;
-        // Appendix equilibria (R = 1)
-        double m[16];
-        m[0] = r; m[1] = jx; m[2] = jy; m[3] = e;
-        m[4] = 2 * P + j2r;
-        m[5] = jx * u - jy * v;
-        m[6] = jx * v;
-        m[7] = (e + 2 * P) * u;
-        m[8] = (e + 2 * P) * v;
-        m[9] = (4 * P + j2r) * u;
-        m[10] = (4 * P + j2r) * v;
-        m[11] = (2 * P + m[5]) * u;
-        m[12] = (m[5] - 2 * P) * v;
-        const double u2 = u * u + v * v;
-        m[13] = 2 * (b + 2) * P * t + (6 + b) * t * j2r + j2r * u2;
-        m[14] = ((b + 4) * P + j2r) * u * v;
-        m[15] = ((b + 4) * P + j2r) * (u * u - v * v);
-        // block inverses
-        const double a1[4] = {m[0], m[3], m[4], m[13]};
-        const double ex[4] = {m[1], m[7], m[9], m[11]};
-        const double ey[4] = {m[2], m[8], m[10], -m[12]};
-        const double b1[2] = {m[5], m[15]};
-        const double b2[2] = {m[6], m[14]};
-        double out[16];
-        for (int g = 0; g < 4; ++g) {
-            double S = 0, Dx = 0, Dy = 0;
-            for (int k = 0; k < 4; ++k) {
-                S += ic.Ainv[g][k] * a1[k];
-                Dx += ic.Binv[g][k] * ex[k];
-                Dy += ic.Binv[g][k] * ey[k];
-            }
-            if (g < 2) {
-                const double Q = ic.C1inv[g][0] * b1[0] + ic.C1inv[g][1] * b1[1];
-                out[4 * g + 0] = 0.25 * S + 0.5 * Dx + 0.25 * Q;
-                out[4 * g + 2] = 0.25 * S - 0.5 * Dx + 0.25 * Q;
-                out[4 * g + 1] = 0.25 * S + 0.5 * Dy - 0.25 * Q;
-                out[4 * g + 3] = 0.25 * S - 0.5 * Dy - 0.25 * Q;
-            } else {
-                const double X = ic.C2inv[g - 2][0] * b2[0] + ic.C2inv[g - 2][1] * b2[1];
-                out[4 * g + 0] = 0.25 * (S + Dx + Dy + X);
-                out[4 * g + 1] = 0.25 * (S - Dx + Dy - X);
-                out[4 * g + 2] = 0.25 * (S - Dx - Dy + X);
-                out[4 * g + 3] = 0.25 * (S + Dx - Dy - X);
-            }
+// The validity test of an input cell on bit patterns, in integer
+// instructions: rho and T positive and finite (a positive finite double's
+// pattern lies in [1, 0x7fefffffffffffff]), u and v finite.
+__device__ __forceinline__ bool init_valid(double r, double u, double v, double t) {
+    const unsigned long long kInf = 0x7ff0000000000000ull;
+    const unsigned long long br = (unsigned long long)__double_as_longlong(r) - 1ull;
+    const unsigned long long bt = (unsigned long long)__double_as_longlong(t) - 1ull;
+    return br < kInf - 1ull && bt < kInf - 1ull && ((unsigned long long)__double_as_longlong(u) & kInf) != kInf &&
+           ((unsigned long long)__double_as_longlong(v) & kInf) != kInf;
+}
+
+// f = M^-1 fhat^eq(rho, u, T) per cell, in FP64, stored as T.  Blocks take
+// runs of one row, so no cell index is divided.  The inverse blocks' 1/4
+// and 1/2 factors are folded into the constants (InitFold), which scales
+// every product and sum by a power of two and so changes no rounding.
+struct InitFold {
+    double Ainv[4][4];    // 1/4 Ainv
+    double Bax[4][4];     // 1/2 Binv for the axis groups, 1/4 for the diagonal ones
+    double C1inv[2][2];   // 1/4 C1inv
+    double C2inv[2][2];   // 1/4 C2inv
+    double b;
+};
+static InitFold init_fold(const InitCoef& ic) {
+    InitFold o;
+    for (int g = 0; g < 4; ++g)
+        for (int k = 0; k < 4; ++k) {
+            o.Ainv[g][k] = 0.25 * ic.Ainv[g][k];
+            o.Bax[g][k] = (g < 2 ? 0.5 : 0.25) * ic.Binv[g][k];
         }
-        const long o = (long)(y + 1) * L.pitch + L.G + x;
-        for (int i = 0; i < 16; ++i) f[i * L.plane + o] = (T)out[i];
+    for (int g = 0; g < 2; ++g)
+        for (int j = 0; j < 2; ++j) {
+            o.C1inv[g][j] = 0.25 * ic.C1inv[g][j];
+            o.C2inv[g][j] = 0.25 * ic.C2inv[g][j];
+        }
+    o.b = ic.b;
+    return o;
+}
+
+template <class T>
+__global__ void init_kernel(Layout L, InitFold ic, const double* __restrict__ rho,
+                            const double* __restrict__ ux, const double* __restrict__ uy,
+                            const double* __restrict__ Tf, T* __restrict__ f, unsigned* flag, int y0, int y1) {
+    for (int y = y0 + blockIdx.y; y < y1; y += gridDim.y) {
+        for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < L.nx; x += gridDim.x * blockDim.x) {
+            const long c = (long)y * L.nx + x;
+            const double r = rho[c], u = ux[c], v = uy[c], t = Tf[c];
+            if (!init_valid(r, u, v, t)) atomicOr(flag, FLAG_UNSTABLE);
+            const double b = ic.b;
+            const double jx = r * u, jy = r * v;
+            const double P = r * t;
+            const double j2r = jx * u + jy * v;
+            const double e = b * P + j2r;
+            // Appendix equilibria (R = 1)
+            double m[16];
+            m[0] = r; m[1] = jx; m[2] = jy; m[3] = e;
+            m[4] = 2 * P + j2r;
+            m[5] = jx * u - jy * v;
+            m[6] = jx * v;
+            m[7] = (e + 2 * P) * u;
+            m[8] = (e + 2 * P) * v;
+            m[9] = (4 * P + j2r) * u;
+            m[10] = (4 * P + j2r) * v;
+            m[11] = (2 * P + m[5]) * u;
+            m[12] = (m[5] - 2 * P) * v;
+            const double u2 = u * u + v * v;
+            m[13] = 2 * (b + 2) * P * t + (6 + b) * t * j2r + j2r * u2;
+            m[14] = ((b + 4) * P + j2r) * u * v;
+            m[15] = ((b + 4) * P + j2r) * (u * u - v * v);
+            // block inverses (scaled: S = Ainv a / 4, Dx = Binv ex / 2 or / 4, ...)
+            const double a1[4] = {m[0], m[3], m[4], m[13]};
+            const double ex[4] = {m[1], m[7], m[9], m[11]};
+            const double ey[4] = {m[2], m[8], m[10], -m[12]};
+            const double b1[2] = {m[5], m[15]};
+            const double b2[2] = {m[6], m[14]};
+            double out[16];
+#pragma unroll
+            for (int g = 0; g < 4; ++g) {
+                double S = 0, Dx = 0, Dy = 0;
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    S += ic.Ainv[g][k] * a1[k];
+                    Dx += ic.Bax[g][k] * ex[k];
+                    Dy += ic.Bax[g][k] * ey[k];
+                }
+                if (g < 2) {
+                    const double Q = ic.C1inv[g][0] * b1[0] + ic.C1inv[g][1] * b1[1];
+                    out[4 * g + 0] = S + Dx + Q;
+                    out[4 * g + 2] = S - Dx + Q;
+                    out[4 * g + 1] = S + Dy - Q;
+                    out[4 * g + 3] = S - Dy - Q;
+                } else {
+                    const double X = ic.C2inv[g - 2][0] * b2[0] + ic.C2inv[g - 2][1] * b2[1];
+                    out[4 * g + 0] = S + Dx + Dy + X;
+                    out[4 * g + 1] = S - Dx + Dy - X;
+                    out[4 * g + 2] = S - Dx - Dy + X;
+                    out[4 * g + 3] = S + Dx - Dy - X;
+                }
+            }
+            const long o = (long)(y + 1) * L.pitch + L.G + x;
+#pragma unroll
+            for (int i = 0; i < 16; ++i) f[i * L.plane + o] = (T)out[i];
+        }
     }
 }
 
@@ -284,20 +324,40 @@ __device__ __forceinline__ void cons_moments(const T* f, const Layout& L, long o
     q[3] = kW(0) * S[0] + kW(1) * S[1] + kW(2) * S[2] + kW(3) * S[3];
 }
 
-// rho, u, T per cell (FP64); T = (e - j^2/rho)/(b rho).
+// rho, u, T per cell (FP64) of rows [y0, y1); u = j/rho, T = (e - j^2/rho)/(b rho),
+// with one reciprocal of rho per cell (the FP64 pipe bounds this kernel).
 template <class T>
-__global__ void macro_kernel(Layout L, double b, const T* __restrict__ f, double* rho, double* ux,
-                             double* uy, double* Tf) {
-    const long n = (long)L.nx * L.ny;
-    for (long c = blockIdx.x * (long)blockDim.x + threadIdx.x; c < n; c += (long)gridDim.x * blockDim.x) {
-        const int x = (int)(c % L.nx), y = (int)(c / L.nx);
-        double q[4];
-        cons_moments<T>(f, L, (long)(y + 1) * L.pitch + L.G + x, q);
-        if (rho) rho[c] = q[0];
-        if (ux) ux[c] = q[1] / q[0];
-        if (uy) uy[c] = q[2] / q[0];
-        if (Tf) Tf[c] = (q[3] - (q[1] * q[1] + q[2] * q[2]) / q[0]) / (b * q[0]);
+__global__ void macro_kernel(Layout L, double inv_b, const T* __restrict__ f, double* rho, double* ux,
+                             double* uy, double* Tf, int y0, int y1) {
+    for (int y = y0 + blockIdx.y; y < y1; y += gridDim.y) {
+        for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < L.nx; x += gridDim.x * blockDim.x) {
+            const long c = (long)y * L.nx + x;
+            double q[4];
+            cons_moments<T>(f, L, (long)(y + 1) * L.pitch + L.G + x, q);
+            const double ri = 1.0 / q[0];
+            const double u = q[1] * ri, v = q[2] * ri;
+            if (rho) rho[c] = q[0];
+            if (ux) ux[c] = u;
+            if (uy) uy[c] = v;
+            if (Tf) Tf[c] = (q[3] - (q[1] * u + q[2] * v)) * (ri * inv_b);
+        }
     }
+}
+
+// Launch shape of the row-range kernels: blocks of 256 along a row, blocks
+// in y over the rows.
+static dim3 rows_grid(const Layout& L, int rows) {
+    return dim3((unsigned)std::min<long>((L.nx + 255) / 256, 64), (unsigned)std::max(1, std::min(rows, 4096)));
+}
+
+// Row chunks of a host upload or readout of the four fields: about 64 MB
+// of fields each, at most 8.
+static int field_chunks(const Layout& L) {
+    const long bytes = 32L * L.nx * L.ny;
+    long k = (bytes + (64L << 20) - 1) / (64L << 20);
+    if (k > 8) k = 8;
+    if (k > L.ny) k = L.ny;
+    return (int)std::max(1L, k);
 }
 
 constexpr int RED_THREADS = 256;
@@ -565,6 +625,7 @@ static void release(mrt_grid* g) {
     cudaSetDevice(g->device);
     if (g->stream) cudaStreamSynchronize(g->stream);
     if (g->tstream) cudaStreamSynchronize(g->tstream);
+    if (g->xstream) cudaStreamSynchronize(g->xstream);
     cudaFree(g->f[0]);
     cudaFree(g->f[1]);
     cudaFree(g->flag);
@@ -585,6 +646,8 @@ static void release(mrt_grid* g) {
         if (g->ev_red[b]) cudaEventDestroy(g->ev_red[b]);
     }
     if (g->tstream) cudaStreamDestroy(g->tstream);
+    if (g->xstream) cudaStreamDestroy(g->xstream);
+    if (g->ev_x) cudaEventDestroy(g->ev_x);
     for (int c = 0; c < 2; ++c)
         for (int q = 0; q < 2; ++q)
             if (g->pair_exec[c][q]) cudaGraphExecDestroy(g->pair_exec[c][q]);
@@ -623,15 +686,54 @@ static void launch_ghosts(mrt_grid* g, int buf) {
     launch_ghost_kernels<T>(g, static_cast<T*>(g->f[buf]), true);
 }
 
+// The initial state of rows [y0, y1) (fields indexed over the whole grid).
+template <class T>
+static mrt_status init_rows(mrt_grid* g, const InitFold& ic, const double* rho, const double* ux,
+                            const double* uy, const double* T_, int y0, int y1) {
+    init_kernel<T><<<rows_grid(g->L, y1 - y0), 256, 0, g->stream>>>(g->L, ic, rho, ux, uy, T_,
+                                                                    static_cast<T*>(g->f[0]), g->flag, y0, y1);
+    CUDA_TRY(cudaGetLastError());
+    return MRT_OK;
+}
+
+// The initial state from device fields, or from host fields uploaded in row
+// chunks on the copy stream, each chunk initialised on the grid's stream
+// once its upload is done (the next chunk's upload overlapping it); then
+// the ghosts and the copy into the second buffer.
 template <class T>
 static mrt_status do_init(mrt_grid* g, const double* rho, const double* ux, const double* uy,
-                          const double* T_) {
+                          const double* T_, bool host) {
     InitCoef ic;
     if (mrt_init_coef_build(g->b, &ic) != 0) return fail(MRT_ECUDA, "model blocks singular");
+    const InitFold fold = init_fold(ic);
     const long n = (long)g->L.nx * g->L.ny;
-    init_kernel<T><<<grid_for(n, 256), 256, 0, g->stream>>>(g->L, ic, rho, ux, uy, T_,
-                                                            static_cast<T*>(g->f[0]), g->flag);
-    CUDA_TRY(cudaGetLastError());
+    if (!host) {
+        mrt_status st = init_rows<T>(g, fold, rho, ux, uy, T_, 0, g->L.ny);
+        if (st != MRT_OK) return st;
+    } else {
+        if (!g->macro_tmp) {
+            cudaError_t e = cudaMalloc(&g->macro_tmp, 4 * sizeof(double) * (size_t)n);
+            if (e != cudaSuccess) return fail(MRT_ENOMEM, "cudaMalloc staging: %s", cudaGetErrorString(e));
+        }
+        const double* h[4] = {rho, ux, uy, T_};
+        double* d = g->macro_tmp;
+        // the copy stream starts behind the grid's stream (an earlier readout
+        // of the staging buffer, a re-initialisation of a stepping grid)
+        CUDA_TRY(cudaEventRecord(g->ev_x, g->stream));
+        CUDA_TRY(cudaStreamWaitEvent(g->xstream, g->ev_x, 0));
+        const int k = field_chunks(g->L), rows = (g->L.ny + k - 1) / k;
+        for (int y0 = 0; y0 < g->L.ny; y0 += rows) {
+            const int y1 = std::min(g->L.ny, y0 + rows);
+            const long c0 = (long)y0 * g->L.nx, cn = (long)(y1 - y0) * g->L.nx;
+            for (int q = 0; q < 4; ++q)
+                CUDA_TRY(cudaMemcpyAsync(d + q * n + c0, h[q] + c0, cn * sizeof(double), cudaMemcpyHostToDevice,
+                                         g->xstream));
+            CUDA_TRY(cudaEventRecord(g->ev_x, g->xstream));
+            CUDA_TRY(cudaStreamWaitEvent(g->stream, g->ev_x, 0));
+            mrt_status st = init_rows<T>(g, fold, d, d + n, d + 2 * n, d + 3 * n, y0, y1);
+            if (st != MRT_OK) return st;
+        }
+    }
     launch_ghosts<T>(g, 0);
     CUDA_TRY(cudaGetLastError());
     // both buffers carry the same ghosts (fixed ones are never rewritten)
@@ -681,8 +783,9 @@ extern "C" mrt_status mrt_create(const mrt_params* params, const double* rho, co
     if ((e = cudaMalloc(&g->f[0], bytes)) != cudaSuccess || (e = cudaMalloc(&g->f[1], bytes)) != cudaSuccess)
         return bail(fail(e == cudaErrorMemoryAllocation ? MRT_ENOMEM : MRT_ECUDA,
                          "cudaMalloc of 2 x %zu bytes failed: %s", bytes, cudaGetErrorString(e)));
-    if ((e = cudaMemsetAsync(g->f[0], 0, bytes, g->stream)) != cudaSuccess ||
-        (e = cudaMemsetAsync(g->f[1], 0, bytes, g->stream)) != cudaSuccess)
+    // buffer 0's padding stays zero from here on; buffer 1 is a copy of
+    // buffer 0 once the initial state is written
+    if ((e = cudaMemsetAsync(g->f[0], 0, bytes, g->stream)) != cudaSuccess)
         return bail(fail(MRT_ECUDA, "memset: %s", cudaGetErrorString(e)));
     if ((e = cudaMalloc(&g->flag, sizeof(unsigned))) != cudaSuccess ||
         (e = cudaMemsetAsync(g->flag, 0, sizeof(unsigned), g->stream)) != cudaSuccess ||
@@ -704,7 +807,9 @@ extern "C" mrt_status mrt_create(const mrt_params* params, const double* rho, co
         if ((e = cudaEventCreateWithFlags(&g->ev_step[b], cudaEventDisableTiming)) != cudaSuccess ||
             (e = cudaEventCreateWithFlags(&g->ev_red[b], cudaEventDisableTiming)) != cudaSuccess)
             return bail(fail(MRT_ECUDA, "cudaEventCreate: %s", cudaGetErrorString(e)));
-    if ((e = cudaStreamCreateWithFlags(&g->tstream, cudaStreamNonBlocking)) != cudaSuccess)
+    if ((e = cudaStreamCreateWithFlags(&g->tstream, cudaStreamNonBlocking)) != cudaSuccess ||
+        (e = cudaStreamCreateWithFlags(&g->xstream, cudaStreamNonBlocking)) != cudaSuccess ||
+        (e = cudaEventCreateWithFlags(&g->ev_x, cudaEventDisableTiming)) != cudaSuccess)
         return bail(fail(MRT_ECUDA, "cudaStreamCreate: %s", cudaGetErrorString(e)));
 
     // kernel choice and launch geometry
@@ -810,25 +915,12 @@ mrt_status mrt_fail(mrt_status s, const char* fmt, ...) {
 mrt_status mrt_reinit(mrt_grid* g, const double* rho, const double* ux, const double* uy, const double* T,
                       int on_device) {
     if (!rho || !ux || !uy || !T) return fail(MRT_EINVAL, "null field pointer");
-    const long n = (long)g->L.nx * g->L.ny;
     cudaError_t e;
-    const double* d_in[4] = {rho, ux, uy, T};
-    double* staged = nullptr;
-    if (!on_device) {
-        if ((e = cudaMalloc(&staged, 4 * sizeof(double) * (size_t)n)) != cudaSuccess)
-            return fail(MRT_ENOMEM, "cudaMalloc staging: %s", cudaGetErrorString(e));
-        for (int q = 0; q < 4; ++q) {
-            if ((e = cudaMemcpyAsync(staged + q * n, d_in[q], n * sizeof(double), cudaMemcpyHostToDevice,
-                                     g->stream)) != cudaSuccess) {
-                cudaFree(staged);
-                return fail(MRT_ECUDA, "upload: %s", cudaGetErrorString(e));
-            }
-            d_in[q] = staged + q * n;
-        }
-    }
+    // host fields go through the grid's readout buffer (four fields of the
+    // grid's size, kept for mrt_get_macro to host memory)
     CUDA_TRY(cudaMemsetAsync(g->flag, 0, sizeof(unsigned), g->stream));
-    mrt_status st = g->fp64 ? do_init<double>(g, d_in[0], d_in[1], d_in[2], d_in[3])
-                            : do_init<float>(g, d_in[0], d_in[1], d_in[2], d_in[3]);
+    mrt_status st = g->fp64 ? do_init<double>(g, rho, ux, uy, T, !on_device)
+                            : do_init<float>(g, rho, ux, uy, T, !on_device);
     // the initial state is validated by the init kernel through the flag
     unsigned h = 0;
     if (st == MRT_OK) {
@@ -838,7 +930,8 @@ mrt_status mrt_reinit(mrt_grid* g, const double* rho, const double* ux, const do
     } else {
         cudaStreamSynchronize(g->stream);
     }
-    if (staged) cudaFree(staged);
+    // no upload from the caller's memory outlives the call, even a failed one
+    if (!on_device) cudaStreamSynchronize(g->xstream);
     if (st != MRT_OK) return st;
     if (h & FLAG_UNSTABLE) return fail(MRT_EINVAL, "initial state: rho and T must be finite and > 0");
     g->cur = 0;
@@ -1031,10 +1124,9 @@ extern "C" mrt_status mrt_step(mrt_grid* g, long nsteps) {
 }
 
 template <class T>
-static mrt_status macro_impl(mrt_grid* g, double* rho, double* ux, double* uy, double* Tf) {
-    const long n = (long)g->L.nx * g->L.ny;
-    macro_kernel<T><<<grid_for(n, 256), 256, 0, g->stream>>>(g->L, g->b, static_cast<const T*>(g->f[g->cur]),
-                                                             rho, ux, uy, Tf);
+static mrt_status macro_impl(mrt_grid* g, double* rho, double* ux, double* uy, double* Tf, int y0, int y1) {
+    macro_kernel<T><<<rows_grid(g->L, y1 - y0), 256, 0, g->stream>>>(
+        g->L, 1.0 / g->b, static_cast<const T*>(g->f[g->cur]), rho, ux, uy, Tf, y0, y1);
     CUDA_TRY(cudaGetLastError());
     return MRT_OK;
 }
@@ -1043,17 +1135,35 @@ extern "C" mrt_status mrt_get_macro(mrt_grid* g, double* rho, double* ux, double
                                     int dst_on_device) {
     if (!g) return fail(MRT_EINVAL, "grid is NULL");
     const long n = (long)g->L.nx * g->L.ny;
-    if (dst_on_device) return g->fp64 ? macro_impl<double>(g, rho, ux, uy, T) : macro_impl<float>(g, rho, ux, uy, T);
+    if (dst_on_device)
+        return g->fp64 ? macro_impl<double>(g, rho, ux, uy, T, 0, g->L.ny)
+                       : macro_impl<float>(g, rho, ux, uy, T, 0, g->L.ny);
     if (!g->macro_tmp) CUDA_TRY(cudaMalloc(&g->macro_tmp, 4 * sizeof(double) * (size_t)n));
     double* d[4];
     double* h[4] = {rho, ux, uy, T};
     for (int q = 0; q < 4; ++q) d[q] = h[q] ? g->macro_tmp + q * n : nullptr;
-    mrt_status st = g->fp64 ? macro_impl<double>(g, d[0], d[1], d[2], d[3]) : macro_impl<float>(g, d[0], d[1], d[2], d[3]);
-    if (st != MRT_OK) return st;
-    for (int q = 0; q < 4; ++q)
-        if (h[q]) CUDA_TRY(cudaMemcpyAsync(h[q], d[q], n * sizeof(double), cudaMemcpyDeviceToHost, g->stream));
-    CUDA_TRY(cudaStreamSynchronize(g->stream));
-    return MRT_OK;
+    // row chunks: the kernel on the grid's stream, each chunk's download on
+    // the copy stream once its kernel is done (overlapping the next chunk's)
+    const int k = field_chunks(g->L), rows = (g->L.ny + k - 1) / k;
+    mrt_status st = MRT_OK;
+    for (int y0 = 0; y0 < g->L.ny && st == MRT_OK; y0 += rows) {
+        const int y1 = std::min(g->L.ny, y0 + rows);
+        const long c0 = (long)y0 * g->L.nx, cn = (long)(y1 - y0) * g->L.nx;
+        st = g->fp64 ? macro_impl<double>(g, d[0], d[1], d[2], d[3], y0, y1)
+                     : macro_impl<float>(g, d[0], d[1], d[2], d[3], y0, y1);
+        cudaError_t e = cudaSuccess;
+        if (st == MRT_OK && ((e = cudaEventRecord(g->ev_x, g->stream)) != cudaSuccess ||
+                             (e = cudaStreamWaitEvent(g->xstream, g->ev_x, 0)) != cudaSuccess))
+            st = fail(MRT_ECUDA, "readout: %s", cudaGetErrorString(e));
+        for (int q = 0; q < 4 && st == MRT_OK; ++q)
+            if (h[q] && (e = cudaMemcpyAsync(h[q] + c0, d[q] + c0, cn * sizeof(double), cudaMemcpyDeviceToHost,
+                                             g->xstream)) != cudaSuccess)
+                st = fail(MRT_ECUDA, "readout: %s", cudaGetErrorString(e));
+    }
+    // no download into the caller's memory outlives the call, even a failed one
+    const cudaError_t e = cudaStreamSynchronize(g->xstream);
+    if (st == MRT_OK && e != cudaSuccess) st = fail(MRT_ECUDA, "readout: %s", cudaGetErrorString(e));
+    return st;
 }
 
 template <class T>

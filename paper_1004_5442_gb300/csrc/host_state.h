@@ -85,7 +85,12 @@ struct mrt_grid {
     cudaEvent_t tev[kTotalsEvents] = {};  // completion markers of asynchronous totals copies
     long tickets = 0;                // asynchronous totals copies issued
     bool totals_fresh = false;
-    double* macro_tmp = nullptr;     // 4 fields, for host readout
+    double* macro_tmp = nullptr;     // 4 fields, for host upload at creation and host readout
+    // Host uploads and readouts of the four fields run in row chunks on a
+    // copy stream, each chunk's copy overlapping the next (or previous)
+    // chunk's initialisation or readout kernel on the grid's stream.
+    cudaStream_t xstream = nullptr;
+    cudaEvent_t ev_x = nullptr;
     long steps = 0;
     int kernel = MRT_KERNEL_DIRECT;  // in use
     CUtensorMap maps[2];       // loads: whole padded rows, box with halo
