@@ -121,7 +121,9 @@ typedef struct mrt_params {
 typedef struct mrt_grid mrt_grid;
 
 /* Create a grid and set f = f^eq(rho, u, T) in every cell (Sect. (b):
- * f^eq = M^-1 fhat^eq, formed in FP64 and stored in the grid's precision).
+ * f^eq = M^-1 fhat^eq, formed in FP64 for FP64 grids; for FP32 grids in
+ * double-float arithmetic, about 44 bits, whose FP32 rounding is that of
+ * the FP64 value except within about 2^-44 of a rounding boundary).
  * rho, ux, uy, T are [ny][nx] doubles, on the device if fields_on_device,
  * else on the host; host fields are uploaded through a device buffer of
  * 4 nx ny doubles that the grid keeps for mrt_get_macro's host readout.

@@ -172,49 +172,104 @@ __device__ __forceinline__ bool init_valid(double r, double u, double v, double 
            ((unsigned long long)__double_as_longlong(v) & kInf) != kInf;
 }
 
-// f = M^-1 fhat^eq(rho, u, T) per cell, in FP64, stored as T.  Blocks take
-// runs of one row, so no cell index is divided.  The inverse blocks' 1/4
-// and 1/2 factors are folded into the constants (InitFold), which scales
-// every product and sum by a power of two and so changes no rounding.
-struct InitFold {
-    double Ainv[4][4];    // 1/4 Ainv
-    double Bax[4][4];     // 1/2 Binv for the axis groups, 1/4 for the diagonal ones
-    double C1inv[2][2];   // 1/4 C1inv
-    double C2inv[2][2];   // 1/4 C2inv
-    double b;
+// Double-float arithmetic for the initialisation of FP32 grids: a value is
+// the unevaluated sum hi + lo of two floats (|lo| <= ulp(hi) / 2), about 44
+// significant bits, kept on the FP32 pipe.  Sums use Knuth's TwoSum and the
+// "sloppy" double-word addition, products the FMA-based exact product and
+// the double-word product (Joldes, Muller and Popescu, ACM TOMS 44(2),
+// 2017): each operation errs by about 2^-44 of its operands' magnitudes, so
+// rounding a result to FP32 gives the FP32 rounding of the FP64 formula's
+// value except within about 2^-44 of a rounding boundary.
+struct DF {
+    float hi, lo;
 };
-static InitFold init_fold(const InitCoef& ic) {
-    InitFold o;
+__device__ __forceinline__ DF df_fast_two_sum(float a, float b) {   // |a| >= |b|
+    const float s = a + b;
+    return {s, b - (s - a)};
+}
+__device__ __forceinline__ DF operator+(DF x, DF y) {
+    const float s = x.hi + y.hi, bb = s - x.hi;
+    float e = (x.hi - (s - bb)) + (y.hi - bb);   // TwoSum error of the high parts
+    e += x.lo + y.lo;
+    return df_fast_two_sum(s, e);
+}
+__device__ __forceinline__ DF operator-(DF x) { return {-x.hi, -x.lo}; }
+__device__ __forceinline__ DF operator-(DF x, DF y) { return x + (-y); }
+__device__ __forceinline__ DF operator*(DF x, DF y) {
+    const float p = x.hi * y.hi;
+    float e = fmaf(x.hi, y.hi, -p);                // exact error of the high product
+    e = fmaf(x.hi, y.lo, fmaf(x.lo, y.hi, e));
+    return df_fast_two_sum(p, e);
+}
+__device__ __forceinline__ DF operator*(int k, DF x) { return {(float)k * x.hi, (float)k * x.lo}; }  // k = 2, 4: exact
+
+template <class A>
+__device__ __forceinline__ A init_in(double x);
+template <>
+__device__ __forceinline__ double init_in<double>(double x) { return x; }
+template <>
+__device__ __forceinline__ DF init_in<DF>(double x) {
+    const float hi = __double2float_rn(x);
+    return {hi, __double2float_rn(x - (double)hi)};
+}
+__device__ __forceinline__ double init_out(double x) { return x; }
+__device__ __forceinline__ float init_out(DF x) { return x.hi + x.lo; }
+
+// f = M^-1 fhat^eq(rho, u, T) per cell in arithmetic A (FP64 grids: double;
+// FP32 grids: double-float), stored as T.  Blocks take runs of one row, so
+// no cell index is divided.  The inverse blocks' 1/4 and 1/2 factors are
+// folded into the constants (InitK), which scales every product and sum by
+// a power of two and so changes no rounding.
+template <class A>
+struct InitK {
+    A Ainv[4][4];    // 1/4 Ainv
+    A Bax[4][4];     // 1/2 Binv for the axis groups, 1/4 for the diagonal ones
+    A C1inv[2][2];   // 1/4 C1inv
+    A C2inv[2][2];   // 1/4 C2inv
+    A b, c13a, c13b, c14;   // b, 2 (b + 2), 6 + b, b + 4
+};
+static double init_const(double x, double*) { return x; }
+static DF init_const(double x, DF*) {
+    const float hi = (float)x;
+    return {hi, (float)(x - (double)hi)};
+}
+template <class A>
+static InitK<A> init_k(const InitCoef& ic) {
+    InitK<A> o;
+    A* tag = nullptr;
     for (int g = 0; g < 4; ++g)
         for (int k = 0; k < 4; ++k) {
-            o.Ainv[g][k] = 0.25 * ic.Ainv[g][k];
-            o.Bax[g][k] = (g < 2 ? 0.5 : 0.25) * ic.Binv[g][k];
+            o.Ainv[g][k] = init_const(0.25 * ic.Ainv[g][k], tag);
+            o.Bax[g][k] = init_const((g < 2 ? 0.5 : 0.25) * ic.Binv[g][k], tag);
         }
     for (int g = 0; g < 2; ++g)
         for (int j = 0; j < 2; ++j) {
-            o.C1inv[g][j] = 0.25 * ic.C1inv[g][j];
-            o.C2inv[g][j] = 0.25 * ic.C2inv[g][j];
+            o.C1inv[g][j] = init_const(0.25 * ic.C1inv[g][j], tag);
+            o.C2inv[g][j] = init_const(0.25 * ic.C2inv[g][j], tag);
         }
-    o.b = ic.b;
+    o.b = init_const(ic.b, tag);
+    o.c13a = init_const(2 * (ic.b + 2), tag);
+    o.c13b = init_const(6 + ic.b, tag);
+    o.c14 = init_const(ic.b + 4, tag);
     return o;
 }
 
-template <class T>
-__global__ void init_kernel(Layout L, InitFold ic, const double* __restrict__ rho,
+template <class T, class A>
+__global__ void init_kernel(Layout L, InitK<A> K, const double* __restrict__ rho,
                             const double* __restrict__ ux, const double* __restrict__ uy,
                             const double* __restrict__ Tf, T* __restrict__ f, unsigned* flag, int y0, int y1) {
     for (int y = y0 + blockIdx.y; y < y1; y += gridDim.y) {
         for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < L.nx; x += gridDim.x * blockDim.x) {
             const long c = (long)y * L.nx + x;
-            const double r = rho[c], u = ux[c], v = uy[c], t = Tf[c];
-            if (!init_valid(r, u, v, t)) atomicOr(flag, FLAG_UNSTABLE);
-            const double b = ic.b;
-            const double jx = r * u, jy = r * v;
-            const double P = r * t;
-            const double j2r = jx * u + jy * v;
-            const double e = b * P + j2r;
+            const double rd = rho[c], ud = ux[c], vd = uy[c], td = Tf[c];
+            if (!init_valid(rd, ud, vd, td)) atomicOr(flag, FLAG_UNSTABLE);
+            const A r = init_in<A>(rd), u = init_in<A>(ud), v = init_in<A>(vd), t = init_in<A>(td);
+            const A jx = r * u, jy = r * v;
+            const A P = r * t;
+            const A j2r = jx * u + jy * v;
+            const A e = K.b * P + j2r;
             // Appendix equilibria (R = 1)
-            double m[16];
+            A m[16];
             m[0] = r; m[1] = jx; m[2] = jy; m[3] = e;
             m[4] = 2 * P + j2r;
             m[5] = jx * u - jy * v;
@@ -225,34 +280,34 @@ __global__ void init_kernel(Layout L, InitFold ic, const double* __restrict__ rh
             m[10] = (4 * P + j2r) * v;
             m[11] = (2 * P + m[5]) * u;
             m[12] = (m[5] - 2 * P) * v;
-            const double u2 = u * u + v * v;
-            m[13] = 2 * (b + 2) * P * t + (6 + b) * t * j2r + j2r * u2;
-            m[14] = ((b + 4) * P + j2r) * u * v;
-            m[15] = ((b + 4) * P + j2r) * (u * u - v * v);
+            const A u2 = u * u + v * v;
+            m[13] = K.c13a * P * t + K.c13b * t * j2r + j2r * u2;
+            m[14] = (K.c14 * P + j2r) * u * v;
+            m[15] = (K.c14 * P + j2r) * (u * u - v * v);
             // block inverses (scaled: S = Ainv a / 4, Dx = Binv ex / 2 or / 4, ...)
-            const double a1[4] = {m[0], m[3], m[4], m[13]};
-            const double ex[4] = {m[1], m[7], m[9], m[11]};
-            const double ey[4] = {m[2], m[8], m[10], -m[12]};
-            const double b1[2] = {m[5], m[15]};
-            const double b2[2] = {m[6], m[14]};
-            double out[16];
+            const A a1[4] = {m[0], m[3], m[4], m[13]};
+            const A ex[4] = {m[1], m[7], m[9], m[11]};
+            const A ey[4] = {m[2], m[8], m[10], -m[12]};
+            const A b1[2] = {m[5], m[15]};
+            const A b2[2] = {m[6], m[14]};
+            A out[16];
 #pragma unroll
             for (int g = 0; g < 4; ++g) {
-                double S = 0, Dx = 0, Dy = 0;
+                A S = K.Ainv[g][0] * a1[0], Dx = K.Bax[g][0] * ex[0], Dy = K.Bax[g][0] * ey[0];
 #pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    S += ic.Ainv[g][k] * a1[k];
-                    Dx += ic.Bax[g][k] * ex[k];
-                    Dy += ic.Bax[g][k] * ey[k];
+                for (int k = 1; k < 4; ++k) {
+                    S = S + K.Ainv[g][k] * a1[k];
+                    Dx = Dx + K.Bax[g][k] * ex[k];
+                    Dy = Dy + K.Bax[g][k] * ey[k];
                 }
                 if (g < 2) {
-                    const double Q = ic.C1inv[g][0] * b1[0] + ic.C1inv[g][1] * b1[1];
+                    const A Q = K.C1inv[g][0] * b1[0] + K.C1inv[g][1] * b1[1];
                     out[4 * g + 0] = S + Dx + Q;
                     out[4 * g + 2] = S - Dx + Q;
                     out[4 * g + 1] = S + Dy - Q;
                     out[4 * g + 3] = S - Dy - Q;
                 } else {
-                    const double X = ic.C2inv[g - 2][0] * b2[0] + ic.C2inv[g - 2][1] * b2[1];
+                    const A X = K.C2inv[g - 2][0] * b2[0] + K.C2inv[g - 2][1] * b2[1];
                     out[4 * g + 0] = S + Dx + Dy + X;
                     out[4 * g + 1] = S - Dx + Dy - X;
                     out[4 * g + 2] = S - Dx - Dy + X;
@@ -261,7 +316,7 @@ __global__ void init_kernel(Layout L, InitFold ic, const double* __restrict__ rh
             }
             const long o = (long)(y + 1) * L.pitch + L.G + x;
 #pragma unroll
-            for (int i = 0; i < 16; ++i) f[i * L.plane + o] = (T)out[i];
+            for (int i = 0; i < 16; ++i) f[i * L.plane + o] = (T)init_out(out[i]);
         }
     }
 }
@@ -686,12 +741,17 @@ static void launch_ghosts(mrt_grid* g, int buf) {
     launch_ghost_kernels<T>(g, static_cast<T*>(g->f[buf]), true);
 }
 
-// The initial state of rows [y0, y1) (fields indexed over the whole grid).
+// The initial state of rows [y0, y1) (fields indexed over the whole grid):
+// FP64 grids in FP64, FP32 grids in double-float arithmetic.
 template <class T>
-static mrt_status init_rows(mrt_grid* g, const InitFold& ic, const double* rho, const double* ux,
+static mrt_status init_rows(mrt_grid* g, const InitCoef& ic, const double* rho, const double* ux,
                             const double* uy, const double* T_, int y0, int y1) {
-    init_kernel<T><<<rows_grid(g->L, y1 - y0), 256, 0, g->stream>>>(g->L, ic, rho, ux, uy, T_,
-                                                                    static_cast<T*>(g->f[0]), g->flag, y0, y1);
+    if constexpr (sizeof(T) == 8)
+        init_kernel<T, double><<<rows_grid(g->L, y1 - y0), 256, 0, g->stream>>>(
+            g->L, init_k<double>(ic), rho, ux, uy, T_, static_cast<T*>(g->f[0]), g->flag, y0, y1);
+    else
+        init_kernel<T, DF><<<rows_grid(g->L, y1 - y0), 256, 0, g->stream>>>(
+            g->L, init_k<DF>(ic), rho, ux, uy, T_, static_cast<T*>(g->f[0]), g->flag, y0, y1);
     CUDA_TRY(cudaGetLastError());
     return MRT_OK;
 }
@@ -705,10 +765,9 @@ static mrt_status do_init(mrt_grid* g, const double* rho, const double* ux, cons
                           const double* T_, bool host) {
     InitCoef ic;
     if (mrt_init_coef_build(g->b, &ic) != 0) return fail(MRT_ECUDA, "model blocks singular");
-    const InitFold fold = init_fold(ic);
     const long n = (long)g->L.nx * g->L.ny;
     if (!host) {
-        mrt_status st = init_rows<T>(g, fold, rho, ux, uy, T_, 0, g->L.ny);
+        mrt_status st = init_rows<T>(g, ic, rho, ux, uy, T_, 0, g->L.ny);
         if (st != MRT_OK) return st;
     } else {
         if (!g->macro_tmp) {
@@ -730,7 +789,7 @@ static mrt_status do_init(mrt_grid* g, const double* rho, const double* ux, cons
                                          g->xstream));
             CUDA_TRY(cudaEventRecord(g->ev_x, g->xstream));
             CUDA_TRY(cudaStreamWaitEvent(g->stream, g->ev_x, 0));
-            mrt_status st = init_rows<T>(g, fold, d, d + n, d + 2 * n, d + 3 * n, y0, y1);
+            mrt_status st = init_rows<T>(g, ic, d, d + n, d + 2 * n, d + 3 * n, y0, y1);
             if (st != MRT_OK) return st;
         }
     }
