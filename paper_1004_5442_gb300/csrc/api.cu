@@ -361,6 +361,31 @@ __global__ void ghost_rows_kernel(Layout L, int lo, int hi, T* f) {
     }
 }
 
+// The border of a padded buffer, everything but the interior cells: rows 0
+// and ny + 1 whole, and in rows 1 .. ny the columns before the interior
+// (padding and the left ghost) and after it (the right ghost and padding).
+// border_kernel zeroes it in dst (src == nullptr) or copies it from src.
+template <class T>
+__global__ void border_kernel(Layout L, const T* __restrict__ src, T* __restrict__ dst) {
+    const long side = L.pitch - L.nx;                    // border columns of an interior row
+    const long per_plane = 2L * L.pitch + (long)L.ny * side;
+    const long n = 16L * per_plane;
+    for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < n; t += (long)gridDim.x * blockDim.x) {
+        const long i = t / per_plane, k = t % per_plane;
+        long o;
+        if (k < L.pitch) {
+            o = k;                                       // row 0
+        } else if (k < 2L * L.pitch) {
+            o = (long)(L.ny + 1) * L.pitch + (k - L.pitch);   // row ny + 1
+        } else {
+            const long r = (k - 2L * L.pitch) / side, c = (k - 2L * L.pitch) % side;
+            o = (r + 1) * L.pitch + (c < L.G ? c : c + L.nx);
+        }
+        o += i * L.plane;
+        dst[o] = src ? src[o] : (T)0;
+    }
+}
+
 template <class T>
 __device__ __forceinline__ void cons_moments(const T* f, const Layout& L, long o, double q[4]) {
     double v[16];
@@ -766,6 +791,11 @@ static mrt_status do_init(mrt_grid* g, const double* rho, const double* ux, cons
     InitCoef ic;
     if (mrt_init_coef_build(g->b, &ic) != 0) return fail(MRT_ECUDA, "model blocks singular");
     const long n = (long)g->L.nx * g->L.ny;
+    // padding zero (a guard band no kernel writes) and ghosts cleared for
+    // the ghost kernels; the initialisation writes the interior
+    border_kernel<T><<<grid_for(16L * (2L * g->L.pitch + (long)g->L.ny * (g->L.pitch - g->L.nx)), 256), 256, 0,
+                       g->stream>>>(g->L, nullptr, static_cast<T*>(g->f[0]));
+    CUDA_TRY(cudaGetLastError());
     if (!host) {
         mrt_status st = init_rows<T>(g, ic, rho, ux, uy, T_, 0, g->L.ny);
         if (st != MRT_OK) return st;
@@ -795,8 +825,11 @@ static mrt_status do_init(mrt_grid* g, const double* rho, const double* ux, cons
     }
     launch_ghosts<T>(g, 0);
     CUDA_TRY(cudaGetLastError());
-    // both buffers carry the same ghosts (fixed ones are never rewritten)
-    CUDA_TRY(cudaMemcpyAsync(g->f[1], g->f[0], 16 * g->L.plane * g->elem, cudaMemcpyDeviceToDevice, g->stream));
+    // both buffers carry the same ghosts (fixed ones are never rewritten) and
+    // zero padding; the first step writes the other buffer's interior
+    border_kernel<T><<<grid_for(16L * (2L * g->L.pitch + (long)g->L.ny * (g->L.pitch - g->L.nx)), 256), 256, 0,
+                       g->stream>>>(g->L, static_cast<const T*>(g->f[0]), static_cast<T*>(g->f[1]));
+    CUDA_TRY(cudaGetLastError());
     return MRT_OK;
 }
 
@@ -842,10 +875,8 @@ extern "C" mrt_status mrt_create(const mrt_params* params, const double* rho, co
     if ((e = cudaMalloc(&g->f[0], bytes)) != cudaSuccess || (e = cudaMalloc(&g->f[1], bytes)) != cudaSuccess)
         return bail(fail(e == cudaErrorMemoryAllocation ? MRT_ENOMEM : MRT_ECUDA,
                          "cudaMalloc of 2 x %zu bytes failed: %s", bytes, cudaGetErrorString(e)));
-    // buffer 0's padding stays zero from here on; buffer 1 is a copy of
-    // buffer 0 once the initial state is written
-    if ((e = cudaMemsetAsync(g->f[0], 0, bytes, g->stream)) != cudaSuccess)
-        return bail(fail(MRT_ECUDA, "memset: %s", cudaGetErrorString(e)));
+    // the initialisation writes every word of buffer 0 (interior, ghosts,
+    // zero padding) and the border of buffer 1
     if ((e = cudaMalloc(&g->flag, sizeof(unsigned))) != cudaSuccess ||
         (e = cudaMemsetAsync(g->flag, 0, sizeof(unsigned), g->stream)) != cudaSuccess ||
         (e = cudaMalloc(&g->totals_dev, 4 * mrt_grid::kTotalsSlot * sizeof(double))) != cudaSuccess ||
