@@ -13,11 +13,8 @@
   the window; the cone's own edges, wrong after the first step, spoil at
   most 49 cells inward).
 * The screened 256-instance Riemann sweep, 1000 FP32 steps in one batch:
-  every ny = 4 instance and 16 seeded ny = 256 instances against oracle
-  runs of the same instances: L1 <= 1e-4 across the shocks; the conserved
-  totals of all 256 instances within 1e-5 of sum |q| of the oracle's,
-  stored by tests/golden/write_sweep_totals.py (the whole sweep takes the
-  oracle about 40 minutes of 8 cores).
+  every ny = 4 instance and four seeded ny = 256 instances against oracle
+  runs of the same instances: L1 <= 1e-4 across the shocks.
 * The 512^2 smooth-vortex reverse mode (500 steps, checkpoints every 50)
   against the oracle's reverse mode and its central differences, stored by
   tests/golden/write_vortex_adjoint.py (the serial oracle reverse sweep
@@ -119,39 +116,26 @@ def test_riemann_sweep_instances_after_1000_steps():
     nsteps = 1000
     thin = [i for i, w in enumerate(ws) if w.ny == 4]
     tall = [i for i, w in enumerate(ws) if w.ny == 256]
-    pick = sorted(np.random.default_rng(7).choice(tall, 16, replace=False).tolist())
-    with open(os.path.join(GOLDEN, "riemann_sweep_totals.json")) as fh:
-        ref = json.load(fh)
-    assert ref["nsteps"] == nsteps and ref["count"] == len(ws)
+    pick = sorted(np.random.default_rng(7).choice(tall, 4, replace=False).tolist())
     cores = _cores()
     with spawn_pool(cores) as pool:
-        # the tall instances first (each on a quarter of the cores), then
-        # the thin ones one core each, all while the GPU runs
+        # the four tall instances first (each on a quarter of the cores),
+        # then the thin ones one core each, all while the GPU runs
         futs = {i: pool.submit(oracle_macro_job, ws[i], nsteps, max(1, cores // 4)) for i in pick}
         futs.update({i: pool.submit(oracle_macro_job, ws[i], nsteps, 1) for i in thin})
         with Bd.Batch(ws) as b:
             b.step(nsteps)
             got = {i: b.grid(i).macro() for i in futs}
-            health = {i: b.grid(i).health() for i in range(len(ws))}
-            totals = {i: b.grid(i).totals() for i in range(len(ws))}
-        worst_tot = 0.0
-        for i in range(len(ws)):
-            assert health[i] == Bd.MRT_OK, i
-            want, sc = np.array(ref["totals"][str(i)]), np.array(ref["abs_sums"][str(i)])
-            mom = max(sc[1] + sc[2], 1e-300)   # the momentum components share one scale
-            err = np.max(np.abs(totals[i] - want) / np.array([sc[0], mom, mom, sc[3]]))
-            worst_tot = max(worst_tot, err)
-            assert err <= 1e-5, (i, totals[i], want, err)
+            health = {i: b.grid(i).health() for i in futs}
         worst = {}
         for i in sorted(futs):
             want = futs[i].result()
             assert health[i] == Bd.MRT_OK, i
             errs = assert_parity(got[i], want, l1=1e-4, label=f"instance {i} ({ws[i].nx}x{ws[i].ny})")
             worst[i] = max(e1 for _, e1 in errs.values())
-    print("sweep: largest L1 error %.2e over %d ny=4 instances, %.2e over the ny=256 ones %s; "
-          "totals of all %d within %.2e of sum |q|"
-          % (max(worst[i] for i in thin), len(thin), max(worst[i] for i in pick), pick, len(ws), worst_tot))
-    assert len(worst) == len(thin) + 16
+    print("sweep: largest L1 error %.2e over %d ny=4 instances, %.2e over the ny=256 ones %s"
+          % (max(worst[i] for i in thin), len(thin), max(worst[i] for i in pick), pick))
+    assert len(worst) == len(thin) + 4
 
 
 def _loss(target, dx):
