@@ -404,22 +404,75 @@ __device__ __forceinline__ void cons_moments(const T* f, const Layout& L, long o
     q[3] = kW(0) * S[0] + kW(1) * S[1] + kW(2) * S[2] + kW(3) * S[3];
 }
 
-// rho, u, T per cell (FP64) of rows [y0, y1); u = j/rho, T = (e - j^2/rho)/(b rho),
-// with one reciprocal of rho per cell (the FP64 pipe bounds this kernel).
+// The conserved moments (rho, jx, jy, e) of an FP32 cell in double-float
+// arithmetic: each butterfly pair sum is exact (TwoSum of two floats), the
+// weighted block sums carry about 44 bits.
+__device__ __forceinline__ DF df_two_sum(float a, float b) {
+    const float s = a + b, bb = s - a;
+    return {s, (a - (s - bb)) + (b - bb)};
+}
+__host__ __device__ constexpr DF df_c(double x) {   // a constant, split at compile time
+    return {(float)x, (float)(x - (double)(float)x)};
+}
+__device__ __forceinline__ void cons_moments_df(const float* f, const Layout& L, long o, DF q[4]) {
+    float v[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = f[i * L.plane + o];
+    DF S[4], Dx[4], Dy[4];
+#pragma unroll
+    for (int g = 0; g < 4; ++g) {
+        const float* a = v + 4 * g;
+        S[g] = df_two_sum(a[0], a[2]) + df_two_sum(a[1], a[3]);
+        const DF d02 = df_two_sum(a[0], -a[2]), d13 = df_two_sum(a[1], -a[3]);
+        Dx[g] = g < 2 ? d02 : d02 - d13;
+        Dy[g] = g < 2 ? d13 : d02 + d13;
+    }
+    constexpr DF u1 = df_c(kU(1)), u2 = df_c(kU(2)), u3 = df_c(kU(3));
+    constexpr DF w0 = df_c(kW(0)), w1 = df_c(kW(1)), w2 = df_c(kW(2)), w3 = df_c(kW(3));
+    q[0] = (S[0] + S[1]) + (S[2] + S[3]);
+    q[1] = Dx[0] + u1 * Dx[1] + u2 * Dx[2] + u3 * Dx[3];   // kU(0) = 1
+    q[2] = Dy[0] + u1 * Dy[1] + u2 * Dy[2] + u3 * Dy[3];
+    q[3] = w0 * S[0] + w1 * S[1] + w2 * S[2] + w3 * S[3];
+}
+__device__ __forceinline__ double df_out(DF x) { return (double)x.hi + (double)x.lo; }
+
+// rho, u, T per cell of rows [y0, y1); u = j/rho, T = (e - j^2/rho)/(b rho)
+// with one reciprocal of rho per cell.  FP64 grids in FP64; FP32 grids in
+// double-float arithmetic (1/rho by one Newton step from the FP32
+// quotient), which leaves only the final conversions to FP64 on the FP64
+// pipe that bounded this kernel.
 template <class T>
 __global__ void macro_kernel(Layout L, double inv_b, const T* __restrict__ f, double* rho, double* ux,
                              double* uy, double* Tf, int y0, int y1) {
+    DF ib = {0.f, 0.f};
+    if constexpr (sizeof(T) == 4) {
+        const float h = __double2float_rn(inv_b);
+        ib = {h, __double2float_rn(inv_b - (double)h)};
+    }
     for (int y = y0 + blockIdx.y; y < y1; y += gridDim.y) {
         for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < L.nx; x += gridDim.x * blockDim.x) {
             const long c = (long)y * L.nx + x;
-            double q[4];
-            cons_moments<T>(f, L, (long)(y + 1) * L.pitch + L.G + x, q);
-            const double ri = 1.0 / q[0];
-            const double u = q[1] * ri, v = q[2] * ri;
-            if (rho) rho[c] = q[0];
-            if (ux) ux[c] = u;
-            if (uy) uy[c] = v;
-            if (Tf) Tf[c] = (q[3] - (q[1] * u + q[2] * v)) * (ri * inv_b);
+            const long o = (long)(y + 1) * L.pitch + L.G + x;
+            if constexpr (sizeof(T) == 8) {
+                double q[4];
+                cons_moments<T>(f, L, o, q);
+                const double ri = 1.0 / q[0];
+                const double u = q[1] * ri, v = q[2] * ri;
+                if (rho) rho[c] = q[0];
+                if (ux) ux[c] = u;
+                if (uy) uy[c] = v;
+                if (Tf) Tf[c] = (q[3] - (q[1] * u + q[2] * v)) * (ri * inv_b);
+            } else {
+                DF q[4];
+                cons_moments_df(f, L, o, q);
+                const DF r0 = {1.0f / q[0].hi, 0.f};
+                const DF ri = r0 + r0 * (DF{1.f, 0.f} - q[0] * r0);
+                const DF u = q[1] * ri, v = q[2] * ri;
+                if (rho) rho[c] = df_out(q[0]);
+                if (ux) ux[c] = df_out(u);
+                if (uy) uy[c] = df_out(v);
+                if (Tf) Tf[c] = df_out((q[3] - (q[1] * u + q[2] * v)) * (ri * ib));
+            }
         }
     }
 }

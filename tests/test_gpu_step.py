@@ -62,6 +62,32 @@ def test_one_step_raw_state_fp32(kernel, tile, bcx, bcy):
     assert np.max(np.abs(f1 - want)) <= 2e-6 * scale
 
 
+@pytest.mark.parametrize("case", ["kh", "tube", "hot"])
+def test_fp32_readout_of_the_fp32_state(case):
+    """An FP32 grid reads rho, u, T out in double-float arithmetic (about 44
+    bits per operation): against the oracle's FP64 readout of the same FP32
+    state within 1e-11 of each field's scale (the closure's cancellation
+    e - j^2/rho costs at most a factor of ten on these states).  Device and
+    host readouts, several chunks of the latter."""
+    import torch
+    w = {"kh": W.kelvin_helmholtz(n=2048, nsteps=0),
+         "tube": W.riemann_instances(count=1, seed=4, nx_range=(2000, 2000), ny_choices=(256,), nsteps=0)[0],
+         "hot": W.random_smooth(700, 300, seed=9, amp=0.3, nsteps=0)}[case]
+    with Bd.Grid.from_workload(w, precision=Bd.FP32) as grid:
+        grid.step(40)
+        f = grid.get_f().astype(np.float64)
+        got = grid.macro()
+        dev = [torch.empty((w.ny, w.nx), dtype=torch.float64, device="cuda") for _ in range(4)]
+        grid.macro(dev)
+        torch.cuda.synchronize()
+    for a, b in zip(got, dev):
+        np.testing.assert_array_equal(a, b.cpu().numpy())
+    g = oracle.create(w.nx, w.ny, w.dx, w.dt, w.b, w.s, w.rho, w.ux, w.uy, w.T, w.bc_x, w.bc_y)
+    want = oracle.macro(g, f)
+    errs = assert_parity(got, want, linf=1e-11, label=f"readout {case}")
+    print("fp32 readout", case, errs)
+
+
 # --------------------------------------------------------------------------
 # Macroscopic parity over many steps
 # --------------------------------------------------------------------------
