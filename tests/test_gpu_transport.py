@@ -128,3 +128,59 @@ def test_sound_speed(prec, gamma, T0):
     print("sound", prec, gamma, T0, cs, np.sqrt(gamma * T0), len(tz))
     assert len(tz) >= 4
     assert abs(cs / np.sqrt(gamma * T0) - 1) < 0.005, (cs, np.sqrt(gamma * T0))
+
+
+@pytest.mark.parametrize("prec", [Bd.FP32, Bd.FP64])
+@pytest.mark.parametrize("gamma", [1.4, 5.0 / 3.0])
+def test_prandtl_number_and_gamma(prec, gamma):
+    """The two model parameters the extra energy degree of freedom frees,
+    measured at one rate set (sigma_6 = sigma_7 = 0.01, sigma_8 = sigma_9 =
+    0.71 sigma_6: Pr = s_8 / s_6 = 0.71) and T0 = 2 (spectral radius 0.99997
+    at gamma 1.4, 0.99924 at 5/3): gamma = c_s^2 / T0 from a sound wave
+    within 1 % (measured +0.4 %), and Pr = nu / alpha from a shear and an
+    entropy wave within 2 %: at sigma = 0.01, the smallest rate for which
+    these states are stable (sigma = 0.005: spectral radius 1.0008 to
+    1.003), the step's O(sigma) terms put nu at +0.8 % and alpha at -0.5 %
+    of their Chapman-Enskog values in FP32 and FP64 alike, so their ratio
+    lands at +1.3 to +1.5 %."""
+    sig = W.default_sigma(0.01, 0.71)
+    T0, k2 = 2.0, (2 * np.pi) ** 2
+    amp = 5e-2 if prec == Bd.FP32 else A
+    g, w, s = _grid(sig, 1.0, 0.0, amp * np.sin(2 * np.pi * _x()), T0, gamma, prec)
+    with g:
+        g.step(2000)
+        shear = []
+        for n in range(2000, 30001, 4000):
+            shear.append((n, _proj(g.macro()[2])))
+            g.step(4000)
+    nu = _decay_rate(shear, w.dt) / k2
+    d = A * np.sin(2 * np.pi * _x())
+    g, w, s = _grid(sig, 1.0 / (1 + d), 0.0, 0.0, T0 * (1 + d), gamma, prec)
+    with g:
+        g.step(2000)
+        ent = []
+        for n in range(2000, 20001, 2000):
+            r, _, _, Tf = g.macro()
+            ent.append((n, _proj(Tf) / T0 - (gamma - 1) / gamma * _proj(r * Tf) / T0))
+            g.step(2000)
+    alpha = _decay_rate(ent, w.dt) / k2
+    rho = 1 + A * np.sin(2 * np.pi * _x(2 * NX))
+    g, w2, _ = _grid(sig, rho, 0.0, 0.0, T0, gamma, prec, nx=2 * NX)
+    period_steps = 1.0 / np.sqrt(gamma * T0) / w2.dt
+    every = max(1, int(period_steps / 120))
+    with g:
+        ts, ps = [], []
+        for n in range(0, int(2.6 * period_steps), every):
+            r, _, _, Tf = g.macro()
+            ts.append(n * w2.dt)
+            ps.append(_proj(r * Tf))
+            g.step(every)
+    ts, ps = np.array(ts), np.array(ps)
+    i = np.where(np.sign(ps[:-1]) != np.sign(ps[1:]))[0]
+    tz = ts[i] - ps[i] * (ts[i + 1] - ts[i]) / (ps[i + 1] - ps[i])
+    cs = 1.0 / (2 * np.mean(np.diff(tz)))
+    pr, gam = nu / alpha, cs * cs / T0
+    print("Pr, gamma", prec, gamma, pr, gam)
+    assert abs(nu * s[6] / T0 - 1) < 0.01 and abs(alpha * s[7] / T0 - 1) < 0.01, (nu, alpha)
+    assert abs(pr / 0.71 - 1) < 0.02, (pr, nu, alpha)
+    assert abs(gam / gamma - 1) < 0.01, (gam, gamma)
